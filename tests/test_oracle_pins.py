@@ -1,0 +1,348 @@
+"""Pins for the CPU oracle: each check ties an oracle function to the paper or to mathematics
+it cannot reproduce by construction (invariants, closed forms, printed values, brute force)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import heat as H
+from workloads import synthetic as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny(dim, scheme, theta=0.5, varcoef=True, mx=4, my=3, n=6, seed=11):
+    my = 1 if dim == 1 else my
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=varcoef, seed=seed)
+    return w, H.Problem.from_workload(w)
+
+
+# ----------------------------------------------------------------------------- transforms
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 33, 64])
+def test_dst_matrix_invariants(n):
+    """S_n symmetric, orthogonal, involutory and S_n P_n S_n = D_n (Sec. 3.1.1)."""
+    S = H.dst_matrix(n)
+    assert np.allclose(S, S.T, atol=1e-15)
+    assert np.allclose(S @ S, np.eye(n), atol=1e-13)
+    Pn = 0.5 * (np.eye(n, k=1) + np.eye(n, k=-1))
+    D = S @ Pn @ S
+    assert np.allclose(D, np.diag(H.time_cos(n)), atol=1e-13)
+    # eigenvalues of tridiag(-1,2,-1): 2 - 2 cos(k pi/(n+1)) = 4 sin^2(k pi/(2(n+1)))
+    L = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    k = np.arange(1, n + 1)
+    assert np.allclose(np.diag(S @ L @ S), 4 * np.sin(k * math.pi / (2 * (n + 1))) ** 2, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,axis", [(7, 0), (16, 1), (31, 0)])
+def test_dst_routine_is_sine_matrix(n, axis):
+    """The library transform the oracle calls equals the matrix S_n of Sec. 3.1.1."""
+    rng = np.random.default_rng(n)
+    V = rng.standard_normal((n, 5)) if axis == 0 else rng.standard_normal((5, n))
+    ref = H.dst_matrix(n) @ V if axis == 0 else V @ H.dst_matrix(n)
+    assert np.allclose(H.dst(V, axis=axis), ref, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- space operator
+@pytest.mark.parametrize("dim", [1, 2])
+def test_stiffness_energy_form(dim):
+    """v^T K v = sum over faces a_f (v_p - v_q)^2 / h^2 with zero boundary values (eq. matrix_Km_va)."""
+    w, p = _tiny(dim, "theta", mx=6, my=5)
+    K = H.stiffness(p).toarray()
+    assert np.allclose(K, K.T)
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(p.m)
+    a = w.a_nodal
+    e = 0.0
+    if dim == 1:
+        vp = np.concatenate([[0.0], v, [0.0]])
+        for i in range(p.mx + 1):
+            af = 0.5 * (a[i] + a[i + 1])
+            e += af * (vp[i + 1] - vp[i]) ** 2 / p.hx ** 2
+    else:
+        V = np.zeros((p.my + 2, p.mx + 2))
+        V[1:-1, 1:-1] = v.reshape(p.my, p.mx)
+        for j in range(1, p.my + 1):
+            for i in range(p.mx + 1):
+                af = 0.5 * (a[j, i] + a[j, i + 1])
+                e += af * (V[j, i + 1] - V[j, i]) ** 2 / p.hx ** 2
+        for j in range(p.my + 1):
+            for i in range(1, p.mx + 1):
+                af = 0.5 * (a[j, i] + a[j + 1, i])
+                e += af * (V[j + 1, i] - V[j, i]) ** 2 / p.hy ** 2
+    assert np.isclose(v @ K @ v, e, rtol=1e-12)
+    assert np.all(np.linalg.eigvalsh(K) > 0)
+
+
+def test_stiffness_constant_eigenvectors():
+    """For a = 1 the sine modes are eigenvectors: K s_p = (2 - 2cos(p pi h))/h^2 s_p (+ y term)."""
+    p = H.Problem(2, 7, 5, 3)
+    K = H.stiffness(p)
+    X, Y = W.interior_grid(7, 5)
+    for (a, b) in [(1, 1), (3, 2), (7, 5)]:
+        s = (np.sin(a * math.pi * X) * np.sin(b * math.pi * Y)).reshape(-1)
+        lam = (2 - 2 * math.cos(a * math.pi * p.hx)) / p.hx ** 2 + (2 - 2 * math.cos(b * math.pi * p.hy)) / p.hy ** 2
+        assert np.allclose(K @ s, lam * s, atol=1e-9)
+    mu = H.averaged_stiffness_eigs(p)
+    assert np.allclose(np.sort(mu), np.sort(np.linalg.eigvalsh(K.toarray())), rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------- all-at-once system
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("scheme", ["theta", "bdf2"])
+def test_flipped_operator_symmetric(dim, scheme):
+    """Y T is symmetric (eq. main_system / main_system_gem_sym) and T^T = Y T Y."""
+    w, p = _tiny(dim, scheme)
+    Nn = p.N
+    E = np.eye(Nn)
+    YT = np.stack([H.apply_op(p, E[i]).reshape(-1) for i in range(Nn)], axis=1)
+    assert np.allclose(YT, YT.T, atol=1e-12)
+    T = H.all_at_once_matrix(p).toarray()
+    Y = H.flip_matrix(p.n, p.m).toarray()
+    assert np.allclose(Y @ T, YT, atol=1e-12)
+    assert np.allclose(T.T, Y @ T @ Y, atol=1e-12)
+    # transpose application
+    v = np.random.default_rng(3).standard_normal(Nn)
+    assert np.allclose(H.apply_T_transpose(p, v).reshape(-1), T.T @ v, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("scheme,theta", [("theta", 1.0), ("theta", 0.5), ("theta", 0.3), ("bdf2", 1.0)])
+def test_all_at_once_equals_time_marching(dim, scheme, theta):
+    """Solving T u = f_H at once equals stepping the scheme sequentially (Sec. 1)."""
+    w, p = _tiny(dim, scheme, theta=theta, mx=5, my=4, n=7)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    T = H.all_at_once_matrix(p).tocsc()
+    u_direct = spla.spsolve(T, fH.reshape(-1)).reshape(p.n, p.m)
+    u_march = H.march(p, w.f, w.u0, w.u_prev)
+    assert np.allclose(u_direct, u_march, rtol=1e-11, atol=1e-11)
+
+
+def _error_1d(scheme, theta, mx, n):
+    if scheme == "bdf2":
+        w = W.config_1d_sine(mx, n, theta=1.0)
+        w.scheme = "bdf2"
+        w.u_prev = math.exp(-w.tau) * w.u0
+    else:
+        w = W.config_1d_sine(mx, n, theta=theta)
+    p = H.Problem.from_workload(w)
+    u = H.march(p, w.f, w.u0, w.u_prev)
+    return np.abs(u - w.u_exact).max()
+
+
+@pytest.mark.parametrize("scheme,theta,order", [("theta", 1.0, 1), ("theta", 0.5, 2), ("bdf2", 1.0, 2)])
+def test_time_order(scheme, theta, order):
+    """Manufactured solution: backward Euler is first order, Crank-Nicolson and BDF2 second."""
+    mx = 2047  # spatial error ~ h^2 far below the time error at these n
+    e1 = _error_1d(scheme, theta, mx, 16)
+    e2 = _error_1d(scheme, theta, mx, 32)
+    rate = math.log2(e1 / e2)
+    assert abs(rate - order) < 0.15, rate
+
+
+def test_space_order():
+    """Second order in space (Crank-Nicolson with many steps isolates the spatial error)."""
+    e = [_error_1d("theta", 0.5, mx, 4096) for mx in (15, 31)]
+    assert abs(math.log2(e[0] / e[1]) - 2.0) < 0.1
+
+
+def test_table5_backward_euler_errors():
+    """Example 2 errors printed in Table 5 (backward Euler, m+1 = 32), three digits."""
+    g = json.load(open(os.path.join(GOLDEN, "table5_backward_euler.json")))
+    for n, ref in zip(g["n"], g["error"]):
+        w = W.paper_example2(g["m_plus_1"] - 1, n, 1.0)
+        p = H.Problem.from_workload(w)
+        fH = H.rhs(p, w.f, w.u0)
+        x, info = H.solve(p, fH, tol=1e-6, maxit=100)
+        err = np.abs(x - w.u_exact).max()
+        assert float(f"{err:.2e}") == ref, (n, err, ref)
+
+
+def test_table_iteration_counts():
+    """Iteration counts of Tables 1-3 (P_H, P_theta) within +-2 (stopping-rule details differ)."""
+    g = json.load(open(os.path.join(GOLDEN, "table_iterations.json")))
+    for c in g["cases"]:
+        mx = c["m_plus_1"] - 1
+        if c["example"] == 1:
+            w = W.paper_example1(mx, c["n"], c["theta"])
+        else:
+            w = W.paper_example2(mx, c["n"], c["theta"])
+        p = H.Problem.from_workload(w, prec=c["prec"])
+        fH = H.rhs(p, w.f, w.u0)
+        x, info = H.solve(p, fH, tol=1e-6, maxit=100)
+        assert abs(info["iterations"] - c["iter"]) <= g["tolerance_iterations"], (c, info["iterations"])
+
+
+# ----------------------------------------------------------------------------- preconditioners
+def _averaged_dense_K(p):
+    """Average K's entries along each of its diagonals (Sec. 3.1.1), 2D: x- and y-couplings apart."""
+    K = H.stiffness(p).toarray()
+    m, mx = p.m, p.mx
+    d = np.mean(np.diag(K))
+    offx = np.diag(K, 1)
+    ex = np.mean(offx[np.arange(m - 1) % mx != mx - 1]) if mx > 1 else 0.0
+    Kb = d * np.eye(m)
+    for i in range(m - 1):
+        if (i % mx) != mx - 1:
+            Kb[i, i + 1] = Kb[i + 1, i] = ex
+    if p.dim == 2:
+        ey = np.mean(np.diag(K, mx))
+        for i in range(m - mx):
+            Kb[i, i + mx] = Kb[i + mx, i] = ey
+    return Kb
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("scheme", ["theta", "bdf2"])
+@pytest.mark.parametrize("varcoef", [False, True])
+def test_prec_squared_is_block_matrix(dim, scheme, varcoef):
+    """P^{-1} P^{-1} (P^2 v) = v with P^2 built entry by entry from eq. def:matrix_P / def:matrix_P_gen."""
+    w, p = _tiny(dim, scheme, theta=0.7, varcoef=varcoef, mx=5, my=4, n=7)
+    Kb = _averaged_dense_K(p)
+    P2 = H.dense_PH_squared(p, Kb)
+    v = np.random.default_rng(5).standard_normal((p.n, p.m))
+    z = H.apply_prec(p, H.apply_prec(p, (P2 @ v.reshape(-1)).reshape(p.n, p.m)))
+    assert np.allclose(z, v, rtol=1e-11, atol=1e-11)
+    # and the dense principal square root gives the same preconditioner
+    Pd = H.sqrtm_spd(P2)
+    assert np.allclose(H.apply_prec(p, v).reshape(-1), np.linalg.solve(Pd, v.reshape(-1)), atol=1e-11)
+
+
+def test_lemma_rank_difference():
+    """T^T T - P_H^2 = diag(0, ..., 0, -A1^2) (Lemma rankC_P), constant a."""
+    p = H.Problem(2, 3, 3, 6, 1.0, "theta", 0.5)
+    T = H.all_at_once_matrix(p).toarray()
+    P2 = H.dense_PH_squared(p)
+    D = T.T @ T - P2
+    m = p.m
+    K = H.stiffness(p).toarray()
+    A1 = -np.eye(m) + (1 - p.theta) * p.tau * K
+    expect = np.zeros_like(D)
+    expect[-m:, -m:] = -A1 @ A1
+    assert np.allclose(D, expect, atol=1e-9)
+
+
+def test_normal_equations_unit_eigenvalues():
+    """P^{-1} T^T T P^{-1} has at least m(n-1) eigenvalues equal to one (Theorem main_P_normal)."""
+    p = H.Problem(1, 4, 1, 7, 1.0, "theta", 1.0)
+    T = H.all_at_once_matrix(p).toarray()
+    Pinv = np.linalg.inv(H.sqrtm_spd(H.dense_PH_squared(p)))
+    ev = np.linalg.eigvalsh(Pinv @ T.T @ T @ Pinv)
+    assert np.sum(np.abs(ev - 1.0) < 1e-9) >= p.m * (p.n - 1)
+
+
+def test_bdf2_rank():
+    """rank(T[|g|^2] - P-hat^2) = 2m for BDF2 (Sec. 4, Lemma rankC_P_gen with l = 2)."""
+    p = H.Problem(1, 3, 1, 9, 1.0, "bdf2")
+    D = H.dense_symbol_toeplitz_sq(p) - H.dense_PH_squared(p)
+    assert np.linalg.matrix_rank(D, tol=1e-9) == 2 * p.m
+
+
+@pytest.mark.parametrize("varcoef", [False, True])
+def test_ptheta_matches_dense(varcoef):
+    """P_theta^{-1} v equals the dense solve with H (x) I + H_theta (x) tau K (eq. def:matrix_mod_P)."""
+    w, p = _tiny(2, "theta", theta=0.5, varcoef=varcoef, mx=4, my=3, n=6)
+    p.prec = "Ptheta"
+    v = np.random.default_rng(2).standard_normal((p.n, p.m))
+    ref = np.linalg.solve(H.dense_Ptheta(p), v.reshape(-1))
+    assert np.allclose(H.apply_ptheta(p, v).reshape(-1), ref, atol=1e-11)
+
+
+def test_preconditioned_spectrum_clusters():
+    """Eigenvalues of P^{-1} Y T cluster at +-1 with a number of outliers that does not depend on n
+    (Theorem absP_main). The blocks A0, A1 are held fixed (fixed tau) while n grows."""
+    for th in (1.0, 0.5):
+        outl = []
+        for n in (32, 64, 128):
+            p = H.Problem(1, 3, 1, n, n / 32.0, "theta", th)
+            T = H.all_at_once_matrix(p).toarray()
+            Y = H.flip_matrix(n, p.m).toarray()
+            Pinv = np.linalg.inv(H.sqrtm_spd(H.dense_PH_squared(p)))
+            ev = np.linalg.eigvals(Pinv @ Y @ T).real
+            dist = np.minimum(np.abs(ev - 1), np.abs(ev + 1))
+            outl.append(int(np.sum(dist > 0.01)))
+        assert len(set(outl)) == 1 and outl[0] <= 3 * p.m, (th, outl)
+
+
+# ----------------------------------------------------------------------------- MINRES
+def test_ideal_preconditioner_two_steps():
+    """With sqrt(T^T T) as preconditioner MINRES converges in at most two steps (Proposition absC)."""
+    p = H.Problem(2, 3, 2, 5, 1.0, "theta", 0.5)
+    T = H.all_at_once_matrix(p).toarray()
+    Y = H.flip_matrix(p.n, p.m).toarray()
+    Pinv = np.linalg.inv(H.sqrtm_spd(T.T @ T))
+    b = np.random.default_rng(4).standard_normal(p.N)
+    x, info = H.minres(lambda v: Y @ T @ v, lambda v: Pinv @ v, b, 1e-12, 10)
+    assert info["iterations"] <= 2
+    assert np.linalg.norm(Y @ T @ x - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_minres_iterates_are_krylov_minimisers():
+    """Iterate k minimises ||b - A x||_{M^{-1}} over x in span{M^{-1}b, (M^{-1}A) M^{-1}b, ...}."""
+    w, p = _tiny(1, "theta", theta=1.0, mx=4, n=5)
+    T = H.all_at_once_matrix(p).toarray()
+    Y = H.flip_matrix(p.n, p.m).toarray()
+    A = Y @ T
+    Pd = H.sqrtm_spd(H.dense_PH_squared(p, _averaged_dense_K(p)))
+    Minv = np.linalg.inv(Pd)
+    b = np.random.default_rng(8).standard_normal(p.N)
+    iterates = {}
+    H.minres(lambda v: A @ v, lambda v: Minv @ v, b, 0.0, 8,
+             callback=lambda k, x, est: iterates.__setitem__(k, (x.copy(), est)))
+    L = np.linalg.cholesky(Minv)  # ||r||_{M^{-1}} = ||L^T r||
+    basis = [Minv @ b]
+    for k in range(1, 9):
+        Q, _ = np.linalg.qr(np.stack(basis, axis=1))
+        c, *_ = np.linalg.lstsq(L.T @ A @ Q, L.T @ b, rcond=None)
+        xk = Q @ c
+        x_or, est = iterates[k]
+        assert np.allclose(x_or, xk, rtol=1e-7, atol=1e-9), k
+        rn = np.linalg.norm(L.T @ (b - A @ xk)) / np.linalg.norm(L.T @ b)
+        assert np.isclose(est, rn, rtol=1e-6, atol=1e-12), (k, est, rn)
+        basis.append(Minv @ (A @ basis[-1]))
+    ests = [iterates[k][1] for k in sorted(iterates)]
+    assert all(b2 <= b1 * (1 + 1e-12) for b1, b2 in zip(ests, ests[1:]))
+
+
+@pytest.mark.parametrize("scheme", ["theta", "bdf2"])
+def test_solve_matches_direct(scheme):
+    w, p = _tiny(2, scheme, theta=0.5, mx=6, my=5, n=8)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    x, info = H.solve(p, fH, tol=1e-13, maxit=200)
+    ref = spla.spsolve(H.all_at_once_matrix(p).tocsc(), fH.reshape(-1)).reshape(p.n, p.m)
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("dim,theta", [(1, 1.0), (2, 1.0), (2, 0.5)])
+def test_adjoint_gradients_vs_finite_differences(dim, theta):
+    """dL/d(f, u0, a) from the transposed solve equals central differences of the forward march."""
+    w, p = _tiny(dim, "theta", theta=theta, varcoef=True, mx=5, my=4, n=6, seed=21)
+    rng = np.random.default_rng(9)
+    u_obs = rng.standard_normal((p.n, p.m))
+
+    def loss(f, u0, a):
+        q = H.Problem(p.dim, p.mx, p.my, p.n, p.T, p.scheme, p.theta, a)
+        u = H.march(q, f, u0)
+        return 0.5 * np.sum((u - u_obs) ** 2)
+
+    u = H.march(p, w.f, w.u0)
+    lam, info = H.solve_transpose(p, u - u_obs, tol=1e-14, maxit=400)
+    T = H.all_at_once_matrix(p).tocsc()
+    lam_direct = spla.spsolve(T.T.tocsc(), (u - u_obs).reshape(-1)).reshape(p.n, p.m)
+    assert np.allclose(lam, lam_direct, rtol=1e-9, atol=1e-10)
+    gf, gu0, ga = H.adjoint_gradients(p, u, lam_direct, w.u0)
+    for target in ("f", "u0", "a"):
+        if target == "f":
+            d = rng.standard_normal(w.f.shape); g = np.sum(gf * d)
+            Lp = loss(w.f + 1e-5 * d, w.u0, w.a_nodal); Lm = loss(w.f - 1e-5 * d, w.u0, w.a_nodal)
+        elif target == "u0":
+            d = rng.standard_normal(w.u0.shape); g = np.sum(gu0 * d)
+            Lp = loss(w.f, w.u0 + 1e-5 * d, w.a_nodal); Lm = loss(w.f, w.u0 - 1e-5 * d, w.a_nodal)
+        else:
+            d = rng.standard_normal(w.a_nodal.shape); g = np.sum(ga * d)
+            Lp = loss(w.f, w.u0, w.a_nodal + 1e-5 * d); Lm = loss(w.f, w.u0, w.a_nodal - 1e-5 * d)
+        fd = (Lp - Lm) / 2e-5
+        assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (target, fd, g)
