@@ -1,0 +1,181 @@
+// Internal declarations shared by the translation units of the solver library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/st_minres.h"
+
+namespace st {
+
+// Geometry and coefficients of one problem, passed by value to kernels.
+struct Geom {
+  int dim, mx, my, n;
+  long long m, N;
+  int scheme;           // ST_THETA / ST_BDF2
+  double tau, theta;
+  const double *cx;     // [my][mx+1]  tau * a(x-face) / hx^2, faces i = 0..mx between nodes i-1, i
+  const double *cy;     // [my+1][mx]  tau * a(y-face) / hy^2 (NULL in 1D)
+};
+
+// Spectral tables used by the preconditioner kernels.
+template <class T>
+struct Spec {
+  const T *mux;    // [mx]  x-part of the (averaged) stiffness eigenvalue, times tau
+  const T *muy;    // [my]  y-part, times tau (zeros in 1D)
+  const T *hk;     // [n]   1 - cos(x_k), x_k = k pi/(n+1), k = 1..n (from 2 sin^2(x_k/2))
+  const T *ck;     // [n]   cos(x_k)
+  const T *sk;     // [n]   sin(x_k)
+  const T *lh;     // [n]   eigenvalues of H = sqrt(tridiag(-1,2,-1)): 2 sin(x_k/2)
+  const T *lht;    // [n]   eigenvalues of H_theta
+  const T *sintab; // [2(n+1)] sqrt(2/(n+1)) sin(r pi/(n+1))
+  int prec;        // ST_PREC_PH / ST_PREC_PTHETA
+  int scheme;
+  T theta;
+};
+
+// Device-resident MINRES scalars.  Written only by the last block of a kernel (the
+// "last block" reduction pattern) or by the host between solves.
+struct State {
+  double alpha, beta, beta_prev, beta1, eta;
+  double c1, s1, c2, s2;               // rotations k-1 and k-2
+  double inv_beta;                     // 1/beta_k, scale of z_k in the stencil
+  double lz_a, lz_b;                   // vhat_{k+1} = p - lz_a vhat_k - lz_b vhat_{k-1}
+  double dz, d1, d2, xc;               // d_k = dz z_k + d1 d_{k-1} + d2 d_{k-2};  x += xc d_k
+  double est, target;
+  double rnorm2;                       // residual kernel output ||r||^2
+  double bnorm2;                       // ||b||^2
+  int k, maxit;
+  int active, finish, status;
+  int pad;
+  unsigned int counter[8];             // completion counters of the last-block reductions
+};
+
+enum { CNT_STENCIL = 0, CNT_TIME = 1, CNT_RESID = 2, CNT_NORM = 3 };
+
+// Last-block completion: every block writes its partial, the last block to arrive sums all
+// partials in a fixed order (deterministic) and returns the total to thread 0.
+// Returns true in the (single) last block; *total is valid in its thread 0.
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__device__ inline double block_sum(double v, double *red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = (lane < NT / 32) ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in warp 0
+}
+
+// Flat thread index within the block, for 1D/2D blocks.
+__device__ inline int flat_tid() { return threadIdx.x + threadIdx.y * blockDim.x; }
+
+template <int NT>
+__device__ inline bool last_block_reduce(double part, double *partials, unsigned int *counter,
+                                         int nblocks, int bid, double *red, double *total) {
+  __shared__ bool is_last;
+  const int tid = flat_tid();
+  double s = block_sum<NT>(part, red);
+  if (tid == 0) {
+    partials[bid] = s;
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == (unsigned int)(nblocks - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = tid; i < nblocks; i += NT) acc += ((volatile double *)partials)[i];
+  double tot = block_sum<NT>(acc, red);
+  if (tid == 0) {
+    *total = tot;
+    *counter = 0u;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- kernel-class profiler
+// While a handle's profiler is on, each kernel launch is bracketed by CUDA events recorded on
+// the launching stream; the host sums the elapsed times per kernel class afterwards.
+enum {
+  KC_STENCIL = 0,  // flipped space-time stencil (MINRES and apply modes)
+  KC_LANCZOS = 1,  // Lanczos three-term update
+  KC_DSTX = 2,     // spatial DST along x (contiguous lines)
+  KC_DSTY = 3,     // spatial DST along y (strided lines)
+  KC_TIME = 4,     // time DST -> spectral scaling -> time DST (+ energy, Givens)
+  KC_UPDATE = 5,   // direction and solution update
+  KC_RESID = 6,    // true residual (stencil in residual mode)
+  KC_AUX = 7,      // rhs assembly, flips, norms, gradient
+  KC_COUNT = 8
+};
+
+struct Prof {
+  int on;
+  int cap, used;
+  cudaEvent_t *ev;  // 2*cap events
+  int *cls;         // class of each recorded pair
+  long long launches[KC_COUNT];
+};
+
+// per-thread pointer to the profiler of the handle whose call is running (or null)
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+// ---------------------------------------------------------------- launch-side declarations
+// stencil modes
+enum { SM_MINRES = 0, SM_APPLY = 1, SM_RESID = 2, SM_TRANSPOSE_APPLY = 3 };
+
+template <class Tz>
+cudaError_t launch_stencil(const Geom &g, int mode, const Tz *z, double *out, const double *fH,
+                           State *S, double *partials, int nblocks_hint, cudaStream_t st);
+int stencil_blocks(const Geom &g);
+
+cudaError_t launch_rhs(const Geom &g, const double *f, const double *u0, const double *uprev,
+                       const double *extra, double *fH, cudaStream_t st);
+cudaError_t launch_grad_a(const Geom &g, const double *lam, const double *u, const double *u0,
+                          double *gface_x, double *gface_y, double *grad, cudaStream_t st);
+
+// preconditioner pipeline: z = P^-1 v (v may be double, z double or float)
+struct PrecPlan {
+  int Lx, Ly;                 // FFT lengths 2(mx+1), 2(my+1)
+  const double *twx_d, *twy_d;  // e^{-2 pi i j/L}, j < L/2, interleaved (re, im)
+  const float *twx_f, *twy_f;
+  Spec<double> spec_d;
+  Spec<float> spec_f;
+  int time_J_d, time_J_f;     // spatial columns per time-kernel block
+  int time_blocks_d, time_blocks_f;
+  const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
+  const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
+};
+
+// energy mode of the time kernel's last block
+enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2 };
+
+template <class Tc, class Tin, class Tout>
+cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
+                        int tmode, double *partials, cudaStream_t st);
+int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32);
+
+// vector kernels
+cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,
+                           State *S, cudaStream_t st);
+template <class Tz>
+cudaError_t launch_update(long long N, const Tz *z, const double *d1, double *d2_out, double *x,
+                          State *S, cudaStream_t st);
+cudaError_t launch_flip(const Geom &g, const double *src, double *dst, cudaStream_t st);
+cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st);
+cudaError_t launch_norm2(long long N, const double *v, State *S, double *partials,
+                         cudaStream_t st);
+
+}  // namespace st

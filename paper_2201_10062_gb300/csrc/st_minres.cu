@@ -1,0 +1,867 @@
+// Host driver and C ABI of the solver: setup (face coefficients, spectral tables, workspace),
+// the preconditioned MINRES loop (Paige-Saunders recurrences with device-resident scalars) and
+// the mixed-precision iterative refinement around it.
+//
+// One MINRES iteration k (1-based) is four launches on the handle's stream:
+//   1. stencil:  p = Y T z_k / beta_k and alpha_k = <p, z_k/beta_k>            (st_stencil.cu)
+//   2. lanczos:  vhat_{k+1} = p - (alpha_k/beta_k) vhat_k - (beta_k/beta_{k-1}) vhat_{k-1}
+//   3. prec:     z_{k+1} = P^-1 vhat_{k+1}, beta_{k+1}^2 = <vhat_{k+1}, z_{k+1}>, Givens step (st_prec.cu)
+//   4. update:   d_k = (z_k/beta_k - delta d_{k-1} - eps d_{k-2})/rho,  x += c eta d_k
+// Scalars never leave the device inside the loop; the host reads the state every few
+// iterations to learn whether the device-side stopping test has fired.  Kernels launched after
+// that point return at entry, so the host may run ahead by a few iterations at no cost.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "st_internal.cuh"
+
+using namespace st;
+
+namespace st {
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kStreamBlocks = 152 * 8;
+
+__global__ void __launch_bounds__(kNT)
+    k_lanczos(long long N, const double *__restrict__ q, const double *__restrict__ vk,
+              double *__restrict__ vprev, const State *S) {
+  if (!S->active) return;
+  const double a = S->lz_a, b = S->lz_b;
+  const long long N2 = N >> 1;
+  const double2 *q2 = reinterpret_cast<const double2 *>(q);
+  const double2 *v2 = reinterpret_cast<const double2 *>(vk);
+  double2 *p2 = reinterpret_cast<double2 *>(vprev);
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N2;
+       i += (long long)gridDim.x * kNT) {
+    const double2 qq = q2[i], vv = v2[i], pp = p2[i];
+    double2 r;
+    r.x = qq.x - a * vv.x - b * pp.x;
+    r.y = qq.y - a * vv.y - b * pp.y;
+    p2[i] = r;
+  }
+  if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long i = N - 1;
+    vprev[i] = q[i] - a * vk[i] - b * vprev[i];
+  }
+}
+
+template <class Tz>
+__global__ void __launch_bounds__(kNT)
+    k_update(long long N, const Tz *__restrict__ z, const double *__restrict__ d1,
+             double *__restrict__ d2, double *__restrict__ x, const State *S) {
+  if (!S->active) return;
+  const double cz = S->dz, c1 = S->d1, c2 = S->d2, cx = S->xc;
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kNT) {
+    const double d = cz * (double)z[i] + c1 * d1[i] + c2 * d2[i];
+    d2[i] = d;
+    x[i] += cx * d;
+  }
+}
+
+// dst = Y src (block order reversed); in place when dst == src.
+__global__ void k_flip(long long m, int n, const double *src, double *dst) {
+  const long long total = (dst == src) ? (long long)(n / 2) * m : (long long)n * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / m, p = e - k * m;
+    const long long a = k * m + p, b = (long long)(n - 1 - k) * m + p;
+    if (dst == src) {
+      const double t = dst[a];
+      dst[a] = dst[b];
+      dst[b] = t;
+    } else {
+      dst[b] = src[a];
+    }
+  }
+}
+
+__global__ void k_fill(long long N, double *p, double v) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
+__global__ void __launch_bounds__(kNT)
+    k_norm2(long long N, const double *__restrict__ v, State *S, double *__restrict__ partials) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kNT) {
+    const double t = v[i];
+    acc += t * t;
+  }
+  double tot;
+  if (last_block_reduce<kNT>(acc, partials, &S->counter[CNT_NORM], gridDim.x, blockIdx.x, red,
+                             &tot) &&
+      threadIdx.x == 0)
+    S->bnorm2 = tot;
+}
+
+}  // namespace
+
+thread_local Prof *t_prof = nullptr;
+
+void prof_begin(int cls, cudaStream_t st) {
+  Prof *p = t_prof;
+  if (!p || !p->on) return;
+  p->launches[cls] += 1;
+  if (p->used < p->cap) {
+    p->cls[p->used] = cls;
+    cudaEventRecord(p->ev[2 * p->used], st);
+  }
+}
+
+void prof_end(cudaStream_t st) {
+  Prof *p = t_prof;
+  if (!p || !p->on) return;
+  if (p->used < p->cap) {
+    cudaEventRecord(p->ev[2 * p->used + 1], st);
+    p->used += 1;
+  }
+}
+
+cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,
+                           State *S, cudaStream_t st) {
+  prof_begin(KC_LANCZOS, st);
+  k_lanczos<<<kStreamBlocks, kNT, 0, st>>>(N, q, vk, vkm1_out, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+template <class Tz>
+cudaError_t launch_update(long long N, const Tz *z, const double *d1, double *d2_out, double *x,
+                          State *S, cudaStream_t st) {
+  prof_begin(KC_UPDATE, st);
+  k_update<Tz><<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip(const Geom &g, const double *src, double *dst, cudaStream_t st) {
+  prof_begin(KC_AUX, st);
+  k_flip<<<kStreamBlocks, kNT, 0, st>>>(g.m, g.n, src, dst);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
+  prof_begin(KC_AUX, st);
+  k_fill<<<kStreamBlocks, kNT, 0, st>>>(N, p, v);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(long long N, const double *v, State *S, double *partials,
+                         cudaStream_t st) {
+  prof_begin(KC_AUX, st);
+  k_norm2<<<kStreamBlocks, kNT, 0, st>>>(N, v, S, partials);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace st
+
+// ------------------------------------------------------------------------------------ handle
+struct st_handle {
+  st_problem prob;
+  Geom g;
+  PrecPlan pp;
+  cudaStream_t stream;
+  int device;
+  bool mixed;
+  // device memory
+  void *tables;          // face coefficients, spectral tables, twiddles (one allocation)
+  double *V[2];          // Lanczos vectors vhat
+  void *Z[2];            // preconditioned vectors (double, or float in ST_MIXED)
+  double *D[2];          // MINRES directions
+  double *q;             // stencil output
+  double *partials;      // per-block partial sums
+  State *S;              // device scalars
+  double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
+  double *gfx, *gfy;     // face-gradient scratch for st_grad_a
+  State *hS;             // pinned host mirror of S
+  int partials_len;
+  Prof prof;             // kernel-class timing (off unless st_profile_begin was called)
+};
+
+namespace {
+// Makes the handle's profiler the current one for the duration of a C-ABI call.
+struct ProfScope {
+  Prof *saved;
+  explicit ProfScope(st_handle *h) : saved(t_prof) { t_prof = h ? &h->prof : nullptr; }
+  ~ProfScope() { t_prof = saved; }
+};
+
+void prof_free(Prof &p) {
+  if (p.ev) {
+    for (int i = 0; i < 2 * p.cap; ++i) cudaEventDestroy(p.ev[i]);
+    delete[] p.ev;
+    delete[] p.cls;
+  }
+  p.ev = nullptr;
+  p.cls = nullptr;
+  p.cap = p.used = 0;
+  p.on = 0;
+}
+}  // namespace
+
+namespace {
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int check_problem(const st_problem *p) {
+  if (!p) return ST_ERR_ARG;
+  if (p->dim != 1 && p->dim != 2) return ST_ERR_ARG;
+  if (p->mx < 3 || p->mx > 1023 || !pow2(p->mx + 1)) return ST_ERR_ARG;
+  if (p->dim == 1 && p->my != 1) return ST_ERR_ARG;
+  if (p->dim == 2 && (p->my < 3 || p->my > 1023 || !pow2(p->my + 1))) return ST_ERR_ARG;
+  if (p->n < 1 || p->n > 1024) return ST_ERR_ARG;
+  if (!(p->T > 0.0) || !std::isfinite(p->T)) return ST_ERR_ARG;
+  if (p->scheme != ST_THETA && p->scheme != ST_BDF2) return ST_ERR_ARG;
+  if (p->scheme == ST_THETA && !(p->theta >= 0.0 && p->theta <= 1.0)) return ST_ERR_ARG;
+  if (p->prec != ST_PREC_PH && p->prec != ST_PREC_PTHETA) return ST_ERR_ARG;
+  if (p->precision != ST_FP64 && p->precision != ST_MIXED) return ST_ERR_ARG;
+  if (p->prec == ST_PREC_PTHETA && p->scheme != ST_THETA) return ST_ERR_ARG;
+  if (p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr) return ST_ERR_ARG;
+  if (p->a_nodal) {
+    const long long cnt = (p->dim == 1) ? (p->mx + 2) : (long long)(p->mx + 2) * (p->my + 2);
+    for (long long i = 0; i < cnt; ++i)
+      if (!(p->a_nodal[i] > 0.0) || !std::isfinite(p->a_nodal[i])) return ST_ERR_ARG;
+  }
+  return ST_OK;
+}
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return ST_OK;
+  if (e == cudaErrorMemoryAllocation) return ST_ERR_OOM;
+  return ST_ERR_CUDA;
+}
+
+#define ST_TRY(expr)                      \
+  do {                                    \
+    cudaError_t _e = (expr);              \
+    if (_e != cudaSuccess) return map_cuda(_e); \
+  } while (0)
+
+int partials_needed(const Geom &g) {
+  int a = stencil_blocks(g);
+  int b = time_blocks_for(g, PrecPlan{}, false);
+  int c = time_blocks_for(g, PrecPlan{}, true);
+  int r = a;
+  if (b > r) r = b;
+  if (c > r) r = c;
+  if (r < kStreamBlocks) r = kStreamBlocks;
+  return r;
+}
+
+Geom geom_of(const st_problem *p) {
+  Geom g{};
+  g.dim = p->dim;
+  g.mx = p->mx;
+  g.my = (p->dim == 1) ? 1 : p->my;
+  g.n = p->n;
+  g.m = (long long)g.mx * g.my;
+  g.N = g.m * g.n;
+  g.scheme = p->scheme;
+  g.tau = p->T / p->n;
+  g.theta = (p->scheme == ST_THETA) ? p->theta : 1.0;
+  return g;
+}
+
+size_t table_doubles(const Geom &g) {
+  const size_t faces = (size_t)g.my * (g.mx + 1) + (g.dim == 2 ? (size_t)(g.my + 1) * g.mx : 0);
+  const size_t spec = (size_t)g.mx + g.my + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
+  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2;  // L/2 complex per axis
+  return faces + spec + tw;
+}
+size_t table_floats(const Geom &g) {
+  const size_t spec = (size_t)g.mx + g.my + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
+  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2;
+  return spec + tw;
+}
+
+size_t workspace_bytes(const Geom &g, bool mixed) {
+  const size_t N = (size_t)g.N;
+  size_t b = 0;
+  b += 2 * N * sizeof(double);                             // V
+  b += 2 * N * (mixed ? sizeof(float) : sizeof(double));   // Z
+  b += 2 * N * sizeof(double);                             // D
+  b += N * sizeof(double);                                 // q
+  b += 2 * N * sizeof(double);                             // host staging
+  b += (size_t)partials_needed(g) * sizeof(double);
+  b += sizeof(State);
+  b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(double);  // grad faces
+  b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
+  return b;
+}
+
+// Build every table on the host (float64 with float32 copies) and upload them in one go.
+int build_tables(st_handle *h) {
+  const Geom &g = h->g;
+  const st_problem &p = h->prob;
+  const int mx = g.mx, my = g.my, n = g.n;
+  const double tau = g.tau;
+  const double hx = 1.0 / (mx + 1), hy = (g.dim == 2) ? 1.0 / (my + 1) : 1.0;
+  const double *A = p.a_nodal;
+  auto anode = [&](int J, int I) -> double {
+    if (!A) return 1.0;
+    return (g.dim == 1) ? A[I] : A[(long long)J * (mx + 2) + I];
+  };
+  const size_t nfx = (size_t)my * (mx + 1), nfy = (g.dim == 2) ? (size_t)(my + 1) * mx : 0;
+  std::vector<double> cx(nfx), cy(nfy);
+  for (int j = 0; j < my; ++j)
+    for (int i = 0; i <= mx; ++i)
+      cx[(size_t)j * (mx + 1) + i] = tau * 0.5 * (anode(j + 1, i) + anode(j + 1, i + 1)) / (hx * hx);
+  for (size_t j = 0; j < (g.dim == 2 ? (size_t)my + 1 : 0); ++j)
+    for (int i = 0; i < mx; ++i)
+      cy[j * mx + i] = tau * 0.5 * (anode((int)j, i + 1) + anode((int)j + 1, i + 1)) / (hy * hy);
+  // diagonal-averaged stiffness matrix (times tau): mean diagonal, mean x- and y-couplings
+  double dsum = 0.0;
+  for (int j = 0; j < my; ++j)
+    for (int i = 0; i < mx; ++i) {
+      double d = cx[(size_t)j * (mx + 1) + i] + cx[(size_t)j * (mx + 1) + i + 1];
+      if (g.dim == 2) d += cy[(size_t)j * mx + i] + cy[(size_t)(j + 1) * mx + i];
+      dsum += d;
+    }
+  const double dbar = dsum / (double)g.m;
+  double ex = 0.0, ey = 0.0;
+  if (mx > 1) {
+    double s = 0.0;
+    for (int j = 0; j < my; ++j)
+      for (int i = 1; i < mx; ++i) s += cx[(size_t)j * (mx + 1) + i];
+    ex = s / ((double)my * (mx - 1));
+  }
+  if (g.dim == 2 && my > 1) {
+    double s = 0.0;
+    for (int j = 1; j < my; ++j)
+      for (int i = 0; i < mx; ++i) s += cy[(size_t)j * mx + i];
+    ey = s / ((double)(my - 1) * mx);
+  }
+  const double PI = 3.14159265358979323846;
+  std::vector<double> mux(mx), muy(my), hk(n), ck(n), sk(n), lh(n), lht(n), sintab(2 * (n + 1));
+  for (int i = 0; i < mx; ++i) mux[i] = dbar - 2.0 * ex * std::cos((i + 1) * PI / (mx + 1));
+  for (int j = 0; j < my; ++j)
+    muy[j] = (g.dim == 2) ? -2.0 * ey * std::cos((j + 1) * PI / (my + 1)) : 0.0;
+  const double th = g.theta;
+  for (int k = 1; k <= n; ++k) {
+    const double x = k * PI / (n + 1);
+    const double sh = std::sin(0.5 * x);
+    hk[k - 1] = 2.0 * sh * sh;
+    ck[k - 1] = std::cos(x);
+    sk[k - 1] = std::sin(x);
+    lh[k - 1] = 2.0 * sh;
+    lht[k - 1] = std::sqrt(th * th + (1 - th) * (1 - th) + 2.0 * th * (1 - th) * std::cos(x));
+  }
+  const double sn = std::sqrt(2.0 / (n + 1));
+  for (int r = 0; r < 2 * (n + 1); ++r) sintab[r] = sn * std::sin(r * PI / (n + 1));
+  const int Lx = 2 * (mx + 1), Ly = 2 * (my + 1);
+  std::vector<double> twx(Lx), twy(Ly);
+  for (int j = 0; j < Lx / 2; ++j) {
+    twx[2 * j] = std::cos(2.0 * PI * j / Lx);
+    twx[2 * j + 1] = -std::sin(2.0 * PI * j / Lx);
+  }
+  for (int j = 0; j < Ly / 2; ++j) {
+    twy[2 * j] = std::cos(2.0 * PI * j / Ly);
+    twy[2 * j + 1] = -std::sin(2.0 * PI * j / Ly);
+  }
+  // layout: doubles [cx cy mux muy hk ck sk lh lht sintab twx twy] then floats [mux ... twy]
+  std::vector<double> hd;
+  hd.reserve(table_doubles(g));
+  auto app = [&](const std::vector<double> &v) {
+    size_t off = hd.size();
+    hd.insert(hd.end(), v.begin(), v.end());
+    return off;
+  };
+  const size_t o_cx = app(cx), o_cy = app(cy);
+  const size_t o_mux = app(mux), o_muy = app(muy), o_hk = app(hk), o_ck = app(ck), o_sk = app(sk),
+               o_lh = app(lh), o_lht = app(lht), o_sin = app(sintab), o_twx = app(twx),
+               o_twy = app(twy);
+  const size_t nd = hd.size();
+  std::vector<float> hf(nd - o_mux);
+  for (size_t i = o_mux; i < nd; ++i) hf[i - o_mux] = (float)hd[i];
+  const size_t bytes_d = nd * sizeof(double);
+  const size_t bytes = bytes_d + hf.size() * sizeof(float);
+  ST_TRY(cudaMalloc(&h->tables, bytes));
+  ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
+  ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), hf.size() * sizeof(float),
+                    cudaMemcpyHostToDevice));
+  const double *D = (const double *)h->tables;
+  const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
+  h->g.cx = D + o_cx;
+  h->g.cy = (g.dim == 2) ? D + o_cy : nullptr;
+  PrecPlan &pp = h->pp;
+  pp.Lx = Lx;
+  pp.Ly = Ly;
+  pp.twx_d = D + o_twx;
+  pp.twy_d = D + o_twy;
+  pp.twx_f = F + o_twx;
+  pp.twy_f = F + o_twy;
+  pp.spec_d = Spec<double>{D + o_mux, D + o_muy, D + o_hk, D + o_ck, D + o_sk, D + o_lh, D + o_lht,
+                           D + o_sin, p.prec, p.scheme, th};
+  pp.spec_f = Spec<float>{F + o_mux, F + o_muy, F + o_hk, F + o_ck, F + o_sk, F + o_lh, F + o_lht,
+                          F + o_sin, p.prec, p.scheme, (float)th};
+  return ST_OK;
+}
+
+void free_handle(st_handle *h) {
+  if (!h) return;
+  cudaFree(h->tables);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->V[i]);
+    cudaFree(h->Z[i]);
+    cudaFree(h->D[i]);
+  }
+  cudaFree(h->q);
+  cudaFree(h->partials);
+  cudaFree(h->S);
+  cudaFree(h->hbuf_in);
+  cudaFree(h->hbuf_out);
+  cudaFree(h->gfx);
+  cudaFree(h->gfy);
+  if (h->hS) cudaFreeHost(h->hS);
+  prof_free(h->prof);
+  delete h;
+}
+
+// ---------------------------------------------------------------- MINRES driver
+template <class Tz, class Tc>
+cudaError_t launch_iteration(st_handle *h, int k, double *x) {
+  const int c = (k - 1) & 1, o = k & 1;
+  const Geom &g = h->g;
+  cudaStream_t st = h->stream;
+  Tz *zc = (Tz *)h->Z[c];
+  Tz *zn = (Tz *)h->Z[o];
+  cudaError_t e;
+  e = launch_stencil<Tz>(g, SM_MINRES, zc, h->q, nullptr, h->S, h->partials, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_lanczos(g.N, h->q, h->V[c], h->V[o], h->S, st);
+  if (e != cudaSuccess) return e;
+  e = launch_prec<Tc, double, Tz>(g, h->pp, h->V[o], zn, h->S, TM_ITER, h->partials, st);
+  if (e != cudaSuccess) return e;
+  return launch_update<Tz>(g.N, zc, h->D[c], h->D[o], x, h->S, st);
+}
+
+int sync_state(st_handle *h) {
+  ST_TRY(cudaMemcpyAsync(h->hS, h->S, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+  ST_TRY(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+int push_state(st_handle *h) {
+  ST_TRY(cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, h->stream));
+  return ST_OK;
+}
+
+// Start a MINRES run whose right-hand side b is already in V[0]; x keeps its content.
+template <class Tz, class Tc>
+int minres_start(st_handle *h, double target, int maxit) {
+  const Geom &g = h->g;
+  ST_TRY(cudaMemsetAsync(h->D[0], 0, g.N * sizeof(double), h->stream));
+  ST_TRY(cudaMemsetAsync(h->D[1], 0, g.N * sizeof(double), h->stream));
+  ST_TRY(cudaMemsetAsync(h->V[1], 0, g.N * sizeof(double), h->stream));
+  State &s = *h->hS;
+  const double bn = s.bnorm2;
+  std::memset(&s, 0, sizeof(State));
+  s.bnorm2 = bn;
+  s.active = 1;
+  s.finish = 0;
+  s.target = target;
+  s.maxit = maxit;
+  int r = push_state(h);
+  if (r) return r;
+  ST_TRY((launch_prec<Tc, double, Tz>(g, h->pp, h->V[0], (Tz *)h->Z[0], h->S, TM_INIT,
+                                      h->partials, h->stream)));
+  return ST_OK;
+}
+
+// Run iterations until the device sets finish (or deactivates); returns with hS current.
+template <class Tz, class Tc>
+int minres_iterate(st_handle *h, double *x) {
+  int chunk = 4;
+  for (;;) {
+    const int k0 = h->hS->k;
+    for (int i = 1; i <= chunk; ++i) ST_TRY((launch_iteration<Tz, Tc>(h, k0 + i, x)));
+    int r = sync_state(h);
+    if (r) return r;
+    const State &s = *h->hS;
+    if (s.status != 0 || s.finish || !s.active) return ST_OK;
+    if (chunk < 16) chunk *= 2;
+  }
+}
+
+int true_residual(st_handle *h, const double *fH, const double *x, double *r_out, double *rho) {
+  ST_TRY(launch_stencil<double>(h->g, SM_RESID, x, r_out, fH, h->S, h->partials, 0, h->stream));
+  int e = sync_state(h);
+  if (e) return e;
+  const double bn = h->hS->bnorm2;
+  *rho = (bn > 0.0) ? std::sqrt(h->hS->rnorm2 / bn) : 0.0;
+  return ST_OK;
+}
+
+// b = Y f_H into V[0] and ||b||^2 into the device state (state otherwise cleared).
+int prepare_rhs(st_handle *h, const double *fH) {
+  cudaStream_t st = h->stream;
+  std::memset(h->hS, 0, sizeof(State));
+  int r = push_state(h);
+  if (r) return r;
+  ST_TRY(launch_flip(h->g, fH, h->V[0], st));
+  ST_TRY(launch_norm2(h->g.N, fH, h->S, h->partials, st));
+  return sync_state(h);
+}
+
+int finish_status(const State &s, bool converged) {
+  if (s.status != 0) return s.status;
+  return converged ? ST_OK : ST_ERR_NOT_CONVERGED;
+}
+
+// Plain float64 MINRES with the true-residual stopping rule.
+int solve_fp64(st_handle *h, const double *fH, double *x, double tol, int maxit, st_stats *stats) {
+  const Geom &g = h->g;
+  ST_TRY(cudaMemsetAsync(x, 0, g.N * sizeof(double), h->stream));
+  int r = prepare_rhs(h, fH);
+  if (r) return r;
+  if (h->hS->bnorm2 == 0.0) {
+    if (stats) stats->iterations = 0;
+    return ST_OK;
+  }
+  r = minres_start<double, double>(h, tol, maxit);
+  if (r) return r;
+  int checks = 0;
+  double rho = 1.0;
+  bool converged = false;
+  for (;;) {
+    r = minres_iterate<double, double>(h, x);
+    if (r) return r;
+    State s = *h->hS;
+    r = true_residual(h, fH, x, nullptr, &rho);
+    if (r) return r;
+    ++checks;
+    *h->hS = s;  // the residual kernel changed only rnorm2 / counters
+    if (s.status != 0) break;
+    if (rho <= tol || s.beta == 0.0) {
+      converged = true;
+      break;
+    }
+    if (s.k >= maxit) break;
+    // continue MINRES with a tighter estimate target
+    State &w = *h->hS;
+    w.target = w.target * tol / rho;
+    w.finish = 0;
+    w.active = 1;
+    w.rnorm2 = 0.0;
+    r = push_state(h);
+    if (r) return r;
+  }
+  if (stats) {
+    stats->iterations = h->hS->k;
+    stats->outer_steps = 1;
+    stats->true_checks = checks;
+    stats->est_rel_res = h->hS->est;
+    stats->true_rel_res = rho;
+  }
+  return finish_status(*h->hS, converged);
+}
+
+// Mixed precision: MINRES with the float32 preconditioner solves (Y T) d = r for the current
+// float64 residual r = Y f_H - Y T x, accumulating d into x; the float64 residual is then
+// recomputed (iterative refinement) until ||r||/||b|| <= tol.
+int solve_mixed(st_handle *h, const double *fH, double *x, double tol, int maxit,
+                st_stats *stats) {
+  const Geom &g = h->g;
+  ST_TRY(cudaMemsetAsync(x, 0, g.N * sizeof(double), h->stream));
+  int r = prepare_rhs(h, fH);
+  if (r) return r;
+  if (h->hS->bnorm2 == 0.0) return ST_OK;
+  const double bn2 = h->hS->bnorm2;
+  double rho = 1.0;
+  int total = 0, outer = 0, checks = 0;
+  bool converged = false;
+  double last_est = 1.0;
+  int status = 0;
+  while (total < maxit) {
+    ++outer;
+    const double target = std::max(0.5 * tol / rho, 1e-6);
+    h->hS->bnorm2 = bn2;
+    r = minres_start<float, float>(h, target, maxit - total);
+    if (r) return r;
+    r = minres_iterate<float, float>(h, x);
+    if (r) return r;
+    const State s = *h->hS;
+    total += s.k;
+    last_est = s.est;
+    status = s.status;
+    // r = Y f_H - Y T x written into V[0]: the right-hand side of the next refinement step
+    r = true_residual(h, fH, x, h->V[0], &rho);
+    if (r) return r;
+    ++checks;
+    if (rho <= tol) {
+      converged = true;
+      break;
+    }
+    if (status != 0 || s.k == 0) break;
+  }
+  if (stats) {
+    stats->iterations = total;
+    stats->outer_steps = outer;
+    stats->true_checks = checks;
+    stats->est_rel_res = last_est;
+    stats->true_rel_res = rho;
+  }
+  if (status != 0) return status;
+  return converged ? ST_OK : ST_ERR_NOT_CONVERGED;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------ C ABI
+extern "C" {
+
+int st_version(void) { return 1; }
+
+int st_profile_begin(st_handle *h, int capacity) {
+  if (!h || capacity < 1 || capacity > (1 << 20)) return ST_ERR_ARG;
+  ST_TRY(cudaSetDevice(h->device));
+  prof_free(h->prof);
+  Prof &p = h->prof;
+  std::memset(p.launches, 0, sizeof(p.launches));
+  p.ev = new (std::nothrow) cudaEvent_t[2 * (size_t)capacity];
+  p.cls = new (std::nothrow) int[capacity];
+  if (!p.ev || !p.cls) {
+    delete[] p.ev;
+    delete[] p.cls;
+    p.ev = nullptr;
+    p.cls = nullptr;
+    return ST_ERR_OOM;
+  }
+  for (int i = 0; i < 2 * capacity; ++i) {
+    cudaError_t e = cudaEventCreate(&p.ev[i]);
+    if (e != cudaSuccess) {
+      p.cap = i / 2;
+      prof_free(p);
+      return map_cuda(e);
+    }
+  }
+  p.cap = capacity;
+  p.used = 0;
+  p.on = 1;
+  return ST_OK;
+}
+
+int st_profile_end(st_handle *h, st_kernel_time *out, int nclasses) {
+  if (!h || !out || nclasses < 1) return ST_ERR_ARG;
+  ST_TRY(cudaSetDevice(h->device));
+  Prof &p = h->prof;
+  if (!p.ev) return ST_ERR_ARG;
+  ST_TRY(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < nclasses; ++c) out[c] = st_kernel_time{0, 0, 0.0};
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) return map_cuda(e);
+    const int c = p.cls[i];
+    if (c < nclasses) {
+      out[c].timed += 1;
+      out[c].ms += ms;
+    }
+  }
+  for (int c = 0; c < nclasses && c < KC_COUNT; ++c) out[c].launches = (int)p.launches[c];
+  prof_free(p);
+  return ST_OK;
+}
+
+const char *st_kernel_class_name(int c) {
+  static const char *names[KC_COUNT] = {"stencil", "lanczos", "dst_x", "dst_y",
+                                        "time_dst_scale", "update", "residual", "aux"};
+  return (c >= 0 && c < KC_COUNT) ? names[c] : "unknown";
+}
+
+const char *st_strerror(int code) {
+  switch (code) {
+    case ST_OK: return "ok";
+    case ST_ERR_ARG: return "invalid argument";
+    case ST_ERR_CUDA: return "CUDA error";
+    case ST_ERR_NOT_CONVERGED: return "not converged within maxit";
+    case ST_ERR_BREAKDOWN: return "breakdown (non-positive <v, P^-1 v> or non-finite scalar)";
+    case ST_ERR_TIMEOUT: return "device wait timed out";
+    case ST_ERR_OOM: return "out of memory";
+    default: return "unknown status";
+  }
+}
+
+int st_workspace_bytes(const st_problem *prob, size_t *bytes) {
+  if (!bytes) return ST_ERR_ARG;
+  int r = check_problem(prob);
+  if (r) return r;
+  Geom g = geom_of(prob);
+  *bytes = workspace_bytes(g, prob->precision == ST_MIXED);
+  return ST_OK;
+}
+
+int st_setup(const st_problem *prob, st_handle **out) {
+  if (!out) return ST_ERR_ARG;
+  *out = nullptr;
+  int r = check_problem(prob);
+  if (r) return r;
+  st_handle *h = new (std::nothrow) st_handle();
+  if (!h) return ST_ERR_OOM;
+  std::memset(h, 0, sizeof(st_handle));
+  h->prob = *prob;
+  h->stream = (cudaStream_t)prob->stream;
+  h->mixed = (prob->precision == ST_MIXED);
+  h->g = geom_of(prob);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return ST_ERR_CUDA;
+  }
+  const Geom g = h->g;
+  const size_t N = (size_t)g.N;
+  auto fail = [&](int code) {
+    h->prob.a_nodal = nullptr;
+    free_handle(h);
+    return code;
+  };
+  r = build_tables(h);
+  if (r) return fail(r);
+  const size_t zsz = h->mixed ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&h->V[i], N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->Z[i], N * zsz);
+    if (e == cudaSuccess) e = cudaMalloc(&h->D[i], N * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->q, N * sizeof(double));
+  h->partials_len = partials_needed(g);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->partials_len * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->S, sizeof(State));
+  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_in, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_out, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->gfx, (size_t)g.my * (g.mx + 1) * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&h->gfy, ((size_t)g.my + 1) * g.mx * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hS, sizeof(State));
+  if (e == cudaSuccess) e = cudaMemset(h->S, 0, sizeof(State));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(map_cuda(e));
+  std::memset(h->hS, 0, sizeof(State));
+  h->prob.a_nodal = nullptr;
+  *out = h;
+  return ST_OK;
+}
+
+void st_destroy(st_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  free_handle(h);
+}
+
+int st_assemble_rhs(st_handle *h, const double *f_dev, const double *u0_dev,
+                    const double *uprev_dev, const double *extra_dev, double *fH_dev) {
+  if (!h || !f_dev || !u0_dev || !fH_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY(launch_rhs(h->g, f_dev, u0_dev, uprev_dev, extra_dev, fH_dev, h->stream));
+  return ST_OK;
+}
+
+int st_apply_op(st_handle *h, const double *v_dev, double *y_dev) {
+  if (!h || !v_dev || !y_dev || v_dev == y_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY(launch_stencil<double>(h->g, SM_APPLY, v_dev, y_dev, nullptr, h->S, h->partials, 0,
+                                h->stream));
+  return ST_OK;
+}
+
+int st_apply_prec(st_handle *h, const double *v_dev, double *z_dev) {
+  if (!h || !v_dev || !z_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY((launch_prec<double, double, double>(h->g, h->pp, v_dev, z_dev, h->S, TM_NONE,
+                                              h->partials, h->stream)));
+  return ST_OK;
+}
+
+int st_apply_prec_f32(st_handle *h, const double *v_dev, float *z_dev) {
+  if (!h || !v_dev || !z_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY((launch_prec<float, double, float>(h->g, h->pp, v_dev, z_dev, h->S, TM_NONE,
+                                            h->partials, h->stream)));
+  return ST_OK;
+}
+
+int st_solve(st_handle *h, const double *fH_dev, double *u_dev, double tol, int maxit,
+             st_stats *stats) {
+  if (!h || !fH_dev || !u_dev || fH_dev == u_dev || !(tol >= 0.0) || maxit < 1) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  const double t0 = now_s();
+  st_stats local{};
+  int r = h->mixed ? solve_mixed(h, fH_dev, u_dev, tol, maxit, &local)
+                   : solve_fp64(h, fH_dev, u_dev, tol, maxit, &local);
+  if (r != ST_ERR_CUDA && r != ST_ERR_OOM) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) r = map_cuda(e);
+  }
+  local.status = r;
+  local.seconds = now_s() - t0;
+  if (stats) *stats = local;
+  return r;
+}
+
+int st_solve_host(st_handle *h, const double *fH_host, double *u_host, double tol, int maxit,
+                  st_stats *stats) {
+  if (!h || !fH_host || !u_host) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  const double t0 = now_s();
+  const size_t bytes = (size_t)h->g.N * sizeof(double);
+  ST_TRY(cudaMemcpyAsync(h->hbuf_in, fH_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  st_stats local{};
+  int r = st_solve(h, h->hbuf_in, h->hbuf_out, tol, maxit, &local);
+  if (r == ST_ERR_CUDA || r == ST_ERR_OOM) return r;
+  cudaError_t e = cudaMemcpyAsync(u_host, h->hbuf_out, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) r = map_cuda(e);
+  local.status = r;
+  local.seconds = now_s() - t0;
+  if (stats) *stats = local;
+  return r;
+}
+
+int st_solve_transpose(st_handle *h, const double *g_dev, double *lam_dev, double tol, int maxit,
+                       st_stats *stats) {
+  if (!h || !g_dev || !lam_dev || g_dev == lam_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  // (Y T) mu = g is st_solve with f_H = Y g; then lam = Y mu.
+  ST_TRY(launch_flip(h->g, g_dev, h->hbuf_in, h->stream));
+  int r = st_solve(h, h->hbuf_in, lam_dev, tol, maxit, stats);
+  if (r == ST_ERR_CUDA || r == ST_ERR_OOM) return r;
+  cudaError_t e = launch_flip(h->g, lam_dev, lam_dev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  return r;
+}
+
+int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
+              double *grad_dev) {
+  if (!h || !lam_dev || !u_dev || !u0_dev || !grad_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY(launch_grad_a(h->g, lam_dev, u_dev, u0_dev, h->gfx, h->gfy, grad_dev, h->stream));
+  return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,521 @@
+// Preconditioner kernels: z = P^-1 v by the three steps of Sec. 3.1.1,
+//   1. v~ = (S_n (x) U_m^T) v,  2. z~ = diag(1/p) v~,  3. z = (S_n (x) U_m) z~,
+// with U_m = S_my (x) S_mx (uniform grid, x fastest) and S the orthonormal DST-I, which is
+// symmetric and involutory, so the forward and inverse transforms are the same kernels.
+//
+// Spatial DST-I (lengths mx, my with mx+1, my+1 powers of two): two real lines a, b are packed
+// into one complex sequence, odd-extended to length L = 2(len+1) and transformed by a radix-2
+// FFT in shared memory.  The DFT of the odd extension of a real line x is -2i sum_j x_j
+// sin(pi j k/(len+1)), so for z = a + i b: DST(a)_k = -Im Z_k / sqrt(L), DST(b)_k = Re Z_k /
+// sqrt(L) (orthonormal scaling sqrt(2/(len+1)) folded in).
+//
+// Time DST-I (any n): a dense contraction with S_n over the time axis for a tile of spatial
+// columns held in shared memory, halved by the symmetry S_{k,n+1-t} = (-1)^{k+1} S_{k,t}:
+// odd k use U_t = x_t + x_{n+1-t}, even k use D_t = x_t - x_{n+1-t}.  Between the forward and
+// inverse time transforms each entry is scaled by 1/p_kj, the eigenvalue of P in the transformed
+// basis (Sec. 3.1.1 for theta, Sec. 4 for BDF2, Sec. 3.1.4 for P_theta), and the kernel
+// accumulates <v, P^-1 v> = sum v~^2 / p for MINRES.
+#include <math.h>
+
+#include "st_internal.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int kNT = 256;
+
+template <class T>
+struct C2 {
+  T x, y;
+};
+
+template <class T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  C2<T> r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
+// Inside a MINRES iteration only the first kernel (the stencil) looks at `finish`; it clears
+// `active` so that the rest of that iteration is skipped.  The preconditioner kernels check
+// `active` alone, so an iteration whose time kernel raises `finish` still completes z_{k+1}
+// (needed if the stopping rule later decides to continue).
+__device__ __forceinline__ bool gate_closed(const State *S) {
+  return S != nullptr && !S->active;
+}
+
+// ------------------------------------------------------------------------------ spatial DST
+// XL = true: lines are rows (contiguous, line l starts at l*len).
+// XL = false: lines are columns of the (my x mx) planes: line l = k*mx + i starts at k*m + i and
+// its elements are mx apart.
+template <class Tc, class Tin, class Tout, bool XL>
+__global__ void __launch_bounds__(kNT)
+    k_dst_space(const Tin *in, Tout *out, int len, int logL,
+                long long nlines, int mx, long long m, const Tc *__restrict__ tw, int PB,
+                const State *S) {
+  if (gate_closed(S)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = 1 << logL;
+  const int half = L >> 1;
+  C2<Tc> *tws = reinterpret_cast<C2<Tc> *>(smem_raw);
+  C2<Tc> *zb = tws + half;
+  Tc *zr = reinterpret_cast<Tc *>(zb);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < half; e += kNT) {
+    tws[e].x = tw[2 * e];
+    tws[e].y = tw[2 * e + 1];
+  }
+  const long long line0 = (long long)blockIdx.x * 2 * PB;
+  const int nl = (int)min((long long)2 * PB, nlines - line0);  // lines in this block
+  const int shift = 32 - logL;
+  // zero the positions that stay zero (0 and len+1) and the whole of any absent line
+  for (int pp = tid; pp < PB; pp += kNT) {
+    zb[pp * L + (__brev(0u) >> shift)] = C2<Tc>{Tc(0), Tc(0)};
+    zb[pp * L + (__brev((unsigned)(len + 1)) >> shift)] = C2<Tc>{Tc(0), Tc(0)};
+  }
+  if (nl < 2 * PB) {
+    for (int idx = tid; idx < (2 * PB - nl) * len; idx += kNT) {
+      const int lb = nl + idx / len, e = idx % len;
+      const int pp = lb >> 1, comp = lb & 1;
+      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = Tc(0);
+      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = Tc(0);
+    }
+  }
+  // load (bit-reversed positions for the in-place decimation-in-time FFT)
+  if (XL) {
+    for (int idx = tid; idx < nl * len; idx += kNT) {
+      const int lb = idx / len, e = idx - lb * len;
+      const Tc v = (Tc)in[(line0 + lb) * len + e];
+      const int pp = lb >> 1, comp = lb & 1;
+      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = v;
+      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = -v;
+    }
+  } else {
+    for (int idx = tid; idx < nl * len; idx += kNT) {
+      const int e = idx / nl, lb = idx - e * nl;
+      const long long l = line0 + lb;
+      const long long k = l / mx, i = l - k * mx;
+      const Tc v = (Tc)in[k * m + (long long)e * mx + i];
+      const int pp = lb >> 1, comp = lb & 1;
+      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = v;
+      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = -v;
+    }
+  }
+  // radix-2 decimation-in-time stages
+  for (int s = 1; s <= logL; ++s) {
+    __syncthreads();
+    const int hs = 1 << (s - 1);
+    const int tws_stride = L >> s;
+    for (int b = tid; b < PB * half; b += kNT) {
+      const int pp = b >> (logL - 1);
+      const int bb = b & (half - 1);
+      const int pos = bb & (hs - 1);
+      const int i0 = ((bb >> (s - 1)) << s) + pos;
+      const int i1 = i0 + hs;
+      C2<Tc> *zp = zb + pp * L;
+      const C2<Tc> w = tws[pos * tws_stride];
+      const C2<Tc> a = zp[i0];
+      const C2<Tc> t = cmul(w, zp[i1]);
+      zp[i0] = C2<Tc>{a.x + t.x, a.y + t.y};
+      zp[i1] = C2<Tc>{a.x - t.x, a.y - t.y};
+    }
+  }
+  __syncthreads();
+  const Tc sc = (Tc)(1.0 / sqrt((double)L));
+  if (XL) {
+    for (int idx = tid; idx < nl * len; idx += kNT) {
+      const int lb = idx / len, e = idx - lb * len;
+      const C2<Tc> Z = zb[(lb >> 1) * L + e + 1];
+      const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
+      out[(line0 + lb) * len + e] = (Tout)v;
+    }
+  } else {
+    for (int idx = tid; idx < nl * len; idx += kNT) {
+      const int e = idx / nl, lb = idx - e * nl;
+      const long long l = line0 + lb;
+      const long long k = l / mx, i = l - k * mx;
+      const C2<Tc> Z = zb[(lb >> 1) * L + e + 1];
+      const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
+      out[k * m + (long long)e * mx + i] = (Tout)v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ time DST
+// Dense folded S_n contraction on a tile X[n][J] in shared memory: Y = S_n X.
+// X is folded in place first (rows t-1 <- U_t, n-t <- D_t).  Thread tiles of KT output rows of
+// one parity class by JT columns.
+template <class Tc, int KT, int JT>
+__device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
+  const int tid = threadIdx.x;
+  const int h = n >> 1;
+  for (int idx = tid; idx < h * J; idx += kNT) {
+    const int t = idx / J, c = idx - t * J;
+    const Tc a = X[t * J + c], b = X[(n - 1 - t) * J + c];
+    X[t * J + c] = a + b;
+    X[(n - 1 - t) * J + c] = a - b;
+  }
+  __syncthreads();
+  const int P2 = 2 * (n + 1);
+  const int nodd = (n + 1) >> 1, neven = n >> 1;
+  const int JG = J / JT;
+  const int todd = ((nodd + KT - 1) / KT) * JG;
+  const int tall = todd + ((neven + KT - 1) / KT) * JG;
+  const bool nodd_mid = (n & 1);
+  const int tm = (n + 1) >> 1;  // middle index (1-based) when n is odd
+  for (int tile = tid; tile < tall; tile += kNT) {
+    const bool odd = tile < todd;
+    const int tt = odd ? tile : tile - todd;
+    const int rg = tt / JG, jg = tt - rg * JG;
+    const int cnt = odd ? nodd : neven;
+    int kk[KT], ix[KT];
+#pragma unroll
+    for (int i = 0; i < KT; ++i) {
+      int r = rg * KT + i;
+      if (r >= cnt) r = cnt - 1;  // duplicate a valid row; its result is not stored
+      kk[i] = odd ? 2 * r + 1 : 2 * r + 2;
+      ix[i] = 0;
+    }
+    Tc acc[KT][JT];
+#pragma unroll
+    for (int i = 0; i < KT; ++i)
+#pragma unroll
+      for (int c = 0; c < JT; ++c) acc[i][c] = Tc(0);
+    const Tc *Fb = X + jg * JT;
+    for (int t = 1; t <= h; ++t) {
+      const Tc *F = Fb + (odd ? (t - 1) : (n - t)) * J;
+      Tc f[JT];
+#pragma unroll
+      for (int c = 0; c < JT; ++c) f[c] = F[c];
+#pragma unroll
+      for (int i = 0; i < KT; ++i) {
+        int q = ix[i] + kk[i];
+        q = (q >= P2) ? q - P2 : q;
+        ix[i] = q;
+        const Tc sv = sintab[q];
+#pragma unroll
+        for (int c = 0; c < JT; ++c) acc[i][c] = fma(sv, f[c], acc[i][c]);
+      }
+    }
+    if (odd && nodd_mid) {
+      const Tc *F = Fb + (tm - 1) * J;
+#pragma unroll
+      for (int i = 0; i < KT; ++i) {
+        const Tc sv = sintab[(int)(((long long)kk[i] * tm) % P2)];
+#pragma unroll
+        for (int c = 0; c < JT; ++c) acc[i][c] = fma(sv, F[c], acc[i][c]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KT; ++i) {
+      if (rg * KT + i < cnt) {
+        Tc *Yr = Y + (kk[i] - 1) * J + jg * JT;
+#pragma unroll
+        for (int c = 0; c < JT; ++c) Yr[c] = acc[i][c];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// 1/p for the eigenvalue of the preconditioner at time frequency k (1-based) and tau*mu.
+template <class T>
+__device__ __forceinline__ T inv_symbol(const Spec<T> &sp, int k, T tmu) {
+  const T hk = sp.hk[k - 1], ck = sp.ck[k - 1], sk = sp.sk[k - 1];
+  if (sp.prec == ST_PREC_PTHETA) {
+    // lam_H = sqrt(2 - 2cos x) = 2 sin(x/2), lam_Htheta = sqrt(th^2 + (1-th)^2 + 2 th(1-th) cos x)
+    return T(1) / (sp.lh[k - 1] + sp.lht[k - 1] * tmu);
+  }
+  T re, im;
+  if (sp.scheme == ST_THETA) {
+    // |a0 + a1 e^{ix}|, a0 = 1 + th tmu, a1 = -1 + (1-th) tmu;  a0 + a1 cos x = (1 - cos x) +
+    // tmu (th + (1-th) cos x)
+    re = hk + tmu * (sp.theta + (T(1) - sp.theta) * ck);
+    im = (T(-1) + (T(1) - sp.theta) * tmu) * sk;
+  } else {
+    // |a0 + a1 e^{ix} + a2 e^{2ix}|, a0 = 3/2 + tmu, a1 = -2, a2 = 1/2:
+    // re = (1 - cos x)^2 + tmu, im = -sin x (2 - cos x)
+    re = hk * hk + tmu;
+    im = -sk * (T(1) + hk);
+  }
+  return rsq(re * re + im * im);
+}
+
+__device__ void minres_init_scalars(State *S, double E) {
+  if (!(E >= 0.0) || !isfinite(E)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    return;
+  }
+  const double b1 = sqrt(E);
+  S->beta1 = b1;
+  S->beta = b1;
+  S->beta_prev = 1.0;
+  S->inv_beta = (b1 > 0.0) ? 1.0 / b1 : 0.0;
+  S->eta = b1;
+  S->c1 = 1.0;
+  S->s1 = 0.0;
+  S->c2 = 1.0;
+  S->s2 = 0.0;
+  S->k = 0;
+  S->est = 1.0;
+  if (b1 == 0.0) S->finish = 1;
+}
+
+// One Givens step of MINRES (Paige-Saunders) once beta_{k+1}^2 = E is known.
+__device__ void minres_givens(State *S, double E) {
+  if (!(E >= 0.0) || !isfinite(E)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    S->xc = 0.0;
+    S->dz = S->d1 = S->d2 = 0.0;
+    return;
+  }
+  const double bnext = sqrt(E);
+  const int k = S->k + 1;
+  const double off = (S->k > 0) ? S->beta : 0.0;
+  const double eps = S->s2 * off;
+  const double dbar = S->c2 * off;
+  const double delta = S->c1 * dbar + S->s1 * S->alpha;
+  const double gbar = -S->s1 * dbar + S->c1 * S->alpha;
+  const double rho = hypot(gbar, bnext);
+  if (!(rho > 0.0) || !isfinite(rho) || !isfinite(S->alpha)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    S->xc = 0.0;
+    S->dz = S->d1 = S->d2 = 0.0;
+    return;
+  }
+  const double c = gbar / rho, s = bnext / rho;
+  S->dz = 1.0 / (S->beta * rho);
+  S->d1 = -delta / rho;
+  S->d2 = -eps / rho;
+  S->xc = c * S->eta;
+  S->eta = -s * S->eta;
+  S->c2 = S->c1;
+  S->s2 = S->s1;
+  S->c1 = c;
+  S->s1 = s;
+  S->beta_prev = S->beta;
+  S->beta = bnext;
+  S->inv_beta = (bnext > 0.0) ? 1.0 / bnext : 0.0;
+  S->k = k;
+  S->est = fabs(S->eta) / S->beta1;
+  if (S->est <= S->target || bnext == 0.0 || k >= S->maxit) S->finish = 1;
+}
+
+template <class Tc, int KT, int JT>
+__global__ void __launch_bounds__(kNT)
+    k_time(Tc *data, int n, long long m, int mx, int J, Spec<Tc> sp, State *S,
+           int tmode, int tkind, double *__restrict__ partials, int gated) {
+  __shared__ double red[32];
+  if (gated && gate_closed(S)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc *X = reinterpret_cast<Tc *>(smem_raw);
+  Tc *Y = X + (size_t)n * J;
+  Tc *sintab = Y + (size_t)n * J;
+  Tc *tmu = sintab + 2 * (n + 1);
+  const int tid = threadIdx.x;
+  const long long j0 = (long long)blockIdx.x * J;
+  const int Je = (int)min((long long)J, m - j0);
+  for (int r = tid; r < 2 * (n + 1); r += kNT) sintab[r] = sp.sintab[r];
+  for (int c = tid; c < J; c += kNT) {
+    Tc v = Tc(0);
+    if (c < Je) {
+      const long long j = j0 + c;
+      const long long jy = j / mx, jx = j - jy * mx;
+      v = sp.mux[jx] + sp.muy[jy];
+    }
+    tmu[c] = v;
+  }
+  for (int idx = tid; idx < n * J; idx += kNT) {
+    const int t = idx / J, c = idx - t * J;
+    X[idx] = (c < Je) ? data[(long long)t * m + j0 + c] : Tc(0);
+  }
+  __syncthreads();
+  time_dst_tile<Tc, KT, JT>(X, Y, sintab, n, J);
+  double e = 0.0;
+  if (tkind == 0) {
+    // scale by 1/p and accumulate <v, P^-1 v>
+    for (int idx = tid; idx < n * J; idx += kNT) {
+      const int kr = idx / J, c = idx - kr * J;
+      const Tc ip = inv_symbol(sp, kr + 1, tmu[c]);
+      const Tc y = Y[idx];
+      if (c < Je) e += (double)y * (double)y * (double)ip;
+      Y[idx] = y * ip;
+    }
+    __syncthreads();
+    time_dst_tile<Tc, KT, JT>(Y, X, sintab, n, J);
+    for (int idx = tid; idx < n * J; idx += kNT) {
+      const int t = idx / J, c = idx - t * J;
+      if (c < Je) data[(long long)t * m + j0 + c] = X[idx];
+    }
+  } else {
+    for (int idx = tid; idx < n * J; idx += kNT) {
+      const int t = idx / J, c = idx - t * J;
+      if (c < Je) data[(long long)t * m + j0 + c] = Y[idx];
+    }
+  }
+  if (tmode != TM_NONE) {
+    double tot;
+    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                               &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT)
+        minres_init_scalars(S, tot);
+      else
+        minres_givens(S, tot);
+    }
+  }
+}
+
+template <class Tc>
+size_t dst_smem(int L, int PB) {
+  return (size_t)(L / 2) * 2 * sizeof(Tc) + (size_t)PB * L * 2 * sizeof(Tc);
+}
+
+template <class Tc>
+int dst_pairs(int L) {
+  int PB = (int)(65536 / ((size_t)L * 2 * sizeof(Tc)));
+  if (PB < 1) PB = 1;
+  if (PB > 16) PB = 16;
+  return PB;
+}
+
+template <class Tc>
+size_t time_smem(int n, int J) {
+  return ((size_t)2 * n * J + 2 * (n + 1) + J) * sizeof(Tc);
+}
+
+template <class Tc, class Tin, class Tout, bool XL>
+cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
+                       long long m, const Tc *tw, const State *S, cudaStream_t st) {
+  const int PB = dst_pairs<Tc>(L);
+  const size_t sm = dst_smem<Tc>(L, PB);
+  int logL = 0;
+  while ((1 << logL) < L) ++logL;
+  const long long blocks = (nlines + 2 * PB - 1) / (2 * PB);
+  auto kern = k_dst_space<Tc, Tin, Tout, XL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  prof_begin(XL ? KC_DSTX : KC_DSTY, st);
+  kern<<<(unsigned)blocks, kNT, sm, st>>>(in, out, len, logL, nlines, mx, m, tw, PB, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+template <class Tc>
+struct TimeTile;
+template <>
+struct TimeTile<double> {
+  static constexpr int KT = 4, JT = 2;
+};
+template <>
+struct TimeTile<float> {
+  static constexpr int KT = 8, JT = 4;
+};
+
+template <class Tc>
+int time_J(int n) {
+  // columns per block: two n x J tiles within ~128 KB (at most ~200 KB for long time axes),
+  // J a multiple of the thread-tile width, preferably of 16 for full 128-byte rows
+  const int JT = TimeTile<Tc>::JT;
+  const size_t per_col = (2 * (size_t)n + 1) * sizeof(Tc);
+  int J = (int)((128 * 1024) / per_col);
+  if (J >= 16) {
+    J = (J / 16) * 16;
+    if (J > 64) J = 64;
+  } else {
+    J = (int)((200 * 1024 - 2 * (size_t)(n + 1) * sizeof(Tc)) / per_col);
+    if (J > 16) J = 16;
+  }
+  J = (J / JT) * JT;
+  if (J < JT) J = JT;
+  return J;
+}
+
+template <class Tc>
+cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, int tmode,
+                        int tkind, double *partials, int gated, cudaStream_t st) {
+  const int J = time_J<Tc>(g.n);
+  const size_t sm = time_smem<Tc>(g.n, J);
+  const long long blocks = (g.m + J - 1) / J;
+  constexpr int KT = TimeTile<Tc>::KT, JT = TimeTile<Tc>::JT;
+  auto kern = k_time<Tc, KT, JT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  prof_begin(KC_TIME, st);
+  kern<<<(unsigned)blocks, kNT, sm, st>>>(data, g.n, g.m, g.mx, J, sp, S, tmode, tkind, partials,
+                                          gated);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int time_blocks_for(const Geom &g, const PrecPlan &, bool fp32) {
+  const int J = fp32 ? time_J<float>(g.n) : time_J<double>(g.n);
+  return (int)((g.m + J - 1) / J);
+}
+
+template <class Tc>
+static const Tc *tw_of(const PrecPlan &pp, bool x);
+template <>
+const double *tw_of<double>(const PrecPlan &pp, bool x) {
+  return x ? pp.twx_d : pp.twy_d;
+}
+template <>
+const float *tw_of<float>(const PrecPlan &pp, bool x) {
+  return x ? pp.twx_f : pp.twy_f;
+}
+template <class Tc>
+static const Spec<Tc> &spec_of(const PrecPlan &pp);
+template <>
+const Spec<double> &spec_of<double>(const PrecPlan &pp) {
+  return pp.spec_d;
+}
+template <>
+const Spec<float> &spec_of<float>(const PrecPlan &pp) {
+  return pp.spec_f;
+}
+
+template <class Tc, class Tin, class Tout>
+cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
+                        int tmode, double *partials, cudaStream_t st) {
+  static_assert(sizeof(Tc) == sizeof(Tout), "in-place stages need Tout == Tc");
+  const State *gate = (tmode == TM_ITER) ? S : nullptr;
+  cudaError_t e;
+  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
+  e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), gate,
+                                      st);
+  if (e != cudaSuccess) return e;
+  if (g.dim == 2) {
+    e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
+                                          gate, st);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials,
+                      tmode == TM_ITER, st);
+  if (e != cudaSuccess) return e;
+  if (g.dim == 2) {
+    e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
+                                          gate, st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_dst<Tc, Tout, Tout, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true),
+                                          gate, st);
+}
+
+template cudaError_t launch_prec<double, double, double>(const Geom &, const PrecPlan &,
+                                                         const double *, double *, State *, int,
+                                                         double *, cudaStream_t);
+template cudaError_t launch_prec<float, double, float>(const Geom &, const PrecPlan &,
+                                                       const double *, float *, State *, int,
+                                                       double *, cudaStream_t);
+
+}  // namespace st

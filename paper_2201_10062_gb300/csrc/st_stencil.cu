@@ -1,0 +1,385 @@
+// Space-time stencil kernels: the flipped all-at-once operator Y T (Sec. 1, eq. theta and
+// eq. main_system; Sec. 4, eq. matrix_gen / main_system_gem_sym), the all-at-once right-hand side
+// and the face-coefficient gradient used by the adjoint.
+//
+// T is never stored.  Block row k of T v is A0 v_k + A1 v_{k-1} (+ A2 v_{k-2} for BDF2) with
+//   theta: A0 = I + theta tau K, A1 = -I + (1-theta) tau K,
+//   BDF2:  A0 = 3/2 I + tau K,   A1 = -2 I,  A2 = 1/2 I,
+// and Y only reverses the block order, so row k of T v is written to block n-1-k.
+// One thread owns one spatial node and walks a chunk of consecutive time levels (and their
+// mirror images), carrying neighbouring planes in registers so that each plane of v is read once.
+#include "st_internal.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int kBX2 = 32, kBY2 = 8;   // 2D block: 32 x 8 nodes
+constexpr int kBX1 = 256;            // 1D block: 256 nodes (all block reductions assume 256 threads)
+constexpr int kNT = 256;
+
+struct Tile {
+  int kc, nchunk, gx, gy;
+};
+
+Tile tile_for(const Geom &g) {
+  Tile t;
+  if (g.dim == 1) {
+    t.gx = (g.mx + kBX1 - 1) / kBX1;
+    t.gy = 1;
+  } else {
+    t.gx = (g.mx + kBX2 - 1) / kBX2;
+    t.gy = (g.my + kBY2 - 1) / kBY2;
+  }
+  // chunks cover the first ceil(n/2) planes (each thread also does their mirror images)
+  const int half = (g.n + 1) / 2;
+  const long long tiles = (long long)t.gx * t.gy;
+  const long long target = 152LL * 8;  // 8 resident 256-thread blocks on each of 152 SMs
+  long long nchunk = (target + tiles - 1) / tiles;
+  if (nchunk < 1) nchunk = 1;
+  if (nchunk > half) nchunk = half;
+  t.kc = (int)((half + nchunk - 1) / nchunk);
+  t.nchunk = (half + t.kc - 1) / t.kc;
+  return t;
+}
+
+template <class Tz>
+__device__ __forceinline__ double ld(const Tz *p) {
+  return (double)__ldg(p);
+}
+
+// tau*K applied at node p of plane base (zero Dirichlet values outside the grid).
+template <class Tz>
+__device__ __forceinline__ double tauK(const Tz *__restrict__ base, long long p, int i, int j,
+                                       int mx, int my, int dim, double cw, double ce, double cs,
+                                       double cn, double c) {
+  double r = (cw + ce + cs + cn) * c;
+  if (i > 0) r -= cw * ld(base + p - 1);
+  if (i < mx - 1) r -= ce * ld(base + p + 1);
+  if (dim == 2) {
+    if (j > 0) r -= cs * ld(base + p - mx);
+    if (j < my - 1) r -= cn * ld(base + p + mx);
+  }
+  return r;
+}
+
+// The dot products MINRES needs pair the two halves of the time axis: row k of T z lands in
+// block n-1-k of Y T z, so <Y T z, z> = sum_k <(T z)_k, z_{n-1-k}>.  Each thread therefore walks
+// a chunk of planes k upwards (side A) and the mirrored planes n-1-k downwards (side B) in lock
+// step; the centre value of each side is exactly the z the other side's output is paired with,
+// so the dot costs no extra loads.  Chunks cover the first ceil(n/2) planes; for odd n the middle
+// plane is its own mirror and is done once.
+template <class Tz, int MODE>
+__global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ z,
+                                                 double *__restrict__ out,
+                                                 const double *__restrict__ fH, State *S,
+                                                 double *__restrict__ partials, int kc) {
+  __shared__ double red[32];
+  if (MODE == SM_MINRES) {
+    if (!S->active) return;
+    if (S->finish) {
+      if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && flat_tid() == 0) S->active = 0;
+      return;
+    }
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
+  const long long m = g.m;
+  const bool valid = (i < mx) && (j < my);
+  const int half = (n + 1) >> 1;
+  const int k0 = blockIdx.z * kc;
+  const int k1 = min(half, k0 + kc);
+  const double s = (MODE == SM_MINRES) ? S->inv_beta : 1.0;
+  double acc = 0.0;
+  if (valid) {
+    const long long p = (long long)j * mx + i;
+    const double cw = g.cx[(long long)j * (mx + 1) + i];
+    const double ce = g.cx[(long long)j * (mx + 1) + i + 1];
+    double cs = 0.0, cn = 0.0;
+    if (dim == 2) {
+      cs = g.cy[(long long)j * mx + i];
+      cn = g.cy[(long long)(j + 1) * mx + i];
+    }
+    const double th = g.theta, omth = 1.0 - g.theta;
+    auto center = [&](int k) -> double { return ld(z + (long long)k * m + p); };
+    auto stiff = [&](int k, double c) -> double {
+      return tauK(z + (long long)k * m, p, i, j, mx, my, dim, cw, ce, cs, cn, c);
+    };
+    // side A (ascending) carries plane kA-1 (and kA-2); side B (descending) carries plane kB and
+    // the planes below it
+    double a1 = 0.0, aK1 = 0.0, a2 = 0.0;
+    double b0 = 0.0, bK0 = 0.0, b1 = 0.0;
+    const bool theta = (g.scheme == ST_THETA);
+    if (k0 > 0) {
+      a1 = center(k0 - 1);
+      if (theta) aK1 = stiff(k0 - 1, a1);
+    }
+    if (!theta && k0 > 1) a2 = center(k0 - 2);
+    {
+      const int kb = n - 1 - k0;
+      b0 = center(kb);
+      if (theta) bK0 = stiff(kb, b0);
+      else if (kb > 0) b1 = center(kb - 1);
+    }
+    for (int kA = k0; kA < k1; ++kA) {
+      const int kB = n - 1 - kA;
+      const double cA = center(kA);
+      const double KA = stiff(kA, cA);
+      double yA;
+      if (theta) {
+        yA = (cA - a1) + th * KA + omth * aK1;
+        a1 = cA;
+        aK1 = KA;
+      } else {
+        yA = 1.5 * cA - 2.0 * a1 + 0.5 * a2 + KA;
+        a2 = a1;
+        a1 = cA;
+      }
+      const bool twin = (kB != kA);
+      double yB = 0.0;
+      const double zB = twin ? b0 : cA;  // z in plane kB, partner of yA
+      if (twin) {
+        if (theta) {
+          double nb = 0.0, nK = 0.0;
+          if (kB > 0) {
+            nb = center(kB - 1);
+            nK = stiff(kB - 1, nb);
+          }
+          yB = (b0 - nb) + th * bK0 + omth * nK;
+          b0 = nb;
+          bK0 = nK;
+        } else {
+          const double KB = stiff(kB, b0);
+          const double nb2 = (kB > 1) ? center(kB - 2) : 0.0;
+          yB = 1.5 * b0 - 2.0 * b1 + 0.5 * nb2 + KB;
+          b0 = b1;
+          b1 = nb2;
+        }
+      }
+      const long long oA = (long long)kB * m + p;  // block n-1-kA receives row kA
+      const long long oB = (long long)kA * m + p;  // block n-1-kB = kA receives row kB
+      if (MODE == SM_MINRES) {
+        yA *= s;
+        out[oA] = yA;
+        acc += yA * (zB * s);
+        if (twin) {
+          yB *= s;
+          out[oB] = yB;
+          acc += yB * (cA * s);
+        }
+      } else if (MODE == SM_APPLY) {
+        out[oA] = yA;
+        if (twin) out[oB] = yB;
+      } else {  // SM_RESID: r = Y f_H - Y T x; block n-1-k of Y f_H is f_H block k
+        const double rA = fH[(long long)kA * m + p] - yA;
+        if (out) out[oA] = rA;
+        acc += rA * rA;
+        if (twin) {
+          const double rB = fH[(long long)kB * m + p] - yB;
+          if (out) out[oB] = rB;
+          acc += rB * rB;
+        }
+      }
+    }
+  }
+  if (MODE == SM_MINRES || MODE == SM_RESID) {
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    double tot;
+    unsigned int *cnt = &S->counter[MODE == SM_MINRES ? CNT_STENCIL : CNT_RESID];
+    if (last_block_reduce<kNT>(acc, partials, cnt, nb, bid, red, &tot) && flat_tid() == 0) {
+      if (MODE == SM_MINRES) {
+        S->alpha = tot;
+        S->lz_a = tot / S->beta;
+        S->lz_b = (S->k > 0) ? S->beta / S->beta_prev : 0.0;
+      } else {
+        S->rnorm2 = tot;
+      }
+    }
+  }
+}
+
+// f_H (Sec. 1 for theta, Sec. 4 with the start-up history moved into blocks 1-2 for BDF2).
+__global__ void k_rhs(Geom g, const double *__restrict__ f, const double *__restrict__ u0,
+                      const double *__restrict__ uprev, const double *__restrict__ extra,
+                      double *__restrict__ fH) {
+  const long long N = g.N, m = g.m;
+  const double tau = g.tau;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / m, p = e - k * m;
+    double r;
+    if (g.scheme == ST_THETA) {
+      r = g.theta * tau * f[(k + 1) * m + p] + (1.0 - g.theta) * tau * f[k * m + p];
+      if (k == 0) {
+        const int i = (int)(p % g.mx), j = (int)(p / g.mx);
+        const double cw = g.cx[(long long)j * (g.mx + 1) + i];
+        const double ce = g.cx[(long long)j * (g.mx + 1) + i + 1];
+        double cs = 0.0, cn = 0.0;
+        if (g.dim == 2) {
+          cs = g.cy[(long long)j * g.mx + i];
+          cn = g.cy[(long long)(j + 1) * g.mx + i];
+        }
+        const double c = u0[p];
+        const double Kc = tauK(u0, p, i, j, g.mx, g.my, g.dim, cw, ce, cs, cn, c);
+        r += c - (1.0 - g.theta) * Kc;
+      }
+    } else {
+      r = tau * f[(k + 1) * m + p];
+      if (k == 0) r += 2.0 * u0[p] - 0.5 * (uprev ? uprev[p] : u0[p]);
+      if (k == 1) r -= 0.5 * u0[p];
+    }
+    if (extra) r += extra[e];
+    fH[e] = r;
+  }
+}
+
+// Face terms of dL/da: g_face = -(tau/h^2) sum_k (lam_p - lam_q)(w_p - w_q), with
+// w_k = theta u_k + (1-theta) u_{k-1} (u_{-1} = u0) for theta and w_k = u_k for BDF2.
+// Thread (j, i) of the (my+1) x (mx+1) face grid owns x-face (j, i) [between nodes (j,i-1) and
+// (j,i)] when j < my and y-face (j, i) [between (j-1,i) and (j,i)] when i < mx.
+// cx/cy already hold tau*a/h^2; a_face enters linearly, so tau/h^2 = c/a_face is recovered from
+// the unit-coefficient spacing passed in sx, sy.
+__global__ void k_grad_faces(Geom g, const double *__restrict__ lam, const double *__restrict__ u,
+                             const double *__restrict__ u0, double sx, double sy,
+                             double *__restrict__ gx, double *__restrict__ gy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int mx = g.mx, my = g.my;
+  if (i > mx || j > my) return;
+  const long long m = g.m;
+  const bool doX = (j < my);
+  const bool doY = (g.dim == 2) && (i < mx);
+  if (!doX && !doY) return;
+  const double th = (g.scheme == ST_THETA) ? g.theta : 1.0;
+  // node indices (or -1 for a boundary node)
+  const long long pc = (i < mx && j < my) ? (long long)j * mx + i : -1;
+  const long long pl = (i > 0 && j < my) ? (long long)j * mx + i - 1 : -1;
+  const long long pd = (j > 0 && i < mx) ? (long long)(j - 1) * mx + i : -1;
+  double ax = 0.0, ay = 0.0;
+  double uc_prev = pc >= 0 ? u0[pc] : 0.0, ul_prev = pl >= 0 ? u0[pl] : 0.0,
+         ud_prev = pd >= 0 ? u0[pd] : 0.0;
+  for (int k = 0; k < g.n; ++k) {
+    const double *L = lam + (long long)k * m;
+    const double *U = u + (long long)k * m;
+    const double uc = pc >= 0 ? U[pc] : 0.0;
+    const double ul = pl >= 0 ? U[pl] : 0.0;
+    const double ud = pd >= 0 ? U[pd] : 0.0;
+    const double wc = th * uc + (1.0 - th) * uc_prev;
+    const double wl = th * ul + (1.0 - th) * ul_prev;
+    const double wd = th * ud + (1.0 - th) * ud_prev;
+    const double lc = pc >= 0 ? L[pc] : 0.0;
+    if (doX) {
+      const double ll = pl >= 0 ? L[pl] : 0.0;
+      ax += (lc - ll) * (wc - wl);
+    }
+    if (doY) {
+      const double ld_ = pd >= 0 ? L[pd] : 0.0;
+      ay += (lc - ld_) * (wc - wd);
+    }
+    uc_prev = uc;
+    ul_prev = ul;
+    ud_prev = ud;
+  }
+  if (doX) gx[(long long)j * (mx + 1) + i] = -sx * ax;
+  if (doY) gy[(long long)j * mx + i] = -sy * ay;
+}
+
+// Nodal gradient: each face gradient is split half/half between its two nodes.
+__global__ void k_grad_nodes(int dim, int mx, int my, const double *__restrict__ gx,
+                             const double *__restrict__ gy, double *__restrict__ grad) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;  // 0..mx+1
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;  // 0..my+1 (0 in 1D)
+  if (dim == 1) {
+    if (I > mx + 1 || J > 0) return;
+    double s = 0.0;
+    if (I <= mx) s += 0.5 * gx[I];      // face I: between nodes I and I+1
+    if (I >= 1) s += 0.5 * gx[I - 1];   // face I-1: between nodes I-1 and I
+    grad[I] = s;
+    return;
+  }
+  if (I > mx + 1 || J > my + 1) return;
+  double s = 0.0;
+  // x-faces lie on interior rows j = J-1; face (j, i) joins nodal columns i and i+1
+  if (J >= 1 && J <= my) {
+    const int j = J - 1;
+    if (I <= mx) s += 0.5 * gx[(long long)j * (mx + 1) + I];
+    if (I >= 1) s += 0.5 * gx[(long long)j * (mx + 1) + I - 1];
+  }
+  // y-faces lie on interior columns i = I-1; face (j, i) joins nodal rows j and j+1
+  if (I >= 1 && I <= mx) {
+    const int i = I - 1;
+    if (J <= my) s += 0.5 * gy[(long long)J * mx + i];
+    if (J >= 1) s += 0.5 * gy[(long long)(J - 1) * mx + i];
+  }
+  grad[(long long)J * (mx + 2) + I] = s;
+}
+
+}  // namespace
+
+int stencil_blocks(const Geom &g) {
+  Tile t = tile_for(g);
+  return t.gx * t.gy * t.nchunk;
+}
+
+template <class Tz>
+cudaError_t launch_stencil(const Geom &g, int mode, const Tz *z, double *out, const double *fH,
+                           State *S, double *partials, int, cudaStream_t st) {
+  Tile t = tile_for(g);
+  dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
+  dim3 grid(t.gx, t.gy, t.nchunk);
+  prof_begin(mode == SM_RESID ? KC_RESID : KC_STENCIL, st);
+  switch (mode) {
+    case SM_MINRES:
+      k_stencil<Tz, SM_MINRES><<<grid, block, 0, st>>>(g, z, out, fH, S, partials, t.kc);
+      break;
+    case SM_APPLY:
+      k_stencil<Tz, SM_APPLY><<<grid, block, 0, st>>>(g, z, out, fH, S, partials, t.kc);
+      break;
+    case SM_RESID:
+      k_stencil<Tz, SM_RESID><<<grid, block, 0, st>>>(g, z, out, fH, S, partials, t.kc);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_stencil<double>(const Geom &, int, const double *, double *,
+                                            const double *, State *, double *, int, cudaStream_t);
+template cudaError_t launch_stencil<float>(const Geom &, int, const float *, double *,
+                                           const double *, State *, double *, int, cudaStream_t);
+
+cudaError_t launch_rhs(const Geom &g, const double *f, const double *u0, const double *uprev,
+                       const double *extra, double *fH, cudaStream_t st) {
+  long long blocks = (g.N + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  prof_begin(KC_AUX, st);
+  k_rhs<<<(unsigned)blocks, 256, 0, st>>>(g, f, u0, uprev, extra, fH);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_a(const Geom &g, const double *lam, const double *u, const double *u0,
+                          double *gface_x, double *gface_y, double *grad, cudaStream_t st) {
+  const double hx = 1.0 / (g.mx + 1), hy = 1.0 / (g.my + 1);
+  const double sx = g.tau / (hx * hx), sy = g.tau / (hy * hy);
+  dim3 b(32, 8);
+  const int fy = (g.dim == 2) ? g.my + 1 : 1;
+  dim3 gr((g.mx + 1 + 31) / 32, (fy + 7) / 8);
+  prof_begin(KC_AUX, st);
+  k_grad_faces<<<gr, b, 0, st>>>(g, lam, u, u0, sx, sy, gface_x, gface_y);
+  prof_end(st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ny = (g.dim == 2) ? g.my + 2 : 1;
+  dim3 gn((g.mx + 2 + 31) / 32, (ny + 7) / 8);
+  prof_begin(KC_AUX, st);
+  k_grad_nodes<<<gn, b, 0, st>>>(g.dim, g.mx, g.my, gface_x, gface_y, grad);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace st

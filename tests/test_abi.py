@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports every symbol include/st_minres.h declares
+(no GPU needed: no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_10062_gb300 import build, load_library
+
+    build.build()
+    return load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "st_minres.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(st_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_matches_binding_exports():
+    from paper_2201_10062_gb300 import EXPORTS
+
+    assert _declared() == sorted(EXPORTS)
+
+
+def test_every_declared_symbol_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_version(lib):
+    from paper_2201_10062_gb300 import strerror
+
+    assert lib.st_version() >= 1
+    for c in range(7):
+        assert isinstance(strerror(c), str) and strerror(c)
+    assert strerror(99) == "unknown status"
+
+
+def _spec(**kw):
+    from paper_2201_10062_gb300 import ProblemSpec
+
+    base = dict(dim=2, mx=15, my=15, n=8)
+    base.update(kw)
+    return ProblemSpec(**base)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(mx=14), dict(my=16), dict(dim=3), dict(n=0), dict(n=2000), dict(T=0.0), dict(theta=1.5),
+    dict(dim=1, my=3), dict(mx=2047), dict(prec="Ptheta", scheme="bdf2"),
+])
+def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    spec = _spec(**bad)
+    p, keep = spec.to_c()
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG
+    assert not h.value
+
+
+def test_setup_rejects_nonpositive_a(lib):
+    import numpy as np
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    a = np.ones((17, 17))
+    a[3, 4] = 0.0
+    p, keep = _spec(a_nodal=a).to_c()
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG
+
+
+def test_workspace_bytes(lib):
+    from paper_2201_10062_gb300 import st_workspace_bytes
+
+    b64 = st_workspace_bytes(_spec(mx=255, my=255, n=256))
+    b32 = st_workspace_bytes(_spec(mx=255, my=255, n=256, precision="mixed"))
+    N = 255 * 255 * 256
+    assert 9 * 8 * N <= b64 <= 9 * 8 * N + (64 << 20)
+    assert b32 < b64
+
+
+def test_null_arguments(lib):
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    assert lib.st_setup(None, None) == ST_ERR_ARG
+    assert lib.st_apply_op(None, None, None) == ST_ERR_ARG
+    assert lib.st_solve(None, None, None, 1e-8, 10, None) == ST_ERR_ARG
+    lib.st_destroy(None)

@@ -1,0 +1,201 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import heat as H
+from workloads import synthetic as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_10062_gb300 as P
+    from paper_2201_10062_gb300 import build
+
+    build.build()
+    P.load_library()
+    return P
+
+
+def _spec(P, w, prec="PH", precision="fp64"):
+    return P.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec, precision)
+
+
+def _d(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _h(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rel2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# (dim, mx, my, n, scheme, theta, varcoef): ragged tiles (mx odd vs 32-wide blocks), odd and
+# even n, n = 1 and 2, 1D and 2D, constant and varying a.
+CASES = [
+    (1, 7, 1, 5, "theta", 1.0, False),
+    (1, 63, 1, 64, "theta", 1.0, False),
+    (1, 127, 1, 37, "theta", 0.5, True),
+    (1, 31, 1, 1, "theta", 0.5, True),
+    (1, 15, 1, 2, "bdf2", 1.0, True),
+    (2, 3, 3, 1, "theta", 0.5, False),
+    (2, 15, 15, 16, "theta", 0.5, True),
+    (2, 31, 7, 33, "theta", 1.0, False),
+    (2, 7, 31, 2, "bdf2", 1.0, True),
+    (2, 63, 63, 40, "bdf2", 1.0, True),
+    (2, 63, 31, 65, "theta", 0.3, True),
+]
+
+
+def _ids(c):
+    return f"{c[0]}d-{c[1]}x{c[2]}-n{c[3]}-{c[4]}{c[5]}-{'var' if c[6] else 'const'}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=[_ids(c) for c in CASES])
+def test_apply_op_and_rhs(pkg, case):
+    dim, mx, my, n, scheme, theta, var = case
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=mx + n)
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w))
+    v = np.random.default_rng(1).standard_normal((n, p.m))
+    y = _h(s.st_apply_op(_d(v))).reshape(n, p.m)
+    assert _rel_max(y, H.apply_op(p, v)) <= 1e-13
+    up = _d(w.u_prev) if w.u_prev is not None else None
+    fH = _h(s.st_assemble_rhs(_d(w.f), _d(w.u0), up)).reshape(n, p.m)
+    assert _rel_max(fH, H.rhs(p, w.f, w.u0, w.u_prev)) <= 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[_ids(c) for c in CASES])
+def test_apply_prec_fp64_and_fp32(pkg, case):
+    dim, mx, my, n, scheme, theta, var = case
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=2 * mx + n)
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w))
+    v = np.random.default_rng(2).standard_normal((n, p.m))
+    ref = H.apply_prec(p, v)
+    z = _h(s.st_apply_prec(_d(v))).reshape(n, p.m)
+    assert _rel_max(z, ref) <= 1e-12
+    z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(n, p.m)
+    assert _rel2(z32, ref) <= 2e-5
+    # in place
+    vd = _d(v)
+    s.st_apply_prec(vd, out=vd)
+    assert _rel_max(_h(vd).reshape(n, p.m), ref) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("case", [
+    (1, 63, 1, 64, "theta", 1.0, False),
+    (2, 31, 31, 32, "theta", 0.5, True),
+    (2, 63, 15, 24, "bdf2", 1.0, True),
+    (2, 15, 31, 17, "theta", 1.0, False),
+], ids=_ids)
+def test_solve_equal_iterations(pkg, case):
+    """Same number of MINRES iterations on both sides: solutions agree to 1e-10 (relative 2-norm)."""
+    dim, mx, my, n, scheme, theta, var = case
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=5)
+    p = H.Problem.from_workload(w)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    s = pkg.Solver(_spec(pkg, w))
+    for K in (1, 2, 7, 15):
+        u, st = s.st_solve(_d(fH), tol=0.0, maxit=K, allow_not_converged=True)
+        x_or, info = H.solve(p, fH, tol=0.0, maxit=K, rule="est")
+        assert st["iterations"] == info["iterations"] == K
+        assert _rel2(_h(u).reshape(n, p.m), x_or) <= 1e-10, K
+        assert abs(st["est_rel_res"] - info["est"][-1]) <= 1e-9 * max(info["est"][-1], 1e-12) + 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-8])
+def test_solve_natural_stop(pkg, tol):
+    """Stopping rule on the true residual: iteration counts within one of the oracle's."""
+    for w in (W.config_1d_sine(), W.small_case(2, 31, 31, 48, theta=0.5, varcoef=True, seed=9)):
+        p = H.Problem.from_workload(w)
+        fH = H.rhs(p, w.f, w.u0, w.u_prev)
+        s = pkg.Solver(_spec(pkg, w))
+        u, st = s.st_solve(_d(fH), tol=tol, maxit=300)
+        x_or, info = H.solve(p, fH, tol=tol, maxit=300)
+        assert abs(st["iterations"] - info["iterations"]) <= 1, (st, info["iterations"])
+        assert st["true_rel_res"] <= tol
+        r = H.flip(fH, p.n) - H.apply_op(p, _h(u).reshape(p.n, p.m))
+        assert np.linalg.norm(r) / np.linalg.norm(fH) <= tol * (1 + 1e-6)
+        s.close()
+
+
+def test_mixed_precision_solve(pkg):
+    """float32 preconditioner in float64 refinement: error vs the oracle's converged solution."""
+    w = W.small_case(2, 63, 63, 64, theta=0.5, varcoef=True, seed=13)
+    p = H.Problem.from_workload(w)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    x_ref, info = H.solve(p, fH, tol=1e-13, maxit=500)
+    s = pkg.Solver(_spec(pkg, w, precision="mixed"))
+    u, st = s.st_solve(_d(fH), tol=1e-10, maxit=500)
+    assert st["true_rel_res"] <= 1e-10
+    assert _rel2(_h(u).reshape(p.n, p.m), x_ref) <= 1e-8
+    u8, st8 = s.st_solve(_d(fH), tol=1e-8, maxit=500)
+    assert st8["true_rel_res"] <= 1e-8
+    s.close()
+
+
+def test_transpose_solve_and_grad_a(pkg):
+    """T^T lam = g via (Y T)(Y lam) = g, and the a-gradient contraction, against the oracle."""
+    w = W.small_case(2, 15, 31, 20, theta=1.0, varcoef=True, seed=17)
+    p = H.Problem.from_workload(w)
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal((p.n, p.m))
+    s = pkg.Solver(_spec(pkg, w))
+    lam, st = s.st_solve_transpose(_d(g), tol=1e-13, maxit=400)
+    lam_or, info = H.solve_transpose(p, g, tol=1e-13, maxit=400)
+    assert _rel2(_h(lam).reshape(p.n, p.m), lam_or) <= 1e-10
+    u = rng.standard_normal((p.n, p.m))
+    ga = _h(s.st_grad_a(_d(lam_or), _d(u), _d(w.u0))).reshape(w.a_nodal.shape)
+    _, _, ga_or = H.adjoint_gradients(p, u, lam_or, w.u0)
+    assert _rel_max(ga, ga_or) <= 1e-12
+    s.close()
+
+
+def test_zero_rhs(pkg):
+    w = W.small_case(2, 7, 7, 4, seed=1)
+    s = pkg.Solver(_spec(pkg, w))
+    u, st = s.st_solve(torch.zeros(w.N, dtype=torch.float64, device="cuda"), tol=1e-8, maxit=10)
+    assert st["iterations"] == 0 and float(u.abs().max()) == 0.0
+    s.close()
+
+
+# ------------------------------------------------------------------ full-size workloads
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_2d_crank_nicolson(pkg, precision):
+    """2D 255^2, n = 256, theta = 1/2, manufactured rhs + seeded noise: operator and
+    preconditioner parity on the whole vector, solve residual checked by the oracle's operator."""
+    w = W.config_2d_sine_cn()
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w, precision=precision))
+    fH_or = H.rhs(p, w.f, w.u0) + w.noise
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0), extra=_d(w.noise))
+    assert _rel_max(_h(fH).reshape(p.n, p.m), fH_or) <= 1e-13
+    if precision == "fp64":
+        v = np.random.default_rng(4).standard_normal((p.n, p.m))
+        assert _rel_max(_h(s.st_apply_op(_d(v))).reshape(p.n, p.m), H.apply_op(p, v)) <= 1e-13
+        assert _rel_max(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m), H.apply_prec(p, v)) <= 1e-12
+    u, st = s.st_solve(fH, tol=1e-8, maxit=500)
+    u_h = _h(u).reshape(p.n, p.m)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, u_h)
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-8 * (1 + 1e-6)
+    # discretisation error of the manufactured solution stays at the O(tau^2 + h^2) level
+    assert np.max(np.abs(u_h - w.u_exact)) < 1e-3
+    s.close()
