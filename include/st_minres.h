@@ -143,6 +143,23 @@ int st_solve_transpose(st_handle *h, const double *g_dev, double *lam_dev, doubl
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev);
 
+/* Residual check that allocates nothing (the paper has no counterpart; it is a deployment aid).
+ * Some callers cannot allocate device memory at the moment they need a residual: code that is
+ * recording a CUDA graph, latency-critical loops where cudaFree's implicit device synchronisation
+ * is not acceptable, or hosts that give all device memory to their own arena up front.  This call
+ * needs no handle and no cudaMalloc/cudaFree: its per-block partial sums live in a fixed static
+ * __device__ array of 64 KB (room for 4096 blocks; every GPU that loads the library keeps it until
+ * the process exits).  All valid st_problem sizes fit; anything else returns ST_ERR_ARG.
+ * prob: sizes, scheme, theta, T and stream (prob->a_nodal must be NULL); a_nodal_dev: device copy
+ * of the nodal a grid (layout as st_problem.a_nodal) or NULL for a = 1; fH_dev, u_dev: N entries.
+ * Outputs: r_dev (N entries, may be NULL) = Y f_H - Y T u; sums_dev[0] = ||r||^2 and
+ * sums_dev[1] = ||f_H||^2 (two device doubles), both written on prob->stream.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares the
+ * one array, so calls that overlap on the GPU (other streams, other host threads) race. */
+int st_residual_noalloc(const st_problem *prob, const double *a_nodal_dev, const double *fH_dev,
+                        const double *u_dev, double *r_dev, double *sums_dev);
+
 /* Kernel-class profiler.  st_profile_begin starts bracketing every kernel the handle launches
  * with CUDA events on the handle's stream (room for `capacity` launches; later launches are only
  * counted).  st_profile_end synchronises the stream, writes per-class totals for classes

@@ -27,7 +27,7 @@ EXPORTS = (
     "st_setup", "st_destroy", "st_workspace_bytes", "st_assemble_rhs", "st_apply_op",
     "st_apply_prec", "st_apply_prec_f32", "st_solve", "st_solve_host", "st_solve_transpose",
     "st_grad_a", "st_strerror", "st_version", "st_profile_begin", "st_profile_end",
-    "st_kernel_class_name",
+    "st_kernel_class_name", "st_residual_noalloc",
 )
 KERNEL_CLASSES = ("stencil", "lanczos", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     lib.st_profile_begin.restype = I
     lib.st_profile_end.argtypes = [P, ctypes.POINTER(StKernelTime), I]
     lib.st_profile_end.restype = I
+    lib.st_residual_noalloc.argtypes = [ctypes.POINTER(StProblem), P, P, P, P, P]
+    lib.st_residual_noalloc.restype = I
     lib.st_kernel_class_name.argtypes = [I]
     lib.st_kernel_class_name.restype = ctypes.c_char_p
     _lib = lib
