@@ -1,0 +1,143 @@
+// Radix-8/4/2 Stockham FFT (self-sorting, forward e^{-2 pi i jk/L}) for a batch of complex
+// sequences of length L = 2^p held in shared memory, used by the spatial DST kernels.
+//
+// Pass with radix R and span Ns (Ns = 1, R1, R1 R2, ...): work item j (0..L/R-1) loads the R
+// values j + r L/R, multiplies value r by W_{Ns R}^{r (j mod Ns)}, takes an R-point DFT in
+// registers and stores output q at (j div Ns) Ns R + (j mod Ns) + q Ns.  After the last pass
+// the sequence is in natural order.  Shared-memory slots are padded (one slot every 2^PADSHIFT
+// elements) so that the strided stores of the early passes hit at most two-way bank conflicts.
+#pragma once
+
+namespace st {
+
+template <class T>
+struct cpx {
+  T x, y;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) {
+  return cpx<T>{a.x + b.x, a.y + b.y};
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) {
+  return cpx<T>{a.x - b.x, a.y - b.y};
+}
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+  return cpx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * (-i)
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) {
+  return cpx<T>{a.y, -a.x};
+}
+
+template <class T>
+struct PadShift;
+template <>
+struct PadShift<float> {
+  static constexpr int v = 4;  // 16 complex floats per 128-byte bank row
+};
+template <>
+struct PadShift<double> {
+  static constexpr int v = 3;  // 8 complex doubles per 128-byte bank row
+};
+
+template <class T>
+__host__ __device__ __forceinline__ int fft_pad(int e) {
+  return e + (e >> PadShift<T>::v);
+}
+
+template <class T>
+__host__ __device__ __forceinline__ int fft_padded_len(int L) {
+  return L + (L >> PadShift<T>::v);
+}
+
+// In-register R-point DFT, natural order in and out.
+template <class T, int R>
+struct Dft;
+
+template <class T>
+struct Dft<T, 2> {
+  __host__ __device__ __forceinline__ static void run(cpx<T> *v) {
+    const cpx<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <class T>
+struct Dft<T, 4> {
+  __host__ __device__ __forceinline__ static void run(cpx<T> *v) {
+    const cpx<T> s0 = cadd(v[0], v[2]), d0 = csub(v[0], v[2]);
+    const cpx<T> s1 = cadd(v[1], v[3]), d1 = mul_mi(csub(v[1], v[3]));
+    v[0] = cadd(s0, s1);
+    v[2] = csub(s0, s1);
+    v[1] = cadd(d0, d1);
+    v[3] = csub(d0, d1);
+  }
+};
+
+template <class T>
+struct Dft<T, 8> {
+  __host__ __device__ __forceinline__ static void run(cpx<T> *v) {
+    const T h = T(0.70710678118654752440084436210485);
+    // split into even and odd samples: X_q = E_q + W8^q O_q, X_{q+4} = E_q - W8^q O_q
+    cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4>::run(e);
+    Dft<T, 4>::run(o);
+    // W8^1 = (1 - i)/sqrt2, W8^2 = -i, W8^3 = -(1 + i)/sqrt2
+    const cpx<T> o1 = cpx<T>{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
+    const cpx<T> o2 = mul_mi(o[2]);
+    const cpx<T> o3 = cpx<T>{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+// One Stockham pass on `count` sequences (each fft_padded_len(L) slots apart).  tw[t] =
+// W_L^t for t < L/2.  Work items are strided over `nthreads` threads starting at `tid`.
+template <class T, int R>
+__host__ __device__ __forceinline__ void stockham_pass(const cpx<T> *src, cpx<T> *dst,
+                                                       const cpx<T> *tw, int L, int logL, int Ns,
+                                                       int logNs, int count, int tid,
+                                                       int nthreads) {
+  constexpr int LOGR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
+  const int LR = L / R;
+  const int logLR = logL - LOGR;
+  const int Lp = fft_padded_len<T>(L);
+  const int twstep = L >> (logNs + LOGR);  // L / (Ns R)
+  for (int task = tid; task < count * LR; task += nthreads) {
+    const int pp = task >> logLR;
+    const int j = task & (LR - 1);
+    const cpx<T> *s = src + pp * Lp;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[fft_pad<T>(j + r * LR)];
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const cpx<T> w1 = tw[k * twstep];
+      cpx<T> w = w1;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        v[r] = cmulc(v[r], w);
+        if (r + 1 < R) w = cmulc(w, w1);
+      }
+    }
+    Dft<T, R>::run(v);
+    const int idxD = ((j >> logNs) << (logNs + LOGR)) + k;
+    cpx<T> *d = dst + pp * Lp;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[fft_pad<T>(idxD + r * Ns)] = v[r];
+  }
+}
+
+}  // namespace st

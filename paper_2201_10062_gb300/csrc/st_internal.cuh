@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/st_minres.h"
+#include "st_df.cuh"
 
 namespace st {
 
@@ -166,6 +167,26 @@ template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
                         int tmode, double *partials, cudaStream_t st);
 int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32);
+
+// mixed path: double-float (df) MINRES vectors, float32 preconditioned vectors
+cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, double *partials,
+                              cudaStream_t st);
+cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const double *fH, State *S,
+                            double *partials, cudaStream_t st);
+cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
+                              cudaStream_t st);
+cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
+                             State *S, cudaStream_t st);
+cudaError_t launch_flip_to_df(const Geom &g, const double *src, df *dst, cudaStream_t st);
+cudaError_t launch_df_to_double(long long N, const df *src, double *dst, cudaStream_t st);
+
+// real part used when a transform reads its input in the compute type
+template <class Tc>
+__device__ __forceinline__ Tc to_real(double v) { return (Tc)v; }
+template <class Tc>
+__device__ __forceinline__ Tc to_real(float v) { return (Tc)v; }
+template <class Tc>
+__device__ __forceinline__ Tc to_real(df v) { return (Tc)v.hi; }
 
 // vector kernels
 cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,

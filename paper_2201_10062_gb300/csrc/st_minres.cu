@@ -10,6 +10,7 @@
 // Scalars never leave the device inside the loop; the host reads the state every few
 // iterations to learn whether the device-side stopping test has fired.  Kernels launched after
 // that point return at entry, so the host may run ahead by a few iterations at no cost.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -104,6 +105,82 @@ __global__ void __launch_bounds__(kNT)
 
 }  // namespace
 
+namespace {
+// ------------------------------------------------------------------ double-float vectors
+// Mixed path: vhat, d and x are double-floats (hi + lo float32 pairs, ~46 significant bits);
+// the per-element arithmetic runs on the float32 pipes (see st_df.cuh).
+__device__ __forceinline__ void dacc_add(float &s, float &t, float p, float e) {
+  float ss, err;
+  two_sum(s, p, ss, err);
+  s = ss;
+  t += err + e;
+}
+__device__ __forceinline__ void dacc_prod(float &s, float &t, df a, df b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  dacc_add(s, t, p, e);
+}
+
+__global__ void __launch_bounds__(kNT)
+    k_lanczos_df(long long N, const df *__restrict__ q, const df *__restrict__ vk,
+                 df *__restrict__ vprev, const State *S) {
+  if (!S->active) return;
+  const df a = df_neg(df_of_double(S->lz_a)), b = df_neg(df_of_double(S->lz_b));
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kNT) {
+    const df qq = q[i], vv = vk[i], pp = vprev[i];
+    float s = qq.hi, t = qq.lo;
+    dacc_prod(s, t, a, vv);
+    dacc_prod(s, t, b, pp);
+    vprev[i] = df_from_sum(s, t);
+  }
+}
+
+__global__ void __launch_bounds__(kNT)
+    k_update_df(long long N, const float *__restrict__ z, const df *__restrict__ d1,
+                df *__restrict__ d2, df *__restrict__ x, const State *S) {
+  if (!S->active) return;
+  const df cz = df_of_double(S->dz), c1 = df_of_double(S->d1), c2 = df_of_double(S->d2),
+           cx = df_of_double(S->xc);
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kNT) {
+    float s = 0.f, t = 0.f;
+    {
+      const float zi = z[i];
+      float p, e;
+      two_prod(cz.hi, zi, p, e);
+      e = fmaf(cz.lo, zi, e);
+      dacc_add(s, t, p, e);
+    }
+    dacc_prod(s, t, c1, d1[i]);
+    dacc_prod(s, t, c2, d2[i]);
+    const df d = df_from_sum(s, t);
+    d2[i] = d;
+    const df xo = x[i];
+    float xs = xo.hi, xt = xo.lo;
+    dacc_prod(xs, xt, cx, d);
+    x[i] = df_from_sum(xs, xt);
+  }
+}
+
+__global__ void k_flip_to_df(long long m, int n, const double *__restrict__ src,
+                             df *__restrict__ dst) {
+  const long long total = (long long)n * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / m, p = e - k * m;
+    dst[(long long)(n - 1 - k) * m + p] = df_of_double(src[e]);
+  }
+}
+
+__global__ void k_df_to_double(long long N, const df *__restrict__ src, double *__restrict__ dst) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = df_to_double(src[e]);
+}
+}  // namespace
+
 thread_local Prof *t_prof = nullptr;
 
 void prof_begin(int cls, cudaStream_t st) {
@@ -156,6 +233,36 @@ cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
+                              cudaStream_t st) {
+  prof_begin(KC_LANCZOS, st);
+  k_lanczos_df<<<kStreamBlocks, kNT, 0, st>>>(N, q, vk, vkm1_out, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
+                             State *S, cudaStream_t st) {
+  prof_begin(KC_UPDATE, st);
+  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip_to_df(const Geom &g, const double *src, df *dst, cudaStream_t st) {
+  prof_begin(KC_AUX, st);
+  k_flip_to_df<<<kStreamBlocks, kNT, 0, st>>>(g.m, g.n, src, dst);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_double(long long N, const df *src, double *dst, cudaStream_t st) {
+  prof_begin(KC_AUX, st);
+  k_df_to_double<<<kStreamBlocks, kNT, 0, st>>>(N, src, dst);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm2(long long N, const double *v, State *S, double *partials,
                          cudaStream_t st) {
   prof_begin(KC_AUX, st);
@@ -179,7 +286,8 @@ struct st_handle {
   double *V[2];          // Lanczos vectors vhat
   void *Z[2];            // preconditioned vectors (double, or float in ST_MIXED)
   double *D[2];          // MINRES directions
-  double *q;             // stencil output
+  double *q;             // stencil output (a df array in ST_MIXED)
+  df *Xdf;               // ST_MIXED: double-float solution accumulator
   double *partials;      // per-block partial sums
   State *S;              // device scalars
   double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
@@ -292,6 +400,7 @@ size_t workspace_bytes(const Geom &g, bool mixed) {
   b += 2 * N * (mixed ? sizeof(float) : sizeof(double));   // Z
   b += 2 * N * sizeof(double);                             // D
   b += N * sizeof(double);                                 // q
+  if (mixed) b += N * sizeof(df);                          // x accumulator
   b += 2 * N * sizeof(double);                             // host staging
   b += (size_t)partials_needed(g) * sizeof(double);
   b += sizeof(State);
@@ -417,6 +526,7 @@ void free_handle(st_handle *h) {
     cudaFree(h->D[i]);
   }
   cudaFree(h->q);
+  cudaFree(h->Xdf);
   cudaFree(h->partials);
   cudaFree(h->S);
   cudaFree(h->hbuf_in);
@@ -444,6 +554,26 @@ cudaError_t launch_iteration(st_handle *h, int k, double *x) {
   e = launch_prec<Tc, double, Tz>(g, h->pp, h->V[o], zn, h->S, TM_ITER, h->partials, st);
   if (e != cudaSuccess) return e;
   return launch_update<Tz>(g.N, zc, h->D[c], h->D[o], x, h->S, st);
+}
+
+// Mixed path iteration k: df vectors in V, D, q; float32 z.
+cudaError_t launch_iteration_mixed(st_handle *h, int k) {
+  const int c = (k - 1) & 1, o = k & 1;
+  const Geom &g = h->g;
+  cudaStream_t st = h->stream;
+  const float *zc = (const float *)h->Z[c];
+  float *zn = (float *)h->Z[o];
+  df *V0 = (df *)h->V[c], *V1 = (df *)h->V[o];
+  df *D0 = (df *)h->D[c], *D1 = (df *)h->D[o];
+  df *q = (df *)h->q;
+  cudaError_t e;
+  e = launch_stencil_df(g, zc, q, h->S, h->partials, st);
+  if (e != cudaSuccess) return e;
+  e = launch_lanczos_df(g.N, q, V0, V1, h->S, st);
+  if (e != cudaSuccess) return e;
+  e = launch_prec<float, df, float>(g, h->pp, V1, zn, h->S, TM_ITER, h->partials, st);
+  if (e != cudaSuccess) return e;
+  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
 }
 
 int sync_state(st_handle *h) {
@@ -567,14 +697,54 @@ int solve_fp64(st_handle *h, const double *fH, double *x, double tol, int maxit,
   return finish_status(*h->hS, converged);
 }
 
-// Mixed precision: MINRES with the float32 preconditioner solves (Y T) d = r for the current
-// float64 residual r = Y f_H - Y T x, accumulating d into x; the float64 residual is then
-// recomputed (iterative refinement) until ||r||/||b|| <= tol.
+// Mixed precision: MINRES with the float32 preconditioner and double-float vectors solves
+// (Y T) d = r for the current residual r = Y f_H - Y T x, accumulating d into the double-float
+// x; at the end of each refinement step x is converted to float64 and the residual is
+// recomputed in float64 (iterative refinement) until ||r||/||b|| <= tol.
+int mixed_start(st_handle *h, double target, int maxit) {
+  const Geom &g = h->g;
+  ST_TRY(cudaMemsetAsync(h->D[0], 0, g.N * sizeof(df), h->stream));
+  ST_TRY(cudaMemsetAsync(h->D[1], 0, g.N * sizeof(df), h->stream));
+  ST_TRY(cudaMemsetAsync(h->V[1], 0, g.N * sizeof(df), h->stream));
+  State &s = *h->hS;
+  const double bn = s.bnorm2;
+  std::memset(&s, 0, sizeof(State));
+  s.bnorm2 = bn;
+  s.active = 1;
+  s.target = target;
+  s.maxit = maxit;
+  int r = push_state(h);
+  if (r) return r;
+  ST_TRY((launch_prec<float, df, float>(g, h->pp, (const df *)h->V[0], (float *)h->Z[0], h->S,
+                                        TM_INIT, h->partials, h->stream)));
+  return ST_OK;
+}
+
+int mixed_iterate(st_handle *h) {
+  int chunk = 4;
+  for (;;) {
+    const int k0 = h->hS->k;
+    for (int i = 1; i <= chunk; ++i) ST_TRY(launch_iteration_mixed(h, k0 + i));
+    int r = sync_state(h);
+    if (r) return r;
+    const State &s = *h->hS;
+    if (s.status != 0 || s.finish || !s.active) return ST_OK;
+    if (chunk < 16) chunk *= 2;
+  }
+}
+
 int solve_mixed(st_handle *h, const double *fH, double *x, double tol, int maxit,
                 st_stats *stats) {
   const Geom &g = h->g;
-  ST_TRY(cudaMemsetAsync(x, 0, g.N * sizeof(double), h->stream));
-  int r = prepare_rhs(h, fH);
+  cudaStream_t st = h->stream;
+  ST_TRY(cudaMemsetAsync(h->Xdf, 0, g.N * sizeof(df), st));
+  ST_TRY(cudaMemsetAsync(x, 0, g.N * sizeof(double), st));
+  std::memset(h->hS, 0, sizeof(State));
+  int r = push_state(h);
+  if (r) return r;
+  ST_TRY(launch_flip_to_df(g, fH, (df *)h->V[0], st));
+  ST_TRY(launch_norm2(g.N, fH, h->S, h->partials, st));
+  r = sync_state(h);
   if (r) return r;
   if (h->hS->bnorm2 == 0.0) return ST_OK;
   const double bn2 = h->hS->bnorm2;
@@ -587,17 +757,20 @@ int solve_mixed(st_handle *h, const double *fH, double *x, double tol, int maxit
     ++outer;
     const double target = std::max(0.5 * tol / rho, 1e-6);
     h->hS->bnorm2 = bn2;
-    r = minres_start<float, float>(h, target, maxit - total);
+    r = mixed_start(h, target, maxit - total);
     if (r) return r;
-    r = minres_iterate<float, float>(h, x);
+    r = mixed_iterate(h);
     if (r) return r;
     const State s = *h->hS;
     total += s.k;
     last_est = s.est;
     status = s.status;
-    // r = Y f_H - Y T x written into V[0]: the right-hand side of the next refinement step
-    r = true_residual(h, fH, x, h->V[0], &rho);
+    ST_TRY(launch_df_to_double(g.N, h->Xdf, x, st));
+    // r = Y f_H - Y T x (float64), stored as the next step's double-float right-hand side
+    ST_TRY(launch_resid_df(g, x, (df *)h->V[0], fH, h->S, h->partials, st));
+    r = sync_state(h);
     if (r) return r;
+    rho = (bn2 > 0.0) ? std::sqrt(h->hS->rnorm2 / bn2) : 0.0;
     ++checks;
     if (rho <= tol) {
       converged = true;
@@ -740,6 +913,7 @@ int st_setup(const st_problem *prob, st_handle **out) {
     if (e == cudaSuccess) e = cudaMalloc(&h->D[i], N * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->q, N * sizeof(double));
+  if (e == cudaSuccess && h->mixed) e = cudaMalloc(&h->Xdf, N * sizeof(df));
   h->partials_len = partials_needed(g);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->partials_len * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->S, sizeof(State));

@@ -17,6 +17,7 @@
 // accumulates <v, P^-1 v> = sum v~^2 / p for MINRES.
 #include <math.h>
 
+#include "st_fft.cuh"
 #include "st_internal.cuh"
 
 namespace st {
@@ -24,19 +25,6 @@ namespace st {
 namespace {
 
 constexpr int kNT = 256;
-
-template <class T>
-struct C2 {
-  T x, y;
-};
-
-template <class T>
-__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-  C2<T> r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
 
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
@@ -52,96 +40,98 @@ __device__ __forceinline__ bool gate_closed(const State *S) {
 // ------------------------------------------------------------------------------ spatial DST
 // XL = true: lines are rows (contiguous, line l starts at l*len).
 // XL = false: lines are columns of the (my x mx) planes: line l = k*mx + i starts at k*m + i and
-// its elements are mx apart.
+// its elements are mx apart.  A block owns 2*PB consecutive lines (PB complex sequences), loads
+// them coalesced into shared memory as odd extensions, runs the Stockham passes (ping-pong
+// between two padded buffers) and writes the sine coefficients back.
 template <class Tc, class Tin, class Tout, bool XL>
 __global__ void __launch_bounds__(kNT)
-    k_dst_space(const Tin *in, Tout *out, int len, int logL,
-                long long nlines, int mx, long long m, const Tc *__restrict__ tw, int PB,
-                const State *S) {
+    k_dst_space(const Tin *in, Tout *out, int len, int logL, long long nlines, int mx, long long m,
+                const Tc *tw, int PB, const State *S) {
   if (gate_closed(S)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   const int half = L >> 1;
-  C2<Tc> *tws = reinterpret_cast<C2<Tc> *>(smem_raw);
-  C2<Tc> *zb = tws + half;
-  Tc *zr = reinterpret_cast<Tc *>(zb);
+  const int Lp = fft_padded_len<Tc>(L);
+  cpx<Tc> *tws = reinterpret_cast<cpx<Tc> *>(smem_raw);
+  cpx<Tc> *bufA = tws + half;
+  cpx<Tc> *bufB = bufA + (size_t)PB * Lp;
+  Tc *ra = reinterpret_cast<Tc *>(bufA);
   const int tid = threadIdx.x;
-  for (int e = tid; e < half; e += kNT) {
-    tws[e].x = tw[2 * e];
-    tws[e].y = tw[2 * e + 1];
-  }
+  for (int e = tid; e < half; e += kNT) tws[e] = cpx<Tc>{tw[2 * e], tw[2 * e + 1]};
   const long long line0 = (long long)blockIdx.x * 2 * PB;
-  const int nl = (int)min((long long)2 * PB, nlines - line0);  // lines in this block
-  const int shift = 32 - logL;
-  // zero the positions that stay zero (0 and len+1) and the whole of any absent line
+  const int nl = (int)min((long long)2 * PB, nlines - line0);  // lines present in this block
+  // slots 0 and len+1 of every sequence are zero; absent lines contribute zero components
   for (int pp = tid; pp < PB; pp += kNT) {
-    zb[pp * L + (__brev(0u) >> shift)] = C2<Tc>{Tc(0), Tc(0)};
-    zb[pp * L + (__brev((unsigned)(len + 1)) >> shift)] = C2<Tc>{Tc(0), Tc(0)};
+    bufA[pp * Lp + fft_pad<Tc>(0)] = cpx<Tc>{Tc(0), Tc(0)};
+    bufA[pp * Lp + fft_pad<Tc>(len + 1)] = cpx<Tc>{Tc(0), Tc(0)};
   }
-  if (nl < 2 * PB) {
-    for (int idx = tid; idx < (2 * PB - nl) * len; idx += kNT) {
-      const int lb = nl + idx / len, e = idx % len;
-      const int pp = lb >> 1, comp = lb & 1;
-      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = Tc(0);
-      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = Tc(0);
-    }
+  for (int idx = tid; idx < (2 * PB - nl) * len; idx += kNT) {
+    const int lb = nl + idx / len, e = idx % len;
+    const int pp = lb >> 1, comp = lb & 1;
+    ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = Tc(0);
+    ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = Tc(0);
   }
-  // load (bit-reversed positions for the in-place decimation-in-time FFT)
+  // index maps avoid divisions: len + 1 = L/2 and 2*PB are powers of two
+  const int logH = logL - 1;
+  const int logP2 = 31 - __clz(2 * PB);
   if (XL) {
-    for (int idx = tid; idx < nl * len; idx += kNT) {
-      const int lb = idx / len, e = idx - lb * len;
-      const Tc v = (Tc)in[(line0 + lb) * len + e];
+    for (int idx = tid; idx < (nl << logH); idx += kNT) {
+      const int lb = idx >> logH, e = idx & (half - 1);
+      if (e >= len) continue;
+      const Tc v = to_real<Tc>(in[(line0 + lb) * len + e]);
       const int pp = lb >> 1, comp = lb & 1;
-      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = v;
-      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = -v;
+      ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = v;
+      ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = -v;
     }
   } else {
-    for (int idx = tid; idx < nl * len; idx += kNT) {
-      const int e = idx / nl, lb = idx - e * nl;
-      const long long l = line0 + lb;
-      const long long k = l / mx, i = l - k * mx;
-      const Tc v = (Tc)in[k * m + (long long)e * mx + i];
+    for (int idx = tid; idx < (len << logP2); idx += kNT) {
+      const int e = idx >> logP2, lb = idx & (2 * PB - 1);
+      if (lb >= nl) continue;
+      const int l = (int)line0 + lb;
+      const int k = l / mx, i = l - k * mx;
+      const Tc v = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
       const int pp = lb >> 1, comp = lb & 1;
-      zr[2 * (pp * L + (__brev((unsigned)(e + 1)) >> shift)) + comp] = v;
-      zr[2 * (pp * L + (__brev((unsigned)(L - 1 - e)) >> shift)) + comp] = -v;
-    }
-  }
-  // radix-2 decimation-in-time stages
-  for (int s = 1; s <= logL; ++s) {
-    __syncthreads();
-    const int hs = 1 << (s - 1);
-    const int tws_stride = L >> s;
-    for (int b = tid; b < PB * half; b += kNT) {
-      const int pp = b >> (logL - 1);
-      const int bb = b & (half - 1);
-      const int pos = bb & (hs - 1);
-      const int i0 = ((bb >> (s - 1)) << s) + pos;
-      const int i1 = i0 + hs;
-      C2<Tc> *zp = zb + pp * L;
-      const C2<Tc> w = tws[pos * tws_stride];
-      const C2<Tc> a = zp[i0];
-      const C2<Tc> t = cmul(w, zp[i1]);
-      zp[i0] = C2<Tc>{a.x + t.x, a.y + t.y};
-      zp[i1] = C2<Tc>{a.x - t.x, a.y - t.y};
+      ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = v;
+      ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = -v;
     }
   }
   __syncthreads();
+  cpx<Tc> *src = bufA, *dst = bufB;
+  int Ns = 1, logNs = 0, rem = logL;
+  while (rem > 0) {
+    const int lr = rem >= 3 ? 3 : rem;
+    if (lr == 3)
+      stockham_pass<Tc, 8>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
+    else if (lr == 2)
+      stockham_pass<Tc, 4>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
+    else
+      stockham_pass<Tc, 2>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
+    __syncthreads();
+    cpx<Tc> *t = src;
+    src = dst;
+    dst = t;
+    Ns <<= lr;
+    logNs += lr;
+    rem -= lr;
+  }
   const Tc sc = (Tc)(1.0 / sqrt((double)L));
   if (XL) {
-    for (int idx = tid; idx < nl * len; idx += kNT) {
-      const int lb = idx / len, e = idx - lb * len;
-      const C2<Tc> Z = zb[(lb >> 1) * L + e + 1];
+    for (int idx = tid; idx < (nl << logH); idx += kNT) {
+      const int lb = idx >> logH, e = idx & (half - 1);
+      if (e >= len) continue;
+      const cpx<Tc> Z = src[(lb >> 1) * Lp + fft_pad<Tc>(e + 1)];
       const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
       out[(line0 + lb) * len + e] = (Tout)v;
     }
   } else {
-    for (int idx = tid; idx < nl * len; idx += kNT) {
-      const int e = idx / nl, lb = idx - e * nl;
-      const long long l = line0 + lb;
-      const long long k = l / mx, i = l - k * mx;
-      const C2<Tc> Z = zb[(lb >> 1) * L + e + 1];
+    for (int idx = tid; idx < (len << logP2); idx += kNT) {
+      const int e = idx >> logP2, lb = idx & (2 * PB - 1);
+      if (lb >= nl) continue;
+      const int l = (int)line0 + lb;
+      const int k = l / mx, i = l - k * mx;
+      const cpx<Tc> Z = src[(lb >> 1) * Lp + fft_pad<Tc>(e + 1)];
       const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
-      out[k * m + (long long)e * mx + i] = (Tout)v;
+      out[(long long)k * m + (long long)e * mx + i] = (Tout)v;
     }
   }
 }
@@ -339,14 +329,20 @@ __global__ void __launch_bounds__(kNT)
   }
   __syncthreads();
   time_dst_tile<Tc, KT, JT>(X, Y, sintab, n, J);
-  double e = 0.0;
+  // <v, P^-1 v> partial: compensated (Kahan) sum in the tile's type, float64 across threads
+  Tc esum = Tc(0), ecomp = Tc(0);
   if (tkind == 0) {
     // scale by 1/p and accumulate <v, P^-1 v>
     for (int idx = tid; idx < n * J; idx += kNT) {
       const int kr = idx / J, c = idx - kr * J;
       const Tc ip = inv_symbol(sp, kr + 1, tmu[c]);
       const Tc y = Y[idx];
-      if (c < Je) e += (double)y * (double)y * (double)ip;
+      if (c < Je) {
+        const Tc term = y * y * ip - ecomp;
+        const Tc t = esum + term;
+        ecomp = (t - esum) - term;
+        esum = t;
+      }
       Y[idx] = y * ip;
     }
     __syncthreads();
@@ -362,6 +358,7 @@ __global__ void __launch_bounds__(kNT)
     }
   }
   if (tmode != TM_NONE) {
+    const double e = (double)esum - (double)ecomp;
     double tot;
     if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
                                &tot) &&
@@ -376,15 +373,19 @@ __global__ void __launch_bounds__(kNT)
 
 template <class Tc>
 size_t dst_smem(int L, int PB) {
-  return (size_t)(L / 2) * 2 * sizeof(Tc) + (size_t)PB * L * 2 * sizeof(Tc);
+  return (size_t)(L / 2) * sizeof(cpx<Tc>) +
+         (size_t)2 * PB * fft_padded_len<Tc>(L) * sizeof(cpx<Tc>);
 }
 
 template <class Tc>
 int dst_pairs(int L) {
-  int PB = (int)(65536 / ((size_t)L * 2 * sizeof(Tc)));
-  if (PB < 1) PB = 1;
+  // two padded buffers per sequence within ~72 KB (three blocks per SM)
+  const size_t per = (size_t)2 * fft_padded_len<Tc>(L) * sizeof(cpx<Tc>);
+  int PB = (int)((72 * 1024 - (size_t)(L / 2) * sizeof(cpx<Tc>)) / per);
   if (PB > 16) PB = 16;
-  return PB;
+  int p2 = 1;  // power of two, so that lines in a block index with shifts
+  while (2 * p2 <= PB) p2 *= 2;
+  return p2;
 }
 
 template <class Tc>
@@ -517,5 +518,7 @@ template cudaError_t launch_prec<double, double, double>(const Geom &, const Pre
 template cudaError_t launch_prec<float, double, float>(const Geom &, const PrecPlan &,
                                                        const double *, float *, State *, int,
                                                        double *, cudaStream_t);
+template cudaError_t launch_prec<float, df, float>(const Geom &, const PrecPlan &, const df *,
+                                                   float *, State *, int, double *, cudaStream_t);
 
 }  // namespace st

@@ -69,9 +69,12 @@ __device__ __forceinline__ double tauK(const Tz *__restrict__ base, long long p,
 // step; the centre value of each side is exactly the z the other side's output is paired with,
 // so the dot costs no extra loads.  Chunks cover the first ceil(n/2) planes; for odd n the middle
 // plane is its own mirror and is done once.
-template <class Tz, int MODE>
+__device__ __forceinline__ void put(double *p, double v) { *p = v; }
+__device__ __forceinline__ void put(df *p, double v) { *p = df_of_double(v); }
+
+template <class Tz, int MODE, class TO = double>
 __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ z,
-                                                 double *__restrict__ out,
+                                                 TO *__restrict__ out,
                                                  const double *__restrict__ fH, State *S,
                                                  double *__restrict__ partials, int kc) {
   __shared__ double red[32];
@@ -161,23 +164,23 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
       const long long oB = (long long)kA * m + p;  // block n-1-kB = kA receives row kB
       if (MODE == SM_MINRES) {
         yA *= s;
-        out[oA] = yA;
+        put(out + oA, yA);
         acc += yA * (zB * s);
         if (twin) {
           yB *= s;
-          out[oB] = yB;
+          put(out + oB, yB);
           acc += yB * (cA * s);
         }
       } else if (MODE == SM_APPLY) {
-        out[oA] = yA;
-        if (twin) out[oB] = yB;
+        put(out + oA, yA);
+        if (twin) put(out + oB, yB);
       } else {  // SM_RESID: r = Y f_H - Y T x; block n-1-k of Y f_H is f_H block k
         const double rA = fH[(long long)kA * m + p] - yA;
-        if (out) out[oA] = rA;
+        if (out) put(out + oA, rA);
         acc += rA * rA;
         if (twin) {
           const double rB = fH[(long long)kB * m + p] - yB;
-          if (out) out[oB] = rB;
+          if (out) put(out + oB, rB);
           acc += rB * rB;
         }
       }
@@ -197,6 +200,181 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
         S->rnorm2 = tot;
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ double-float stencil
+// Mixed-precision MINRES: z_k is float32, the output p = Y T z_k / beta_k is a double-float.
+// Every face term a_f (z_c - z_f) uses the exact float difference (TwoSum) and a TwoProd
+// product with the double-float coefficient, and the terms are summed with the high parts
+// added error-free, so the result carries ~46 significant bits with no float64 instruction per
+// element (GB300 runs float64 at 1/64 of the float32 rate).  Same mirrored-plane walk as the
+// float64 kernel; the dot <Y T z, z> is accumulated unscaled and scaled by 1/beta^2 at the end.
+struct acc_df {
+  float s, t;
+  __device__ __forceinline__ void add(float p, float e) {
+    float ss, err;
+    two_sum(s, p, ss, err);
+    s = ss;
+    t += err + e;
+  }
+  __device__ __forceinline__ void add(df a) { add(a.hi, a.lo); }
+  __device__ __forceinline__ void add_prod(df a, df b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    add(p, e);
+  }
+  __device__ __forceinline__ void add_prod(df a, float b) {
+    float p, e;
+    two_prod(a.hi, b, p, e);
+    e = fmaf(a.lo, b, e);
+    add(p, e);
+  }
+  __device__ __forceinline__ df get() const { return df_from_sum(s, t); }
+};
+
+__device__ __forceinline__ void face_term(acc_df &A, df c, float a, float b) {
+  float dh, dl;
+  two_sum(a, -b, dh, dl);
+  float p, e;
+  two_prod(c.hi, dh, p, e);
+  e = fmaf(c.hi, dl, fmaf(c.lo, dh, e));
+  A.add(p, e);
+}
+
+__device__ __forceinline__ df tauK_df(const float *__restrict__ b, long long p, int i, int j, int mx,
+                                      int my, int dim, df cw, df ce, df cs, df cn, float c) {
+  acc_df A{0.f, 0.f};
+  face_term(A, cw, c, i > 0 ? __ldg(b + p - 1) : 0.f);
+  face_term(A, ce, c, i < mx - 1 ? __ldg(b + p + 1) : 0.f);
+  if (dim == 2) {
+    face_term(A, cs, c, j > 0 ? __ldg(b + p - mx) : 0.f);
+    face_term(A, cn, c, j < my - 1 ? __ldg(b + p + mx) : 0.f);
+  }
+  return A.get();
+}
+
+__global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restrict__ z,
+                                                    df *__restrict__ out, State *S,
+                                                    double *__restrict__ partials, int kc) {
+  __shared__ double red[32];
+  if (!S->active) return;
+  if (S->finish) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && flat_tid() == 0) S->active = 0;
+    return;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
+  const long long m = g.m;
+  const bool valid = (i < mx) && (j < my);
+  const int half = (n + 1) >> 1;
+  const int k0 = blockIdx.z * kc;
+  const int k1 = min(half, k0 + kc);
+  const double sd = S->inv_beta;
+  const df s = df_of_double(sd);
+  acc_df D{0.f, 0.f};
+  if (valid) {
+    const long long p = (long long)j * mx + i;
+    const df cw = df_of_double(g.cx[(long long)j * (mx + 1) + i]);
+    const df ce = df_of_double(g.cx[(long long)j * (mx + 1) + i + 1]);
+    df cs{0.f, 0.f}, cn{0.f, 0.f};
+    if (dim == 2) {
+      cs = df_of_double(g.cy[(long long)j * mx + i]);
+      cn = df_of_double(g.cy[(long long)(j + 1) * mx + i]);
+    }
+    const df th = df_of_double(g.theta), omth = df_of_double(1.0 - g.theta);
+    const bool theta = (g.scheme == ST_THETA);
+    auto center = [&](int k) -> float { return __ldg(z + (long long)k * m + p); };
+    auto stiff = [&](int k, float c) -> df {
+      return tauK_df(z + (long long)k * m, p, i, j, mx, my, dim, cw, ce, cs, cn, c);
+    };
+    auto combine = [&](float c, float c1, float c2, df Kc, df K1) -> df {
+      acc_df A{0.f, 0.f};
+      if (theta) {
+        float dh, dl;
+        two_sum(c, -c1, dh, dl);
+        A.add(dh, dl);
+        A.add_prod(th, Kc);
+        A.add_prod(omth, K1);
+      } else {
+        float pp, e;
+        two_prod(1.5f, c, pp, e);
+        A.add(pp, e);
+        A.add(-2.0f * c1, 0.f);
+        A.add(0.5f * c2, 0.f);
+        A.add(Kc);
+      }
+      return A.get();
+    };
+    const df zero{0.f, 0.f};
+    float a1 = 0.f, a2 = 0.f;
+    df aK1 = zero;
+    float b0 = 0.f, b1 = 0.f;
+    df bK0 = zero;
+    if (k0 > 0) {
+      a1 = center(k0 - 1);
+      if (theta) aK1 = stiff(k0 - 1, a1);
+    }
+    if (!theta && k0 > 1) a2 = center(k0 - 2);
+    {
+      const int kb = n - 1 - k0;
+      b0 = center(kb);
+      if (theta) bK0 = stiff(kb, b0);
+      else if (kb > 0) b1 = center(kb - 1);
+    }
+    for (int kA = k0; kA < k1; ++kA) {
+      const int kB = n - 1 - kA;
+      const float cA = center(kA);
+      const df KA = stiff(kA, cA);
+      const df yA = combine(cA, a1, a2, KA, aK1);
+      if (theta) {
+        aK1 = KA;
+      } else {
+        a2 = a1;
+      }
+      a1 = cA;
+      const bool twin = (kB != kA);
+      const float zB = twin ? b0 : cA;
+      df yB = zero;
+      if (twin) {
+        if (theta) {
+          float nb = 0.f;
+          df nK = zero;
+          if (kB > 0) {
+            nb = center(kB - 1);
+            nK = stiff(kB - 1, nb);
+          }
+          yB = combine(b0, nb, 0.f, bK0, nK);
+          b0 = nb;
+          bK0 = nK;
+        } else {
+          const df KB = stiff(kB, b0);
+          const float nb2 = (kB > 1) ? center(kB - 2) : 0.f;
+          yB = combine(b0, b1, nb2, KB, zero);
+          b0 = b1;
+          b1 = nb2;
+        }
+      }
+      out[(long long)kB * m + p] = df_mul(s, yA);
+      D.add_prod(yA, zB);
+      if (twin) {
+        out[(long long)kA * m + p] = df_mul(s, yB);
+        D.add_prod(yB, cA);
+      }
+    }
+  }
+  const double acc = (double)D.s + (double)D.t;
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  double tot;
+  if (last_block_reduce<kNT>(acc, partials, &S->counter[CNT_STENCIL], nb, bid, red, &tot) &&
+      flat_tid() == 0) {
+    const double alpha = tot * sd * sd;
+    S->alpha = alpha;
+    S->lz_a = alpha / S->beta;
+    S->lz_b = (S->k > 0) ? S->beta / S->beta_prev : 0.0;
   }
 }
 
@@ -343,6 +521,28 @@ cudaError_t launch_stencil(const Geom &g, int mode, const Tz *z, double *out, co
     default:
       return cudaErrorInvalidValue;
   }
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, double *partials,
+                              cudaStream_t st) {
+  Tile t = tile_for(g);
+  dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
+  dim3 grid(t.gx, t.gy, t.nchunk);
+  prof_begin(KC_STENCIL, st);
+  k_stencil_df<<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const double *fH, State *S,
+                            double *partials, cudaStream_t st) {
+  Tile t = tile_for(g);
+  dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
+  dim3 grid(t.gx, t.gy, t.nchunk);
+  prof_begin(KC_RESID, st);
+  k_stencil<double, SM_RESID, df><<<grid, block, 0, st>>>(g, x, r_out, fH, S, partials, t.kc);
   prof_end(st);
   return cudaGetLastError();
 }
