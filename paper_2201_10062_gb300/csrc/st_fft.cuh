@@ -54,6 +54,16 @@ __host__ __device__ __forceinline__ int fft_padded_len(int L) {
   return L + (L >> PadShift<T>::v);
 }
 
+// Distance between consecutive sequences in shared memory: at least the padded length and one
+// more than a multiple of a bank row, so that the same element of neighbouring sequences falls
+// in different banks.
+template <class T>
+__host__ __device__ __forceinline__ int fft_seq_stride(int L) {
+  const int row = 1 << PadShift<T>::v;
+  const int p = fft_padded_len<T>(L);
+  return ((p + row - 1) / row) * row + 1;
+}
+
 // In-register R-point DFT, natural order in and out.
 template <class T, int R>
 struct Dft;
@@ -138,6 +148,59 @@ __host__ __device__ __forceinline__ void stockham_pass(const cpx<T> *src, cpx<T>
 #pragma unroll
     for (int r = 0; r < R; ++r) d[fft_pad<T>(idxD + r * Ns)] = v[r];
   }
+}
+
+// In-place Stockham pass over `count` sequences `stride` slots apart: every thread first loads
+// the R values of each of its 8/R work items (eight complex values per thread for every radix),
+// the block synchronises, then every thread transforms and stores.  Requires
+// count * L <= 8 * nthreads.
+template <class T, int R>
+__device__ __forceinline__ void stockham_pass_inplace(cpx<T> *buf, const cpx<T> *tw, int L,
+                                                      int logL, int Ns, int logNs, int count,
+                                                      int stride, int tid, int nthreads) {
+  constexpr int LOGR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
+  constexpr int TASKS = 8 / R;
+  const int LR = L / R;
+  const int logLR = logL - LOGR;
+  const int twstep = L >> (logNs + LOGR);
+  const int ntask = count * LR;
+  cpx<T> v[TASKS][R];
+#pragma unroll
+  for (int u = 0; u < TASKS; ++u) {
+    const int task = tid + u * nthreads;
+    if (task < ntask) {
+      const int pp = task >> logLR;
+      const int j = task & (LR - 1);
+      const cpx<T> *s = buf + pp * stride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u][r] = s[fft_pad<T>(j + r * LR)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < TASKS; ++u) {
+    const int task = tid + u * nthreads;
+    if (task < ntask) {
+      const int pp = task >> logLR;
+      const int j = task & (LR - 1);
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+        const cpx<T> w1 = tw[k * twstep];
+        cpx<T> w = w1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          v[u][r] = cmulc(v[u][r], w);
+          if (r + 1 < R) w = cmulc(w, w1);
+        }
+      }
+      Dft<T, R>::run(v[u]);
+      const int idxD = ((j >> logNs) << (logNs + LOGR)) + k;
+      cpx<T> *d = buf + pp * stride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) d[fft_pad<T>(idxD + r * Ns)] = v[u][r];
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace st

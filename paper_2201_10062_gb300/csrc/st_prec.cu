@@ -40,98 +40,109 @@ __device__ __forceinline__ bool gate_closed(const State *S) {
 // ------------------------------------------------------------------------------ spatial DST
 // XL = true: lines are rows (contiguous, line l starts at l*len).
 // XL = false: lines are columns of the (my x mx) planes: line l = k*mx + i starts at k*m + i and
-// its elements are mx apart.  A block owns 2*PB consecutive lines (PB complex sequences), loads
-// them coalesced into shared memory as odd extensions, runs the Stockham passes (ping-pong
-// between two padded buffers) and writes the sine coefficients back.
-template <class Tc, class Tin, class Tout, bool XL>
-__global__ void __launch_bounds__(kNT)
-    k_dst_space(const Tin *in, Tout *out, int len, int logL, long long nlines, int mx, long long m,
+// its elements are mx apart.  A block owns 2*PB consecutive lines (PB complex sequences, line
+// 2p in the real part and line 2p+1 in the imaginary part), loads them coalesced into shared
+// memory as odd extensions, runs in-place Stockham passes and writes the sine coefficients.
+constexpr int kNTD = 512;  // threads per spatial-DST block
+
+// Stockham passes for a compile-time length 2^LOGL: radix 8 while at least three stages remain,
+// then one radix-4 or radix-2 pass.
+template <class Tc, int LOGL, int LOGNS>
+struct StockhamPasses {
+  __device__ __forceinline__ static void run(cpx<Tc> *buf, const cpx<Tc> *tws, int PB, int Ls,
+                                             int tid) {
+    constexpr int REM = LOGL - LOGNS;
+    if constexpr (REM > 0) {
+      constexpr int LR = REM >= 3 ? 3 : REM;
+      stockham_pass_inplace<Tc, (1 << LR)>(buf, tws, 1 << LOGL, LOGL, 1 << LOGNS, LOGNS, PB, Ls,
+                                           tid, kNTD);
+      StockhamPasses<Tc, LOGL, LOGNS + LR>::run(buf, tws, PB, Ls, tid);
+    }
+  }
+};
+
+template <class Tc, class Tin, class Tout, bool XL, int LOGL>
+__global__ void __launch_bounds__(kNTD, 2)
+    k_dst_space(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
                 const Tc *tw, int PB, const State *S) {
   if (gate_closed(S)) return;
+  constexpr int logL = LOGL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
   const int half = L >> 1;
-  const int Lp = fft_padded_len<Tc>(L);
+  const int Ls = fft_seq_stride<Tc>(L);
   cpx<Tc> *tws = reinterpret_cast<cpx<Tc> *>(smem_raw);
-  cpx<Tc> *bufA = tws + half;
-  cpx<Tc> *bufB = bufA + (size_t)PB * Lp;
-  Tc *ra = reinterpret_cast<Tc *>(bufA);
+  cpx<Tc> *buf = tws + half;
   const int tid = threadIdx.x;
-  for (int e = tid; e < half; e += kNT) tws[e] = cpx<Tc>{tw[2 * e], tw[2 * e + 1]};
+  for (int e = tid; e < half; e += kNTD) tws[e] = cpx<Tc>{tw[2 * e], tw[2 * e + 1]};
   const long long line0 = (long long)blockIdx.x * 2 * PB;
   const int nl = (int)min((long long)2 * PB, nlines - line0);  // lines present in this block
-  // slots 0 and len+1 of every sequence are zero; absent lines contribute zero components
-  for (int pp = tid; pp < PB; pp += kNT) {
-    bufA[pp * Lp + fft_pad<Tc>(0)] = cpx<Tc>{Tc(0), Tc(0)};
-    bufA[pp * Lp + fft_pad<Tc>(len + 1)] = cpx<Tc>{Tc(0), Tc(0)};
-  }
-  for (int idx = tid; idx < (2 * PB - nl) * len; idx += kNT) {
-    const int lb = nl + idx / len, e = idx % len;
-    const int pp = lb >> 1, comp = lb & 1;
-    ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = Tc(0);
-    ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = Tc(0);
-  }
-  // index maps avoid divisions: len + 1 = L/2 and 2*PB are powers of two
   const int logH = logL - 1;
-  const int logP2 = 31 - __clz(2 * PB);
+  const int logPB = 31 - __clz(PB);
+  // slots 0 and len+1 of every sequence are zero
+  for (int pp = tid; pp < PB; pp += kNTD) {
+    buf[pp * Ls + fft_pad<Tc>(0)] = cpx<Tc>{Tc(0), Tc(0)};
+    buf[pp * Ls + fft_pad<Tc>(len + 1)] = cpx<Tc>{Tc(0), Tc(0)};
+  }
+  // one work item per (sequence, element): both lines of the pair, stored as one complex value
+  // at e+1 and its negative at L-1-e (odd extension).  Index maps avoid divisions: len + 1 =
+  // L/2 and PB are powers of two.
   if (XL) {
-    for (int idx = tid; idx < (nl << logH); idx += kNT) {
-      const int lb = idx >> logH, e = idx & (half - 1);
+    for (int idx = tid; idx < (PB << logH); idx += kNTD) {
+      const int pp = idx >> logH, e = idx & (half - 1);
       if (e >= len) continue;
-      const Tc v = to_real<Tc>(in[(line0 + lb) * len + e]);
-      const int pp = lb >> 1, comp = lb & 1;
-      ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = v;
-      ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = -v;
+      const int la = 2 * pp, lb = la + 1;
+      const Tc a = (la < nl) ? to_real<Tc>(in[(line0 + la) * len + e]) : Tc(0);
+      const Tc b = (lb < nl) ? to_real<Tc>(in[(line0 + lb) * len + e]) : Tc(0);
+      buf[pp * Ls + fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
+      buf[pp * Ls + fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
     }
   } else {
-    for (int idx = tid; idx < (len << logP2); idx += kNT) {
-      const int e = idx >> logP2, lb = idx & (2 * PB - 1);
-      if (lb >= nl) continue;
-      const int l = (int)line0 + lb;
-      const int k = l / mx, i = l - k * mx;
-      const Tc v = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
-      const int pp = lb >> 1, comp = lb & 1;
-      ra[2 * (pp * Lp + fft_pad<Tc>(e + 1)) + comp] = v;
-      ra[2 * (pp * Lp + fft_pad<Tc>(L - 1 - e)) + comp] = -v;
+    for (int idx = tid; idx < (len << logPB); idx += kNTD) {
+      const int e = idx >> logPB, pp = idx & (PB - 1);
+      const int la = 2 * pp, lb = la + 1;
+      Tc a = Tc(0), b = Tc(0);
+      if (la < nl) {
+        const int l = (int)line0 + la;
+        const int k = l / mx, i = l - k * mx;
+        a = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
+      }
+      if (lb < nl) {
+        const int l = (int)line0 + lb;
+        const int k = l / mx, i = l - k * mx;
+        b = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
+      }
+      buf[pp * Ls + fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
+      buf[pp * Ls + fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
     }
   }
   __syncthreads();
-  cpx<Tc> *src = bufA, *dst = bufB;
-  int Ns = 1, logNs = 0, rem = logL;
-  while (rem > 0) {
-    const int lr = rem >= 3 ? 3 : rem;
-    if (lr == 3)
-      stockham_pass<Tc, 8>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
-    else if (lr == 2)
-      stockham_pass<Tc, 4>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
-    else
-      stockham_pass<Tc, 2>(src, dst, tws, L, logL, Ns, logNs, PB, tid, kNT);
-    __syncthreads();
-    cpx<Tc> *t = src;
-    src = dst;
-    dst = t;
-    Ns <<= lr;
-    logNs += lr;
-    rem -= lr;
-  }
+  StockhamPasses<Tc, LOGL, 0>::run(buf, tws, PB, Ls, tid);
   const Tc sc = (Tc)(1.0 / sqrt((double)L));
   if (XL) {
-    for (int idx = tid; idx < (nl << logH); idx += kNT) {
-      const int lb = idx >> logH, e = idx & (half - 1);
+    for (int idx = tid; idx < (PB << logH); idx += kNTD) {
+      const int pp = idx >> logH, e = idx & (half - 1);
       if (e >= len) continue;
-      const cpx<Tc> Z = src[(lb >> 1) * Lp + fft_pad<Tc>(e + 1)];
-      const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
-      out[(line0 + lb) * len + e] = (Tout)v;
+      const cpx<Tc> Z = buf[pp * Ls + fft_pad<Tc>(e + 1)];
+      const int la = 2 * pp, lb = la + 1;
+      if (la < nl) out[(line0 + la) * len + e] = (Tout)(-Z.y * sc);
+      if (lb < nl) out[(line0 + lb) * len + e] = (Tout)(Z.x * sc);
     }
   } else {
-    for (int idx = tid; idx < (len << logP2); idx += kNT) {
-      const int e = idx >> logP2, lb = idx & (2 * PB - 1);
-      if (lb >= nl) continue;
-      const int l = (int)line0 + lb;
-      const int k = l / mx, i = l - k * mx;
-      const cpx<Tc> Z = src[(lb >> 1) * Lp + fft_pad<Tc>(e + 1)];
-      const Tc v = (lb & 1) ? Z.x * sc : -Z.y * sc;
-      out[(long long)k * m + (long long)e * mx + i] = (Tout)v;
+    for (int idx = tid; idx < (len << logPB); idx += kNTD) {
+      const int e = idx >> logPB, pp = idx & (PB - 1);
+      const cpx<Tc> Z = buf[pp * Ls + fft_pad<Tc>(e + 1)];
+      const int la = 2 * pp, lb = la + 1;
+      if (la < nl) {
+        const int l = (int)line0 + la;
+        const int k = l / mx, i = l - k * mx;
+        out[(long long)k * m + (long long)e * mx + i] = (Tout)(-Z.y * sc);
+      }
+      if (lb < nl) {
+        const int l = (int)line0 + lb;
+        const int k = l / mx, i = l - k * mx;
+        out[(long long)k * m + (long long)e * mx + i] = (Tout)(Z.x * sc);
+      }
     }
   }
 }
@@ -373,19 +384,16 @@ __global__ void __launch_bounds__(kNT)
 
 template <class Tc>
 size_t dst_smem(int L, int PB) {
-  return (size_t)(L / 2) * sizeof(cpx<Tc>) +
-         (size_t)2 * PB * fft_padded_len<Tc>(L) * sizeof(cpx<Tc>);
+  return (size_t)(L / 2) * sizeof(cpx<Tc>) + (size_t)PB * fft_seq_stride<Tc>(L) * sizeof(cpx<Tc>);
 }
 
 template <class Tc>
 int dst_pairs(int L) {
-  // two padded buffers per sequence within ~72 KB (three blocks per SM)
-  const size_t per = (size_t)2 * fft_padded_len<Tc>(L) * sizeof(cpx<Tc>);
-  int PB = (int)((72 * 1024 - (size_t)(L / 2) * sizeof(cpx<Tc>)) / per);
-  if (PB > 16) PB = 16;
-  int p2 = 1;  // power of two, so that lines in a block index with shifts
-  while (2 * p2 <= PB) p2 *= 2;
-  return p2;
+  // PB sequences per block: a power of two, at most 16, with PB * L <= 8 * kNTD so that every
+  // pass holds at most eight complex values per thread in registers
+  int PB = 16;
+  while (PB > 1 && PB * L > 8 * kNTD) PB /= 2;
+  return PB;
 }
 
 template <class Tc>
@@ -393,21 +401,37 @@ size_t time_smem(int n, int J) {
   return ((size_t)2 * n * J + 2 * (n + 1) + J) * sizeof(Tc);
 }
 
-template <class Tc, class Tin, class Tout, bool XL>
-cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
-                       long long m, const Tc *tw, const State *S, cudaStream_t st) {
+template <class Tc, class Tin, class Tout, bool XL, int LOGL>
+cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
+                         const Tc *tw, const State *S, cudaStream_t st) {
+  constexpr int L = 1 << LOGL;
   const int PB = dst_pairs<Tc>(L);
   const size_t sm = dst_smem<Tc>(L, PB);
-  int logL = 0;
-  while ((1 << logL) < L) ++logL;
   const long long blocks = (nlines + 2 * PB - 1) / (2 * PB);
-  auto kern = k_dst_space<Tc, Tin, Tout, XL>;
+  auto kern = k_dst_space<Tc, Tin, Tout, XL, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   prof_begin(XL ? KC_DSTX : KC_DSTY, st);
-  kern<<<(unsigned)blocks, kNT, sm, st>>>(in, out, len, logL, nlines, mx, m, tw, PB, S);
+  kern<<<(unsigned)blocks, kNTD, sm, st>>>(in, out, len, nlines, mx, m, tw, PB, S);
   prof_end(st);
   return cudaGetLastError();
+}
+
+template <class Tc, class Tin, class Tout, bool XL>
+cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
+                       long long m, const Tc *tw, const State *S, cudaStream_t st) {
+  switch (L) {
+    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, st);
+    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, st);
+    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, st);
+    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, st);
+    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, st);
+    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, st);
+    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, st);
+    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, st);
+    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class Tc>
