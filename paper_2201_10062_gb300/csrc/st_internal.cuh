@@ -106,6 +106,73 @@ __device__ inline bool last_block_reduce(double part, double *partials, unsigned
   return true;
 }
 
+// ---------------------------------------------------------------- MINRES scalar steps
+// Run by one thread of the last block of the kernel that completes <v, P^-1 v>.
+// Start of a run: beta_1 = sqrt(<b, P^-1 b>).
+__device__ inline void minres_init_scalars_dev(State *S, double E) {
+  if (!(E >= 0.0) || !isfinite(E)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    return;
+  }
+  const double b1 = sqrt(E);
+  S->beta1 = b1;
+  S->beta = b1;
+  S->beta_prev = 1.0;
+  S->inv_beta = (b1 > 0.0) ? 1.0 / b1 : 0.0;
+  S->eta = b1;
+  S->c1 = 1.0;
+  S->s1 = 0.0;
+  S->c2 = 1.0;
+  S->s2 = 0.0;
+  S->k = 0;
+  S->est = 1.0;
+  if (b1 == 0.0) S->finish = 1;
+}
+
+// One Givens step of MINRES (Paige-Saunders) once beta_{k+1}^2 = E is known.
+__device__ inline void minres_givens_dev(State *S, double E) {
+  if (!(E >= 0.0) || !isfinite(E)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    S->xc = 0.0;
+    S->dz = S->d1 = S->d2 = 0.0;
+    return;
+  }
+  const double bnext = sqrt(E);
+  const int k = S->k + 1;
+  const double off = (S->k > 0) ? S->beta : 0.0;
+  const double eps = S->s2 * off;
+  const double dbar = S->c2 * off;
+  const double delta = S->c1 * dbar + S->s1 * S->alpha;
+  const double gbar = -S->s1 * dbar + S->c1 * S->alpha;
+  const double rho = hypot(gbar, bnext);
+  if (!(rho > 0.0) || !isfinite(rho) || !isfinite(S->alpha)) {
+    S->status = ST_ERR_BREAKDOWN;
+    S->finish = 1;
+    S->xc = 0.0;
+    S->dz = S->d1 = S->d2 = 0.0;
+    return;
+  }
+  const double c = gbar / rho, s = bnext / rho;
+  S->dz = 1.0 / (S->beta * rho);
+  S->d1 = -delta / rho;
+  S->d2 = -eps / rho;
+  S->xc = c * S->eta;
+  S->eta = -s * S->eta;
+  S->c2 = S->c1;
+  S->s2 = S->s1;
+  S->c1 = c;
+  S->s1 = s;
+  S->beta_prev = S->beta;
+  S->beta = bnext;
+  S->inv_beta = (bnext > 0.0) ? 1.0 / bnext : 0.0;
+  S->k = k;
+  S->est = fabs(S->eta) / S->beta1;
+  if (S->est <= S->target || bnext == 0.0 || k >= S->maxit) S->finish = 1;
+}
+
+
 // ---------------------------------------------------------------- kernel-class profiler
 // While a handle's profiler is on, each kernel launch is bracketed by CUDA events recorded on
 // the launching stream; the host sums the elapsed times per kernel class afterwards.
@@ -158,7 +225,15 @@ struct PrecPlan {
   int time_blocks_d, time_blocks_f;
   const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
+  const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
 };
+
+bool time_tc_supported(int n);
+size_t time_tc_sop_halves(int n);
+void time_tc_build_sop(int n, unsigned short *out);
+cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
+                           const unsigned short *sop, State *S, int tmode, double *partials,
+                           int gated, cudaStream_t st);
 
 // energy mode of the time kernel's last block
 enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2 };

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -406,6 +407,7 @@ size_t workspace_bytes(const Geom &g, bool mixed) {
   b += sizeof(State);
   b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(double);  // grad faces
   b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
+  if (mixed && time_tc_supported(g.n)) b += time_tc_sop_halves(g.n) * 2;
   return b;
 }
 
@@ -494,16 +496,29 @@ int build_tables(st_handle *h) {
   std::vector<float> hf(nd - o_mux);
   for (size_t i = o_mux; i < nd; ++i) hf[i - o_mux] = (float)hd[i];
   const size_t bytes_d = nd * sizeof(double);
-  const size_t bytes = bytes_d + hf.size() * sizeof(float);
+  const size_t bytes_f = hf.size() * sizeof(float);
+  // fp16 S_n image for the tensor-core time kernel (mixed precision, supported n)
+  std::vector<unsigned short> sop;
+  const char *no_tc = std::getenv("ST_DISABLE_TENSOR_CORES");
+  if (p.precision == ST_MIXED && time_tc_supported(n) && !(no_tc && no_tc[0] == '1')) {
+    sop.resize(time_tc_sop_halves(n));
+    time_tc_build_sop(n, sop.data());
+  }
+  const size_t o_sop = (bytes_d + bytes_f + 255) / 256 * 256;
+  const size_t bytes = o_sop + sop.size() * sizeof(unsigned short);
   ST_TRY(cudaMalloc(&h->tables, bytes));
   ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
-  ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), hf.size() * sizeof(float),
-                    cudaMemcpyHostToDevice));
+  ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice));
+  if (!sop.empty())
+    ST_TRY(cudaMemcpy((char *)h->tables + o_sop, sop.data(), sop.size() * sizeof(unsigned short),
+                      cudaMemcpyHostToDevice));
   const double *D = (const double *)h->tables;
   const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
   h->g.cx = D + o_cx;
   h->g.cy = (g.dim == 2) ? D + o_cy : nullptr;
   PrecPlan &pp = h->pp;
+  pp.sop = sop.empty() ? nullptr
+                       : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
   pp.Lx = Lx;
   pp.Ly = Ly;
   pp.twx_d = D + o_twx;

@@ -247,69 +247,6 @@ __device__ __forceinline__ T inv_symbol(const Spec<T> &sp, int k, T tmu) {
   return rsq(re * re + im * im);
 }
 
-__device__ void minres_init_scalars(State *S, double E) {
-  if (!(E >= 0.0) || !isfinite(E)) {
-    S->status = ST_ERR_BREAKDOWN;
-    S->finish = 1;
-    return;
-  }
-  const double b1 = sqrt(E);
-  S->beta1 = b1;
-  S->beta = b1;
-  S->beta_prev = 1.0;
-  S->inv_beta = (b1 > 0.0) ? 1.0 / b1 : 0.0;
-  S->eta = b1;
-  S->c1 = 1.0;
-  S->s1 = 0.0;
-  S->c2 = 1.0;
-  S->s2 = 0.0;
-  S->k = 0;
-  S->est = 1.0;
-  if (b1 == 0.0) S->finish = 1;
-}
-
-// One Givens step of MINRES (Paige-Saunders) once beta_{k+1}^2 = E is known.
-__device__ void minres_givens(State *S, double E) {
-  if (!(E >= 0.0) || !isfinite(E)) {
-    S->status = ST_ERR_BREAKDOWN;
-    S->finish = 1;
-    S->xc = 0.0;
-    S->dz = S->d1 = S->d2 = 0.0;
-    return;
-  }
-  const double bnext = sqrt(E);
-  const int k = S->k + 1;
-  const double off = (S->k > 0) ? S->beta : 0.0;
-  const double eps = S->s2 * off;
-  const double dbar = S->c2 * off;
-  const double delta = S->c1 * dbar + S->s1 * S->alpha;
-  const double gbar = -S->s1 * dbar + S->c1 * S->alpha;
-  const double rho = hypot(gbar, bnext);
-  if (!(rho > 0.0) || !isfinite(rho) || !isfinite(S->alpha)) {
-    S->status = ST_ERR_BREAKDOWN;
-    S->finish = 1;
-    S->xc = 0.0;
-    S->dz = S->d1 = S->d2 = 0.0;
-    return;
-  }
-  const double c = gbar / rho, s = bnext / rho;
-  S->dz = 1.0 / (S->beta * rho);
-  S->d1 = -delta / rho;
-  S->d2 = -eps / rho;
-  S->xc = c * S->eta;
-  S->eta = -s * S->eta;
-  S->c2 = S->c1;
-  S->s2 = S->s1;
-  S->c1 = c;
-  S->s1 = s;
-  S->beta_prev = S->beta;
-  S->beta = bnext;
-  S->inv_beta = (bnext > 0.0) ? 1.0 / bnext : 0.0;
-  S->k = k;
-  S->est = fabs(S->eta) / S->beta1;
-  if (S->est <= S->target || bnext == 0.0 || k >= S->maxit) S->finish = 1;
-}
-
 template <class Tc, int KT, int JT>
 __global__ void __launch_bounds__(kNT)
     k_time(Tc *data, int n, long long m, int mx, int J, Spec<Tc> sp, State *S,
@@ -375,9 +312,9 @@ __global__ void __launch_bounds__(kNT)
                                &tot) &&
         tid == 0) {
       if (tmode == TM_INIT)
-        minres_init_scalars(S, tot);
+        minres_init_scalars_dev(S, tot);
       else
-        minres_givens(S, tot);
+        minres_givens_dev(S, tot);
     }
   }
 }
@@ -524,8 +461,12 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
                                           gate, st);
     if (e != cudaSuccess) return e;
   }
-  e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials,
-                      tmode == TM_ITER, st);
+  if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
+    e = launch_time_tc(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop, S, tmode, partials,
+                       tmode == TM_ITER, st);
+  else
+    e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials,
+                        tmode == TM_ITER, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),

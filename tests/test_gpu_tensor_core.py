@@ -1,0 +1,58 @@
+"""The tensor-core (tcgen05) time-DST kernel of the mixed-precision preconditioner against the
+oracle and against the float32 FFMA kernel it replaces, on the lengths it supports."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import heat as H
+from workloads import synthetic as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_10062_gb300 as P
+    from paper_2201_10062_gb300 import build
+
+    build.build()
+    P.load_library()
+    return P
+
+
+def _rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# n supported by the tensor-core path (multiples of 32 up to 256); spatial sizes with ragged
+# 32-column tiles (m = 63, 15*31, 63*63, 127*127)
+@pytest.mark.parametrize("dim,mx,my,n,scheme,theta", [
+    (1, 63, 1, 32, "theta", 1.0),
+    (2, 15, 31, 64, "theta", 0.5),
+    (2, 63, 63, 128, "bdf2", 1.0),
+    (2, 127, 127, 256, "theta", 0.5),
+    (2, 31, 31, 96, "theta", 0.3),
+])
+def test_tc_time_dst_matches_oracle_and_ffma(pkg, dim, mx, my, n, scheme, theta):
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=True, seed=n + mx)
+    p = H.Problem.from_workload(w)
+    v = np.random.default_rng(6).standard_normal((n, p.m))
+    ref = H.apply_prec(p, v)
+    spec = pkg.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, "PH", "mixed")
+    s_tc = pkg.Solver(spec)
+    z_tc = s_tc.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    os.environ["ST_DISABLE_TENSOR_CORES"] = "1"
+    try:
+        s_ff = pkg.Solver(spec)
+    finally:
+        del os.environ["ST_DISABLE_TENSOR_CORES"]
+    z_ff = s_ff.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    assert _rel2(z_tc.reshape(n, p.m), ref) <= 2e-5
+    assert _rel2(z_ff.reshape(n, p.m), ref) <= 2e-5
+    assert _rel2(z_tc, z_ff) <= 2e-5
+    s_tc.close()
+    s_ff.close()
