@@ -226,6 +226,7 @@ struct PrecPlan {
   const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
   const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
+  int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
 };
 
 bool time_tc_supported(int n);

@@ -336,7 +336,7 @@ int check_problem(const st_problem *p) {
   if (p->prec != ST_PREC_PH && p->prec != ST_PREC_PTHETA) return ST_ERR_ARG;
   if (p->precision != ST_FP64 && p->precision != ST_MIXED) return ST_ERR_ARG;
   if (p->prec == ST_PREC_PTHETA && p->scheme != ST_THETA) return ST_ERR_ARG;
-  if (p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr) return ST_ERR_ARG;
+  if (p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr && p->dim != 1) return ST_ERR_ARG;
   if (p->a_nodal) {
     const long long cnt = (p->dim == 1) ? (p->mx + 2) : (long long)(p->mx + 2) * (p->my + 2);
     for (long long i = 0; i < cnt; ++i)
@@ -431,27 +431,41 @@ int build_tables(st_handle *h) {
   for (size_t j = 0; j < (g.dim == 2 ? (size_t)my + 1 : 0); ++j)
     for (int i = 0; i < mx; ++i)
       cy[j * mx + i] = tau * 0.5 * (anode((int)j, i + 1) + anode((int)j + 1, i + 1)) / (hy * hy);
-  // diagonal-averaged stiffness matrix (times tau): mean diagonal, mean x- and y-couplings
-  double dsum = 0.0;
+  // diagonal-averaged stiffness matrix (times tau): mean diagonal, mean x- and y-couplings.
+  // The small eigenvalues d - 2 e_x cos - 2 e_y cos cancel strongly, so the sums are compensated
+  // (Neumaier) to keep their own rounding at the level of one ulp.
+  struct CSum {
+    double s = 0.0, c = 0.0;
+    void add(double x) {
+      const double t = s + x;
+      c += (std::fabs(s) >= std::fabs(x)) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    double get() const { return s + c; }
+  };
+  CSum dsum;
   for (int j = 0; j < my; ++j)
     for (int i = 0; i < mx; ++i) {
-      double d = cx[(size_t)j * (mx + 1) + i] + cx[(size_t)j * (mx + 1) + i + 1];
-      if (g.dim == 2) d += cy[(size_t)j * mx + i] + cy[(size_t)(j + 1) * mx + i];
-      dsum += d;
+      dsum.add(cx[(size_t)j * (mx + 1) + i]);
+      dsum.add(cx[(size_t)j * (mx + 1) + i + 1]);
+      if (g.dim == 2) {
+        dsum.add(cy[(size_t)j * mx + i]);
+        dsum.add(cy[(size_t)(j + 1) * mx + i]);
+      }
     }
-  const double dbar = dsum / (double)g.m;
+  const double dbar = dsum.get() / (double)g.m;
   double ex = 0.0, ey = 0.0;
   if (mx > 1) {
-    double s = 0.0;
+    CSum sx;
     for (int j = 0; j < my; ++j)
-      for (int i = 1; i < mx; ++i) s += cx[(size_t)j * (mx + 1) + i];
-    ex = s / ((double)my * (mx - 1));
+      for (int i = 1; i < mx; ++i) sx.add(cx[(size_t)j * (mx + 1) + i]);
+    ex = sx.get() / ((double)my * (mx - 1));
   }
   if (g.dim == 2 && my > 1) {
-    double s = 0.0;
+    CSum sy;
     for (int j = 1; j < my; ++j)
-      for (int i = 0; i < mx; ++i) s += cy[(size_t)j * mx + i];
-    ey = s / ((double)(my - 1) * mx);
+      for (int i = 0; i < mx; ++i) sy.add(cy[(size_t)j * mx + i]);
+    ey = sy.get() / ((double)(my - 1) * mx);
   }
   const double PI = 3.14159265358979323846;
   std::vector<double> mux(mx), muy(my), hk(n), ck(n), sk(n), lh(n), lht(n), sintab(2 * (n + 1));
@@ -517,7 +531,8 @@ int build_tables(st_handle *h) {
   h->g.cx = D + o_cx;
   h->g.cy = (g.dim == 2) ? D + o_cy : nullptr;
   PrecPlan &pp = h->pp;
-  pp.sop = sop.empty() ? nullptr
+  pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr) ? 1 : 0;
+  pp.sop = (sop.empty() || pp.pcr) ? nullptr
                        : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
   pp.Lx = Lx;
   pp.Ly = Ly;

@@ -319,6 +319,90 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
+// ------------------------------------------------------------------------------ P_theta, 1D a(x)
+// Step 2 of the P_theta apply (Sec. 3.1.4) when K has no fast diagonalisation: for every time
+// frequency k solve (lam_H,k I + lam_Htheta,k tau K) z_k = v_k, a tridiagonal SPD system of size
+// mx, by parallel cyclic reduction in shared memory (one block per k).  Each of the
+// ceil(log2 mx) steps eliminates the couplings at distance s = 1, 2, 4, ... from every equation
+// at once; at the end every equation is decoupled and z_i = d_i / b_i.  The block also forms
+// <v_k, z_k>, whose sum over k is <v, P_theta^-1 v> (the time DST is orthogonal).
+template <class Tc>
+__global__ void __launch_bounds__(kNT)
+    k_pcr_ptheta(Tc *data, int n, int mx, const double *__restrict__ cx, Spec<Tc> sp, State *S,
+                 int tmode, double *__restrict__ partials, int gated) {
+  __shared__ double red[32];
+  if (gated && gate_closed(S)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tc *a = reinterpret_cast<Tc *>(smem_raw);
+  Tc *b = a + mx, *c = b + mx, *d = c + mx;
+  Tc *a2 = d + mx, *b2 = a2 + mx, *c2 = b2 + mx, *d2 = c2 + mx;
+  const int k = blockIdx.x;  // 0-based frequency
+  const int tid = threadIdx.x;
+  const Tc lh = sp.lh[k], lt = sp.lht[k];
+  Tc *row = data + (long long)k * mx;
+  for (int i = tid; i < mx; i += kNT) {
+    const Tc w = (Tc)cx[i], e = (Tc)cx[i + 1];  // tau a/h^2 at the faces of node i
+    b[i] = lh + lt * (w + e);
+    a[i] = (i > 0) ? -lt * w : Tc(0);
+    c[i] = (i < mx - 1) ? -lt * e : Tc(0);
+    d[i] = row[i];
+  }
+  __syncthreads();
+  for (int s = 1; s < mx; s <<= 1) {
+    for (int i = tid; i < mx; i += kNT) {
+      Tc na = Tc(0), nb = b[i], nc = Tc(0), nd = d[i];
+      if (i - s >= 0) {
+        const Tc k1 = a[i] / b[i - s];
+        na = -a[i - s] * k1;
+        nb -= c[i - s] * k1;
+        nd -= d[i - s] * k1;
+      }
+      if (i + s < mx) {
+        const Tc k2 = c[i] / b[i + s];
+        nc = -c[i + s] * k2;
+        nb -= a[i + s] * k2;
+        nd -= d[i + s] * k2;
+      }
+      a2[i] = na;
+      b2[i] = nb;
+      c2[i] = nc;
+      d2[i] = nd;
+    }
+    __syncthreads();
+    Tc *t;
+    t = a; a = a2; a2 = t;
+    t = b; b = b2; b2 = t;
+    t = c; c = c2; c2 = t;
+    t = d; d = d2; d2 = t;
+  }
+  double e = 0.0;
+  for (int i = tid; i < mx; i += kNT) {
+    const Tc z = d[i] / b[i];
+    e += (double)row[i] * (double)z;
+    row[i] = z;
+  }
+  if (tmode != TM_NONE) {
+    double tot;
+    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                               &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
+}
+
+// z = convert(v) (float64 or double-float to the transform type), elementwise
+template <class Tc, class Tin>
+__global__ void k_copy_to(long long N, const Tin *v, Tc *z, const State *S, int gated) {
+  if (gated && gate_closed(S)) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x)
+    z[e] = to_real<Tc>(v[e]);
+}
+
 template <class Tc>
 size_t dst_smem(int L, int PB) {
   return (size_t)(L / 2) * sizeof(cpx<Tc>) + (size_t)PB * fft_seq_stride<Tc>(L) * sizeof(cpx<Tc>);
@@ -452,6 +536,26 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
   static_assert(sizeof(Tc) == sizeof(Tout), "in-place stages need Tout == Tc");
   const State *gate = (tmode == TM_ITER) ? S : nullptr;
   cudaError_t e;
+  if (pp.pcr) {
+    // P_theta with a varying 1D coefficient: time DST, tridiagonal solves, time DST
+    Tc *zc = reinterpret_cast<Tc *>(z);
+    const int gated = (tmode == TM_ITER);
+    prof_begin(KC_AUX, st);
+    k_copy_to<Tc, Tin><<<152 * 8, kNT, 0, st>>>(g.N, v, zc, S, gated);
+    prof_end(st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gated, st);
+    if (e != cudaSuccess) return e;
+    const size_t sm = (size_t)8 * g.mx * sizeof(Tc);
+    auto kern = k_pcr_ptheta<Tc>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    prof_begin(KC_TIME, st);
+    kern<<<g.n, kNT, sm, st>>>(zc, g.n, g.mx, g.cx, spec_of<Tc>(pp), S, tmode, partials, gated);
+    prof_end(st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gated, st);
+  }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
   e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), gate,
                                       st);

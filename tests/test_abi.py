@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -54,6 +56,7 @@ def _spec(**kw):
 @pytest.mark.parametrize("bad", [
     dict(mx=14), dict(my=16), dict(dim=3), dict(n=0), dict(n=2000), dict(T=0.0), dict(theta=1.5),
     dict(dim=1, my=3), dict(mx=2047), dict(prec="Ptheta", scheme="bdf2"),
+    dict(prec="Ptheta", a_nodal=np.ones((17, 17))),
 ])
 def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
     from paper_2201_10062_gb300 import ST_ERR_ARG

@@ -44,6 +44,30 @@ def _rel2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+EPS = np.finfo(np.float64).eps
+
+
+def _prec_tol(p):
+    """Tolerance for P^-1 v against the oracle.  With a varying coefficient the averaged-K
+    eigenvalues d - 2 e_x cos - 2 e_y cos cancel by max(mu)/min(mu) at the lowest modes, so
+    last-bit differences in the averages (summation order) are amplified by that ratio."""
+    if p.a_nodal is None:
+        return 1e-12
+    mu = H.averaged_stiffness_eigs(p)
+    return max(1e-12, 16 * EPS * mu.max() / mu.min())
+
+
+def _ptheta_tol32(p):
+    """float32 P_theta tolerance: the per-frequency matrices lam_H + lam_Htheta tau K have
+    condition number up to about (2 + tau mu_max)/(lam_H,min + lam_Htheta,min tau mu_min)."""
+    K = H.stiffness(p)
+    ev = np.linalg.eigvalsh(K.toarray()) if p.m <= 1100 else None
+    lh, lt = H.ptheta_time_eigs(p.n, p.theta)
+    mu_min, mu_max = ev.min(), ev.max()
+    cond = max((lh + lt * p.tau * mu_max) / (lh + lt * p.tau * mu_min))
+    return max(2e-5, 4 * 2.0 ** -24 * cond)
+
+
 # (dim, mx, my, n, scheme, theta, varcoef): ragged tiles (mx odd vs 32-wide blocks), odd and
 # even n, n = 1 and 2, 1D and 2D, constant and varying a.
 CASES = [
@@ -89,13 +113,13 @@ def test_apply_prec_fp64_and_fp32(pkg, case):
     v = np.random.default_rng(2).standard_normal((n, p.m))
     ref = H.apply_prec(p, v)
     z = _h(s.st_apply_prec(_d(v))).reshape(n, p.m)
-    assert _rel_max(z, ref) <= 1e-12
+    assert _rel_max(z, ref) <= _prec_tol(p)
     z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(n, p.m)
     assert _rel2(z32, ref) <= 2e-5
     # in place
     vd = _d(v)
     s.st_apply_prec(vd, out=vd)
-    assert _rel_max(_h(vd).reshape(n, p.m), ref) <= 1e-12
+    assert _rel_max(_h(vd).reshape(n, p.m), ref) <= _prec_tol(p)
     s.close()
 
 
@@ -197,5 +221,77 @@ def test_full_size_2d_crank_nicolson(pkg, precision):
     r = H.flip(fH_or, p.n) - H.apply_op(p, u_h)
     assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-8 * (1 + 1e-6)
     # discretisation error of the manufactured solution stays at the O(tau^2 + h^2) level
+    assert np.max(np.abs(u_h - w.u_exact)) < 1e-3
+    s.close()
+
+
+# ------------------------------------------------------------------ P_theta (Sec. 3.1.4)
+PTHETA_CASES = [
+    (1, 63, 1, 16, 1.0, True),    # varying a in 1D: per-frequency tridiagonal solves (PCR)
+    (1, 255, 1, 33, 0.5, True),
+    (1, 1023, 1, 8, 0.3, True),
+    (1, 31, 1, 24, 0.5, False),   # constant a: spectral scaling
+    (2, 31, 15, 20, 1.0, False),
+]
+
+
+@pytest.mark.parametrize("case", PTHETA_CASES, ids=lambda c: f"{c[0]}d-{c[1]}x{c[2]}-n{c[3]}-th{c[4]}-{'var' if c[5] else 'const'}")
+def test_ptheta_apply(pkg, case):
+    dim, mx, my, n, theta, var = case
+    w = W.small_case(dim, mx, my, n, theta=theta, varcoef=var, seed=mx + 3 * n)
+    p = H.Problem.from_workload(w, prec="Ptheta")
+    s = pkg.Solver(_spec(pkg, w, prec="Ptheta"))
+    v = np.random.default_rng(7).standard_normal((n, p.m))
+    ref = H.apply_ptheta(p, v)
+    z = _h(s.st_apply_prec(_d(v))).reshape(n, p.m)
+    assert _rel_max(z, ref) <= 1e-11
+    z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(n, p.m)
+    assert _rel2(z32, ref) <= (_ptheta_tol32(p) if var else 2e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ptheta_solve(pkg, precision):
+    """P_theta-preconditioned MINRES with a varying 1D coefficient: equal-iteration parity (float64)
+    and error against the converged oracle solution (mixed)."""
+    w = W.small_case(1, 255, 1, 64, theta=1.0, varcoef=True, seed=41)
+    p = H.Problem.from_workload(w, prec="Ptheta")
+    fH = H.rhs(p, w.f, w.u0)
+    s = pkg.Solver(_spec(pkg, w, prec="Ptheta", precision=precision))
+    if precision == "fp64":
+        u, st = s.st_solve(_d(fH), tol=0.0, maxit=9, allow_not_converged=True)
+        x_or, info = H.solve(p, fH, tol=0.0, maxit=9, rule="est")
+        assert st["iterations"] == info["iterations"] == 9
+        assert _rel2(_h(u).reshape(p.n, p.m), x_or) <= 1e-10
+        u, st = s.st_solve(_d(fH), tol=1e-8, maxit=200)
+        x_or, info = H.solve(p, fH, tol=1e-8, maxit=200)
+        assert abs(st["iterations"] - info["iterations"]) <= 1
+    else:
+        x_ref, info = H.solve(p, fH, tol=1e-13, maxit=400)
+        u, st = s.st_solve(_d(fH), tol=1e-10, maxit=400)
+        assert st["true_rel_res"] <= 1e-10
+        assert _rel2(_h(u).reshape(p.n, p.m), x_ref) <= 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_2d_varcoef_bdf2(pkg, precision):
+    """2D 511^2, n = 128, BDF2, seeded 8x8-mode coefficient field: the solve reaches 1e-8 (checked
+    with the oracle's operator) and the manufactured solution is recovered to discretisation
+    accuracy; sampled operator / preconditioner parity on the full vector (float64 handle)."""
+    w = W.config_2d_varcoef_bdf2()
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w, precision=precision))
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0), _d(w.u_prev))
+    fH_or = H.rhs(p, w.f, w.u0, w.u_prev)
+    assert _rel_max(_h(fH).reshape(p.n, p.m), fH_or) <= 1e-13
+    if precision == "fp64":
+        v = np.random.default_rng(8).standard_normal((p.n, p.m))
+        assert _rel_max(_h(s.st_apply_op(_d(v))).reshape(p.n, p.m), H.apply_op(p, v)) <= 1e-13
+        assert _rel_max(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m), H.apply_prec(p, v)) <= _prec_tol(p)
+    u, st = s.st_solve(fH, tol=1e-8, maxit=400)
+    u_h = _h(u).reshape(p.n, p.m)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, u_h)
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-8 * (1 + 1e-6)
     assert np.max(np.abs(u_h - w.u_exact)) < 1e-3
     s.close()
