@@ -135,6 +135,14 @@ int st_solve_host(st_handle *h, const double *fH_host, double *u_host, double to
 int st_solve_transpose(st_handle *h, const double *g_dev, double *lam_dev, double tol, int maxit,
                        st_stats *stats);
 
+/* Adjoint of st_assemble_rhs: given lam = dL/df_H (N entries, e.g. from st_solve_transpose),
+ * writes dL/df (grad_f_dev, (n+1) x m), dL/du0 (grad_u0_dev, m, may be NULL) and, for BDF2,
+ * dL/du^(-1) (grad_uprev_dev, m, may be NULL; zeros for theta).  From the rhs of Sec. 1:
+ * theta: df^(k) = theta tau lam_k + (1-theta) tau lam_{k+1}, du0 = (I - (1-theta) tau K) lam_1;
+ * BDF2: df^(k) = tau lam_k (k >= 1), du0 = 2 lam_1 - lam_2/2, du^(-1) = -lam_1/2. */
+int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double *grad_u0_dev,
+                double *grad_uprev_dev);
+
 /* Gradient of L(a) through T(a) u = f_H(a) given the adjoint lam = T^-T dL/du: for theta,
  * dL/da = -tau sum_k lam_k^T (dK/da) (theta u_k + (1-theta) u_{k-1}) with u_0 = u0 (BDF2: u_k);
  * each face value is the mean of its two nodal values, so half of each face term goes to each

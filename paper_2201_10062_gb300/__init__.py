@@ -27,7 +27,7 @@ EXPORTS = (
     "st_setup", "st_destroy", "st_workspace_bytes", "st_assemble_rhs", "st_apply_op",
     "st_apply_prec", "st_apply_prec_f32", "st_solve", "st_solve_host", "st_solve_transpose",
     "st_grad_a", "st_strerror", "st_version", "st_profile_begin", "st_profile_end",
-    "st_kernel_class_name", "st_residual_noalloc",
+    "st_kernel_class_name", "st_residual_noalloc", "st_grad_rhs",
 )
 KERNEL_CLASSES = ("stencil", "lanczos", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("st_solve", "st_solve_host", "st_solve_transpose"):
         getattr(lib, name).argtypes = [P, P, P, D, I, ctypes.POINTER(StStats)]
         getattr(lib, name).restype = I
+    lib.st_grad_rhs.argtypes = [P, P, P, P, P]
+    lib.st_grad_rhs.restype = I
     lib.st_grad_a.argtypes = [P, P, P, P, P]
     lib.st_grad_a.restype = I
     lib.st_strerror.argtypes = [I]
@@ -303,6 +305,19 @@ class Solver:
         _check(self.lib.st_profile_end(self.h, arr, len(KERNEL_CLASSES)), "st_profile_end")
         return {KERNEL_CLASSES[i]: {"launches": arr[i].launches, "timed": arr[i].timed,
                                     "ms": arr[i].ms} for i in range(len(KERNEL_CLASSES))}
+
+    def st_grad_rhs(self, lam):
+        """(dL/df (n+1, m), dL/du0 (m,), dL/du^(-1) (m,)) from lam = dL/df_H."""
+        import torch
+
+        s = self.spec
+        gf = self.empty(s.n + 1, s.m)
+        gu0 = self.empty(s.m)
+        gup = self.empty(s.m)
+        _check(self.lib.st_grad_rhs(self.h, _dev_ptr(lam, torch.float64, s.N),
+                                    _dev_ptr(gf, torch.float64), _dev_ptr(gu0, torch.float64),
+                                    _dev_ptr(gup, torch.float64)), "st_grad_rhs")
+        return gf, gu0, gup
 
     def st_grad_a(self, lam, u, u0, out=None):
         import torch

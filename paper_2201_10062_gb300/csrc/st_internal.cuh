@@ -211,6 +211,8 @@ int stencil_blocks(const Geom &g);
 
 cudaError_t launch_rhs(const Geom &g, const double *f, const double *u0, const double *uprev,
                        const double *extra, double *fH, cudaStream_t st);
+cudaError_t launch_grad_rhs(const Geom &g, const double *lam, double *gf, double *gu0,
+                            double *gup, cudaStream_t st);
 cudaError_t launch_grad_a(const Geom &g, const double *lam, const double *u, const double *u0,
                           double *gface_x, double *gface_y, double *grad, cudaStream_t st);
 

@@ -1059,6 +1059,15 @@ int st_solve_transpose(st_handle *h, const double *g_dev, double *lam_dev, doubl
   return r;
 }
 
+int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double *grad_u0_dev,
+                double *grad_uprev_dev) {
+  if (!h || !lam_dev || !grad_f_dev) return ST_ERR_ARG;
+  ProfScope prof_scope(h);
+  ST_TRY(cudaSetDevice(h->device));
+  ST_TRY(launch_grad_rhs(h->g, lam_dev, grad_f_dev, grad_u0_dev, grad_uprev_dev, h->stream));
+  return ST_OK;
+}
+
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev) {
   if (!h || !lam_dev || !u_dev || !u0_dev || !grad_dev) return ST_ERR_ARG;

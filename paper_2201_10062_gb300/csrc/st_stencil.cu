@@ -413,6 +413,51 @@ __global__ void k_rhs(Geom g, const double *__restrict__ f, const double *__rest
   }
 }
 
+// Adjoint of the right-hand-side assembly: given lam = dL/df_H, the gradients with respect to
+// f (at t_0..t_n), u0 and (BDF2) u^(-1).
+//   theta: f_H block k = theta tau f^(k) + (1-theta) tau f^(k-1), block 1 += (I - (1-theta) tau K) u0
+//   BDF2:  f_H block k = tau f^(k), block 1 += 2 u0 - u^(-1)/2, block 2 += -u0/2
+__global__ void k_grad_rhs(Geom g, const double *__restrict__ lam, double *__restrict__ gf,
+                           double *__restrict__ gu0, double *__restrict__ gup) {
+  const long long m = g.m, total = (long long)(g.n + 1) * m;
+  const int n = g.n;
+  const double tau = g.tau;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / m, p = e - k * m;  // f^(k), k = 0..n
+    double r = 0.0;
+    if (g.scheme == ST_THETA) {
+      if (k >= 1) r += g.theta * tau * lam[(k - 1) * m + p];
+      if (k <= n - 1) r += (1.0 - g.theta) * tau * lam[k * m + p];
+    } else {
+      if (k >= 1) r = tau * lam[(k - 1) * m + p];
+    }
+    gf[e] = r;
+    if (k == 0) {
+      const double l1 = lam[p];
+      if (g.scheme == ST_THETA) {
+        if (gu0) {
+          const int i = (int)(p % g.mx), j = (int)(p / g.mx);
+          const double cw = g.cx[(long long)j * (g.mx + 1) + i];
+          const double ce = g.cx[(long long)j * (g.mx + 1) + i + 1];
+          double cs = 0.0, cn = 0.0;
+          if (g.dim == 2) {
+            cs = g.cy[(long long)j * g.mx + i];
+            cn = g.cy[(long long)(j + 1) * g.mx + i];
+          }
+          const double Kl = tauK(lam, p, i, j, g.mx, g.my, g.dim, cw, ce, cs, cn, l1);
+          gu0[p] = l1 - (1.0 - g.theta) * Kl;
+        }
+        if (gup) gup[p] = 0.0;
+      } else {
+        const double l2 = (n > 1) ? lam[m + p] : 0.0;
+        if (gu0) gu0[p] = 2.0 * l1 - 0.5 * l2;
+        if (gup) gup[p] = -0.5 * l1;
+      }
+    }
+  }
+}
+
 // Face terms of dL/da: g_face = -(tau/h^2) sum_k (lam_p - lam_q)(w_p - w_q), with
 // w_k = theta u_k + (1-theta) u_{k-1} (u_{-1} = u0) for theta and w_k = u_k for BDF2.
 // Thread (j, i) of the (my+1) x (mx+1) face grid owns x-face (j, i) [between nodes (j,i-1) and
@@ -558,6 +603,16 @@ cudaError_t launch_rhs(const Geom &g, const double *f, const double *u0, const d
   if (blocks > 152LL * 16) blocks = 152LL * 16;
   prof_begin(KC_AUX, st);
   k_rhs<<<(unsigned)blocks, 256, 0, st>>>(g, f, u0, uprev, extra, fH);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_rhs(const Geom &g, const double *lam, double *gf, double *gu0,
+                            double *gup, cudaStream_t st) {
+  long long blocks = ((long long)(g.n + 1) * g.m + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  prof_begin(KC_AUX, st);
+  k_grad_rhs<<<(unsigned)blocks, 256, 0, st>>>(g, lam, gf, gu0, gup);
   prof_end(st);
   return cudaGetLastError();
 }
