@@ -151,6 +151,24 @@ int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double 
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev);
 
+/* Batched solves: `count` independent instances (each its own st_problem, precision ST_MIXED;
+ * sizes, theta/BDF2 and a(x) may all differ) solved concurrently, one stream per instance, by a
+ * single CUDA graph that the call relaunches until every instance has converged.  The refinement
+ * decisions (restart or stop) are taken on the device, so nothing inside the graph waits for the
+ * host.  st_setup_batch allocates every instance's workspace (probs[i].stream is ignored; the
+ * batch works on `stream`).  st_solve_batch: fH_devs[i], u_devs[i] as in st_solve; tol and maxit
+ * apply to every instance; stats (count entries, may be NULL) per instance; returns ST_OK when
+ * every instance converged, else the first failure code.  The graph is captured on the first
+ * solve and again whenever the buffer pointers change.  Synchronises `stream` before returning. */
+typedef struct st_batch st_batch;
+int st_setup_batch(const st_problem *probs, int count, void *stream, st_batch **out);
+int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_devs, double tol,
+                   int maxit, st_stats *stats);
+/* Handle of instance i (owned by the batch) for st_assemble_rhs, st_apply_op, ...; those calls
+ * run on the batch's `stream`. */
+int st_batch_instance(st_batch *b, int i, st_handle **out);
+void st_destroy_batch(st_batch *b);
+
 /* Residual check that allocates nothing (the paper has no counterpart; it is a deployment aid).
  * Some callers cannot allocate device memory at the moment they need a residual: code that is
  * recording a CUDA graph, latency-critical loops where cudaFree's implicit device synchronisation

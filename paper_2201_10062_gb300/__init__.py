@@ -27,7 +27,8 @@ EXPORTS = (
     "st_setup", "st_destroy", "st_workspace_bytes", "st_assemble_rhs", "st_apply_op",
     "st_apply_prec", "st_apply_prec_f32", "st_solve", "st_solve_host", "st_solve_transpose",
     "st_grad_a", "st_strerror", "st_version", "st_profile_begin", "st_profile_end",
-    "st_kernel_class_name", "st_residual_noalloc", "st_grad_rhs",
+    "st_kernel_class_name", "st_residual_noalloc", "st_grad_rhs", "st_setup_batch",
+    "st_solve_batch", "st_batch_instance", "st_destroy_batch",
 )
 KERNEL_CLASSES = ("stencil", "lanczos", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
@@ -89,6 +90,15 @@ def load_library(path: str = LIB_PATH):
     for name in ("st_solve", "st_solve_host", "st_solve_transpose"):
         getattr(lib, name).argtypes = [P, P, P, D, I, ctypes.POINTER(StStats)]
         getattr(lib, name).restype = I
+    lib.st_setup_batch.argtypes = [ctypes.POINTER(StProblem), I, P, ctypes.POINTER(P)]
+    lib.st_setup_batch.restype = I
+    lib.st_solve_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I,
+                                   ctypes.POINTER(StStats)]
+    lib.st_solve_batch.restype = I
+    lib.st_batch_instance.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.st_batch_instance.restype = I
+    lib.st_destroy_batch.argtypes = [P]
+    lib.st_destroy_batch.restype = None
     lib.st_grad_rhs.argtypes = [P, P, P, P, P]
     lib.st_grad_rhs.restype = I
     lib.st_grad_a.argtypes = [P, P, P, P, P]
@@ -331,7 +341,73 @@ class Solver:
         return out
 
 
+class _InstanceView(Solver):
+    """A Solver whose handle belongs to a BatchSolver (not destroyed on close)."""
+
+    def __init__(self, spec, handle, stream, device):
+        self.spec = spec
+        self.stream = stream
+        self.device = device
+        self.h = handle
+        self.lib = load_library()
+
+    def close(self):
+        self.h = None
+
+
+class BatchSolver:
+    """Many independent mixed-precision instances solved by one captured CUDA graph."""
+
+    def __init__(self, specs, stream=None):
+        import torch
+
+        self.lib = load_library()
+        self.specs = list(specs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        arr = (StProblem * len(self.specs))()
+        self._keep = []
+        for i, sp in enumerate(self.specs):
+            if sp.precision != "mixed":
+                raise ValueError("batched solves run in mixed precision")
+            p, keep = sp.to_c()
+            arr[i] = p
+            self._keep.append(keep)
+        self.b = ctypes.c_void_p()
+        _check(self.lib.st_setup_batch(arr, len(self.specs), ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(self.b)), "st_setup_batch")
+
+    def instance(self, i) -> Solver:
+        h = ctypes.c_void_p()
+        _check(self.lib.st_batch_instance(self.b, int(i), ctypes.byref(h)), "st_batch_instance")
+        return _InstanceView(self.specs[i], h, self.stream, self.device)
+
+    def st_solve_batch(self, fHs, tol=1e-8, maxit=500, outs=None, allow_not_converged=False):
+        import torch
+
+        n = len(self.specs)
+        outs = outs if outs is not None else [torch.empty_like(f) for f in fHs]
+        fp = (ctypes.c_void_p * n)(*[_dev_ptr(f, torch.float64, sp.N).value for f, sp in zip(fHs, self.specs)])
+        up = (ctypes.c_void_p * n)(*[_dev_ptr(u, torch.float64, sp.N).value for u, sp in zip(outs, self.specs)])
+        stats = (StStats * n)()
+        ok = (ST_OK, ST_ERR_NOT_CONVERGED) if allow_not_converged else (ST_OK,)
+        _check(self.lib.st_solve_batch(self.b, fp, up, float(tol), int(maxit), stats),
+               "st_solve_batch", ok)
+        return outs, [stats[i].as_dict() for i in range(n)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.st_destroy_batch(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 __all__ = [
-    "ProblemSpec", "Solver", "SolverError", "StProblem", "StStats", "load_library", "strerror",
+    "ProblemSpec", "Solver", "BatchSolver", "SolverError", "StProblem", "StStats", "load_library", "strerror",
     "st_setup", "st_destroy", "st_workspace_bytes", "EXPORTS", "LIB_PATH",
 ]

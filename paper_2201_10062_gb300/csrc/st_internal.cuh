@@ -50,6 +50,12 @@ struct State {
   int active, finish, status;
   int pad;
   unsigned int counter[8];             // completion counters of the last-block reductions
+  // device-driven refinement (batched solves): after an inner run finishes, the residual
+  // kernel decides between done and a restart of the inner run
+  double tol_outer;                    // requested ||r||/||b||
+  double rho;                          // last true relative residual
+  int done, restart, total, outer, maxit_total;
+  int pad2;
 };
 
 enum { CNT_STENCIL = 0, CNT_TIME = 1, CNT_RESID = 2, CNT_NORM = 3 };
@@ -127,6 +133,8 @@ __device__ inline void minres_init_scalars_dev(State *S, double E) {
   S->s2 = 0.0;
   S->k = 0;
   S->est = 1.0;
+  S->active = 1;  // `restart` stays set until the run's first stencil: the inverse transforms of
+                  // this preconditioner pass are still gated on it
   if (b1 == 0.0) S->finish = 1;
 }
 
@@ -202,7 +210,7 @@ void prof_end(cudaStream_t st);
 
 // ---------------------------------------------------------------- launch-side declarations
 // stencil modes
-enum { SM_MINRES = 0, SM_APPLY = 1, SM_RESID = 2, SM_TRANSPOSE_APPLY = 3 };
+enum { SM_MINRES = 0, SM_APPLY = 1, SM_RESID = 2, SM_TRANSPOSE_APPLY = 3, SM_RESID_OUTER = 4 };
 
 template <class Tz>
 cudaError_t launch_stencil(const Geom &g, int mode, const Tz *z, double *out, const double *fH,
@@ -236,10 +244,23 @@ size_t time_tc_sop_halves(int n);
 void time_tc_build_sop(int n, unsigned short *out);
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
-                           int gated, cudaStream_t st);
+                           int gk, cudaStream_t st);
 
 // energy mode of the time kernel's last block
-enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2 };
+enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2, TM_RESTART = 3 };
+
+// Which state flag a preconditioner kernel waits for: none (standalone applies and the first
+// start), `active` (inside a MINRES iteration) or `restart` (device-driven restart of an inner
+// run in a batched solve).
+enum { GK_NONE = 0, GK_ACTIVE = 1, GK_RESTART = 2 };
+inline int gate_kind_of(int tmode) {
+  return tmode == TM_ITER ? GK_ACTIVE : (tmode == TM_RESTART ? GK_RESTART : GK_NONE);
+}
+__device__ __forceinline__ bool gate_closed(const State *S, int gk) {
+  if (gk == GK_ACTIVE) return !S->active;
+  if (gk == GK_RESTART) return !S->restart;
+  return false;
+}
 
 template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
@@ -251,6 +272,10 @@ cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, do
                               cudaStream_t st);
 cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const double *fH, State *S,
                             double *partials, cudaStream_t st);
+// device-driven refinement step: runs only when the inner run has finished and the solve is not
+// done; r = Y f_H - Y T x into r_out and, in the last block, the done/restart decision
+cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const double *fH,
+                               State *S, double *partials, cudaStream_t st);
 cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
                               cudaStream_t st);
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
@@ -278,3 +303,29 @@ cudaError_t launch_norm2(long long N, const double *v, State *S, double *partial
                          cudaStream_t st);
 
 }  // namespace st
+
+// ------------------------------------------------------------------ handle (C type of st_handle)
+struct st_handle {
+  st_problem prob;
+  st::Geom g;
+  st::PrecPlan pp;
+  cudaStream_t stream;
+  int device;
+  bool mixed;
+  // device memory
+  void *tables;          // face coefficients, spectral tables, twiddles (one allocation)
+  double *V[2];          // Lanczos vectors vhat
+  void *Z[2];            // preconditioned vectors (double, or float in ST_MIXED)
+  double *D[2];          // MINRES directions
+  double *q;             // stencil output (a df array in ST_MIXED)
+  st::df *Xdf;           // ST_MIXED: double-float solution accumulator
+  double *partials;      // per-block partial sums
+  st::State *S;          // device scalars
+  double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
+  double *gfx, *gfy;     // face-gradient scratch for st_grad_a
+  st::State *hS;         // pinned host mirror of S
+  int partials_len;
+  st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)
+};
+
+

@@ -274,30 +274,6 @@ cudaError_t launch_norm2(long long N, const double *v, State *S, double *partial
 
 }  // namespace st
 
-// ------------------------------------------------------------------------------------ handle
-struct st_handle {
-  st_problem prob;
-  Geom g;
-  PrecPlan pp;
-  cudaStream_t stream;
-  int device;
-  bool mixed;
-  // device memory
-  void *tables;          // face coefficients, spectral tables, twiddles (one allocation)
-  double *V[2];          // Lanczos vectors vhat
-  void *Z[2];            // preconditioned vectors (double, or float in ST_MIXED)
-  double *D[2];          // MINRES directions
-  double *q;             // stencil output (a df array in ST_MIXED)
-  df *Xdf;               // ST_MIXED: double-float solution accumulator
-  double *partials;      // per-block partial sums
-  State *S;              // device scalars
-  double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
-  double *gfx, *gfy;     // face-gradient scratch for st_grad_a
-  State *hS;             // pinned host mirror of S
-  int partials_len;
-  Prof prof;             // kernel-class timing (off unless st_profile_begin was called)
-};
-
 namespace {
 // Makes the handle's profiler the current one for the duration of a C-ABI call.
 struct ProfScope {

@@ -31,11 +31,8 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // Inside a MINRES iteration only the first kernel (the stencil) looks at `finish`; it clears
 // `active` so that the rest of that iteration is skipped.  The preconditioner kernels check
-// `active` alone, so an iteration whose time kernel raises `finish` still completes z_{k+1}
-// (needed if the stopping rule later decides to continue).
-__device__ __forceinline__ bool gate_closed(const State *S) {
-  return S != nullptr && !S->active;
-}
+// `active` alone (gate_closed, GK_ACTIVE), so an iteration whose time kernel raises `finish`
+// still completes z_{k+1} (needed if the stopping rule later decides to continue).
 
 // ------------------------------------------------------------------------------ spatial DST
 // XL = true: lines are rows (contiguous, line l starts at l*len).
@@ -64,8 +61,8 @@ struct StockhamPasses {
 template <class Tc, class Tin, class Tout, bool XL, int LOGL>
 __global__ void __launch_bounds__(kNTD, 2)
     k_dst_space(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
-                const Tc *tw, int PB, const State *S) {
-  if (gate_closed(S)) return;
+                const Tc *tw, int PB, const State *S, int gk) {
+  if (gate_closed(S, gk)) return;
   constexpr int logL = LOGL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
@@ -250,9 +247,9 @@ __device__ __forceinline__ T inv_symbol(const Spec<T> &sp, int k, T tmu) {
 template <class Tc, int KT, int JT>
 __global__ void __launch_bounds__(kNT)
     k_time(Tc *data, int n, long long m, int mx, int J, Spec<Tc> sp, State *S,
-           int tmode, int tkind, double *__restrict__ partials, int gated) {
+           int tmode, int tkind, double *__restrict__ partials, int gk) {
   __shared__ double red[32];
-  if (gated && gate_closed(S)) return;
+  if (gate_closed(S, gk)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tc *X = reinterpret_cast<Tc *>(smem_raw);
   Tc *Y = X + (size_t)n * J;
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(kNT)
     if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
                                &tot) &&
         tid == 0) {
-      if (tmode == TM_INIT)
+      if (tmode == TM_INIT || tmode == TM_RESTART)
         minres_init_scalars_dev(S, tot);
       else
         minres_givens_dev(S, tot);
@@ -329,9 +326,9 @@ __global__ void __launch_bounds__(kNT)
 template <class Tc>
 __global__ void __launch_bounds__(kNT)
     k_pcr_ptheta(Tc *data, int n, int mx, const double *__restrict__ cx, Spec<Tc> sp, State *S,
-                 int tmode, double *__restrict__ partials, int gated) {
+                 int tmode, double *__restrict__ partials, int gk) {
   __shared__ double red[32];
-  if (gated && gate_closed(S)) return;
+  if (gate_closed(S, gk)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tc *a = reinterpret_cast<Tc *>(smem_raw);
   Tc *b = a + mx, *c = b + mx, *d = c + mx;
@@ -386,7 +383,7 @@ __global__ void __launch_bounds__(kNT)
     if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
                                &tot) &&
         tid == 0) {
-      if (tmode == TM_INIT)
+      if (tmode == TM_INIT || tmode == TM_RESTART)
         minres_init_scalars_dev(S, tot);
       else
         minres_givens_dev(S, tot);
@@ -396,8 +393,8 @@ __global__ void __launch_bounds__(kNT)
 
 // z = convert(v) (float64 or double-float to the transform type), elementwise
 template <class Tc, class Tin>
-__global__ void k_copy_to(long long N, const Tin *v, Tc *z, const State *S, int gated) {
-  if (gated && gate_closed(S)) return;
+__global__ void k_copy_to(long long N, const Tin *v, Tc *z, const State *S, int gk) {
+  if (gate_closed(S, gk)) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
        e += (long long)gridDim.x * blockDim.x)
     z[e] = to_real<Tc>(v[e]);
@@ -424,7 +421,7 @@ size_t time_smem(int n, int J) {
 
 template <class Tc, class Tin, class Tout, bool XL, int LOGL>
 cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
-                         const Tc *tw, const State *S, cudaStream_t st) {
+                         const Tc *tw, const State *S, int gk, cudaStream_t st) {
   constexpr int L = 1 << LOGL;
   const int PB = dst_pairs<Tc>(L);
   const size_t sm = dst_smem<Tc>(L, PB);
@@ -433,24 +430,24 @@ cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, in
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   prof_begin(XL ? KC_DSTX : KC_DSTY, st);
-  kern<<<(unsigned)blocks, kNTD, sm, st>>>(in, out, len, nlines, mx, m, tw, PB, S);
+  kern<<<(unsigned)blocks, kNTD, sm, st>>>(in, out, len, nlines, mx, m, tw, PB, S, gk);
   prof_end(st);
   return cudaGetLastError();
 }
 
 template <class Tc, class Tin, class Tout, bool XL>
 cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
-                       long long m, const Tc *tw, const State *S, cudaStream_t st) {
+                       long long m, const Tc *tw, const State *S, int gk, cudaStream_t st) {
   switch (L) {
-    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, st);
-    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, st);
-    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, st);
-    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, st);
-    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, st);
-    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, st);
-    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, st);
-    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, st);
-    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, st);
+    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, gk, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -487,7 +484,7 @@ int time_J(int n) {
 
 template <class Tc>
 cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, int tmode,
-                        int tkind, double *partials, int gated, cudaStream_t st) {
+                        int tkind, double *partials, int gk, cudaStream_t st) {
   const int J = time_J<Tc>(g.n);
   const size_t sm = time_smem<Tc>(g.n, J);
   const long long blocks = (g.m + J - 1) / J;
@@ -497,7 +494,7 @@ cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, i
   if (e != cudaSuccess) return e;
   prof_begin(KC_TIME, st);
   kern<<<(unsigned)blocks, kNT, sm, st>>>(data, g.n, g.m, g.mx, J, sp, S, tmode, tkind, partials,
-                                          gated);
+                                          gk);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -534,51 +531,50 @@ template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
                         int tmode, double *partials, cudaStream_t st) {
   static_assert(sizeof(Tc) == sizeof(Tout), "in-place stages need Tout == Tc");
-  const State *gate = (tmode == TM_ITER) ? S : nullptr;
+  const int gk = gate_kind_of(tmode);
   cudaError_t e;
   if (pp.pcr) {
     // P_theta with a varying 1D coefficient: time DST, tridiagonal solves, time DST
     Tc *zc = reinterpret_cast<Tc *>(z);
-    const int gated = (tmode == TM_ITER);
     prof_begin(KC_AUX, st);
-    k_copy_to<Tc, Tin><<<152 * 8, kNT, 0, st>>>(g.N, v, zc, S, gated);
+    k_copy_to<Tc, Tin><<<152 * 8, kNT, 0, st>>>(g.N, v, zc, S, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gated, st);
+    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, st);
     if (e != cudaSuccess) return e;
     const size_t sm = (size_t)8 * g.mx * sizeof(Tc);
     auto kern = k_pcr_ptheta<Tc>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     prof_begin(KC_TIME, st);
-    kern<<<g.n, kNT, sm, st>>>(zc, g.n, g.mx, g.cx, spec_of<Tc>(pp), S, tmode, partials, gated);
+    kern<<<g.n, kNT, sm, st>>>(zc, g.n, g.mx, g.cx, spec_of<Tc>(pp), S, tmode, partials, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gated, st);
+    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, st);
   }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
-  e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), gate,
+  e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S, gk,
                                       st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          gate, st);
+                                          S, gk, st);
     if (e != cudaSuccess) return e;
   }
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
-    e = launch_time_tc(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop, S, tmode, partials,
-                       tmode == TM_ITER, st);
+    e = launch_time_tc(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop, S, tmode, partials, gk,
+                       st);
   else
-    e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials,
-                        tmode == TM_ITER, st);
+    e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials, gk,
+                        st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          gate, st);
+                                          S, gk, st);
     if (e != cudaSuccess) return e;
   }
-  return launch_dst<Tc, Tout, Tout, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true),
-                                          gate, st);
+  return launch_dst<Tc, Tout, Tout, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
+                                          gk, st);
 }
 
 template cudaError_t launch_prec<double, double, double>(const Geom &, const PrecPlan &,

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
       return;
     }
   }
+  if (MODE == SM_RESID_OUTER && !(S->finish && !S->done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
       } else if (MODE == SM_APPLY) {
         put(out + oA, yA);
         if (twin) put(out + oB, yB);
-      } else {  // SM_RESID: r = Y f_H - Y T x; block n-1-k of Y f_H is f_H block k
+      } else {  // SM_RESID(_OUTER): r = Y f_H - Y T x; block n-1-k of Y f_H is f_H block k
         const double rA = fH[(long long)kA * m + p] - yA;
         if (out) put(out + oA, rA);
         acc += rA * rA;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
       }
     }
   }
-  if (MODE == SM_MINRES || MODE == SM_RESID) {
+  if (MODE == SM_MINRES || MODE == SM_RESID || MODE == SM_RESID_OUTER) {
     const int nb = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     double tot;
@@ -198,6 +199,27 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
         S->lz_b = (S->k > 0) ? S->beta / S->beta_prev : 0.0;
       } else {
         S->rnorm2 = tot;
+        if (MODE == SM_RESID_OUTER) {
+          // refinement decision (mirrors the host-driven mixed solve)
+          const double rho = (S->bnorm2 > 0.0) ? sqrt(tot / S->bnorm2) : 0.0;
+          S->rho = rho;
+          S->total += S->k;
+          S->outer += 1;
+          if (rho <= S->tol_outer) {
+            S->done = 1;
+          } else if (S->status != 0 || S->total >= S->maxit_total || S->k == 0) {
+            S->done = 1;
+            if (S->status == 0) S->status = ST_ERR_NOT_CONVERGED;
+          } else {
+            const double t = 0.5 * S->tol_outer / rho;
+            S->target = t > 1e-6 ? t : 1e-6;
+            S->maxit = S->maxit_total - S->total;
+            S->k = 0;
+            S->finish = 0;
+            S->active = 0;
+            S->restart = 1;
+          }
+        }
       }
     }
   }
@@ -260,10 +282,13 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
                                                     double *__restrict__ partials, int kc) {
   __shared__ double red[32];
   if (!S->active) return;
+  const bool lead = blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && flat_tid() == 0;
   if (S->finish) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && flat_tid() == 0) S->active = 0;
+    if (lead) S->active = 0;
     return;
   }
+  // first iteration after a device-side restart: the restart pass is complete
+  if (lead && S->restart) S->restart = 0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
@@ -577,6 +602,17 @@ cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, do
   dim3 grid(t.gx, t.gy, t.nchunk);
   prof_begin(KC_STENCIL, st);
   k_stencil_df<<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const double *fH,
+                               State *S, double *partials, cudaStream_t st) {
+  Tile t = tile_for(g);
+  dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
+  dim3 grid(t.gx, t.gy, t.nchunk);
+  prof_begin(KC_RESID, st);
+  k_stencil<double, SM_RESID_OUTER, df><<<grid, block, 0, st>>>(g, x, r_out, fH, S, partials, t.kc);
   prof_end(st);
   return cudaGetLastError();
 }

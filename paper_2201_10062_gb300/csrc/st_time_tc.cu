@@ -227,9 +227,9 @@ __device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L,
 
 __global__ void __launch_bounds__(kNT, 1)
     k_time_tc(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
-              State *S, int tmode, double *__restrict__ partials, int gated) {
+              State *S, int tmode, double *__restrict__ partials, int gk) {
   __shared__ double red[32];
-  if (gated && !S->active) return;
+  if (gate_closed(S, gk)) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int h = n >> 1;
   const TcSmem L = tc_layout(n);
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kNT, 1)
     if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
                                &tot) &&
         tid == 0) {
-      if (tmode == TM_INIT)
+      if (tmode == TM_INIT || tmode == TM_RESTART)
         minres_init_scalars_dev(S, tot);
       else
         minres_givens_dev(S, tot);
@@ -395,7 +395,7 @@ int time_tc_grid() {
 
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
-                           int gated, cudaStream_t st) {
+                           int gk, cudaStream_t st) {
   const TcSmem L = tc_layout(g.n);
   cudaError_t e = cudaFuncSetAttribute(k_time_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L.total);
@@ -406,7 +406,7 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
   prof_begin(KC_TIME, st);
   k_time_tc<<<grid, kNT, L.total, st>>>(data, g.n, g.m, g.mx, sp,
                                         reinterpret_cast<const __half *>(sop), S, tmode, partials,
-                                        gated);
+                                        gk);
   prof_end(st);
   return cudaGetLastError();
 }
