@@ -298,6 +298,8 @@ def run_ours(args, world, rank, local):
                               "ms_per_step": t_e2e * 1e3}
         s.close()
 
+    extra = {} if args.no_extra else run_extra_workloads(P, W, stream, dev, world)
+
     if rank != 0:
         return
     mixed = results["mixed"]
@@ -363,7 +365,91 @@ def run_ours(args, world, rank, local):
                  / (fp["ms"] * 1e-3)},
         "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def _timed(stream, fn, reps):
+    import torch
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def run_extra_workloads(P, W, stream, dev, world):
+    """The other solve workloads, one line object each: 2D variable-coefficient BDF2 at
+    511^2 x 128 (mixed and FP64), and the 64-instance uneven batch (one captured graph, mixed)
+    against the same 64 instances solved one by one in mixed and in FP64."""
+    import torch
+
+    out = {}
+    # ---- 2D variable a, BDF2, 511^2 x 128
+    w = W.config_2d_varcoef_bdf2()
+    f = torch.tensor(w.f, device=dev)
+    u0 = torch.tensor(w.u0, device=dev)
+    up = torch.tensor(w.u_prev, device=dev)
+    res = {}
+    for precision, reps in (("mixed", 3), ("fp64", 1)):
+        s = P.Solver(P.ProblemSpec(2, w.mx, w.my, w.n, w.T, "bdf2", 1.0, w.a_nodal, "PH", precision),
+                     stream)
+        fH = s.st_assemble_rhs(f, u0, up)
+        u = s.empty(w.n, w.m)
+        s.st_solve(fH, tol=TOL, maxit=600, out=u)  # warm-up
+        ms, (_, st) = _timed(stream, lambda: s.st_solve(fH, tol=TOL, maxit=600, out=u), reps)
+        ms = max_over_ranks(ms, world)
+        res[precision] = {"value": world * w.N / (ms * 1e-3), "ms_per_step": ms,
+                          "iterations": st["iterations"], "true_rel_res": st["true_rel_res"],
+                          "steps": reps}
+        s.close()
+    del f, u0, up
+    out["bdf2_var_511x511_n128"] = {"unit": UNIT, "unknowns": w.N, "tol": TOL, **res}
+    # ---- 64 uneven instances
+    draws = W.batch_draws(64, seed=4)
+    ws = [W.config_2d_varcoef_theta(d["mx"], d["n"], d["theta"], d["seed"]) for d in draws]
+    total = sum(x.N for x in ws)
+    specs = [P.ProblemSpec(2, x.mx, x.my, x.n, x.T, "theta", x.theta, x.a_nodal, "PH", "mixed")
+             for x in ws]
+    B = P.BatchSolver(specs, stream)
+    fHs = [B.instance(i).st_assemble_rhs(torch.tensor(x.f, device=dev), torch.tensor(x.u0, device=dev))
+           for i, x in enumerate(ws)]
+    outs = [torch.empty_like(x) for x in fHs]
+    B.st_solve_batch(fHs, tol=TOL, maxit=800, outs=outs)  # capture + warm-up
+    ms_b, (_, stats) = _timed(stream, lambda: B.st_solve_batch(fHs, tol=TOL, maxit=800, outs=outs), 2)
+    ms_b = max_over_ranks(ms_b, world)
+    ok = all(q["status"] == 0 and q["true_rel_res"] <= TOL for q in stats)
+    B.close()
+    seq = {}
+    for precision in ("mixed", "fp64"):
+        solvers = [P.Solver(sp if precision == "mixed" else
+                            P.ProblemSpec(2, x.mx, x.my, x.n, x.T, "theta", x.theta, x.a_nodal, "PH",
+                                          "fp64"), stream) for sp, x in zip(specs, ws)]
+        for sv in solvers:  # same launch shapes as the batch (per-shape cache)
+            sv.st_autotune()
+
+        def one_by_one():
+            return [sv.st_solve(fh, tol=TOL, maxit=800, out=o)[1] for sv, fh, o in zip(solvers, fHs, outs)]
+
+        ms, st = _timed(stream, one_by_one, 1)
+        ms = max_over_ranks(ms, world)
+        seq[precision] = {"value": world * total / (ms * 1e-3), "ms_per_step": ms,
+                          "iterations_total": sum(q["iterations"] for q in st)}
+        for sv in solvers:
+            sv.close()
+    del fHs, outs
+    out["batch_64_uneven"] = {
+        "unit": UNIT, "instances": 64, "unknowns": total, "tol": TOL,
+        "graph": {"value": world * total / (ms_b * 1e-3), "ms_per_step": ms_b, "steps": 2,
+                  "all_converged": ok, "iterations_total": sum(q["iterations"] for q in stats)},
+        "one_by_one_mixed": seq["mixed"], "one_by_one_fp64": seq["fp64"],
+    }
+    return out
 
 
 def main():
@@ -372,6 +458,8 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true",
+                    help="time only the 2D Crank-Nicolson 255^2 x 256 workload")
     args = ap.parse_args()
     if args.impl == "reference":
         world = _env_int("WORLD_SIZE", 1)

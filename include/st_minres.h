@@ -151,6 +151,13 @@ int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double 
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev);
 
+/* Autotuner: times the candidate launch shapes of this handle's kernels on its own buffers
+ * (CUDA events, `reps` launches each, 1..100) -- blocks per stencil launch, sequences per
+ * spatial-DST block, column tile of the FFMA time kernel -- keeps the fastest, and caches the
+ * choice per (dim, mx, my, n, precision, kernel path) for the process.  Synchronous; clobbers
+ * the handle's workspace (call it between solves).  st_setup_batch runs it for every instance. */
+int st_autotune(st_handle *h, int reps);
+
 /* Batched solves: `count` independent instances (each its own st_problem, precision ST_MIXED;
  * sizes, theta/BDF2 and a(x) may all differ) solved concurrently, one stream per instance, by a
  * single CUDA graph that the call relaunches until every instance has converged.  The refinement

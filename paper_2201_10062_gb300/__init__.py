@@ -28,7 +28,7 @@ EXPORTS = (
     "st_apply_prec", "st_apply_prec_f32", "st_solve", "st_solve_host", "st_solve_transpose",
     "st_grad_a", "st_strerror", "st_version", "st_profile_begin", "st_profile_end",
     "st_kernel_class_name", "st_residual_noalloc", "st_grad_rhs", "st_setup_batch",
-    "st_solve_batch", "st_batch_instance", "st_destroy_batch",
+    "st_solve_batch", "st_batch_instance", "st_destroy_batch", "st_autotune",
 )
 KERNEL_CLASSES = ("stencil", "lanczos", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("st_solve", "st_solve_host", "st_solve_transpose"):
         getattr(lib, name).argtypes = [P, P, P, D, I, ctypes.POINTER(StStats)]
         getattr(lib, name).restype = I
+    lib.st_autotune.argtypes = [P, I]
+    lib.st_autotune.restype = I
     lib.st_setup_batch.argtypes = [ctypes.POINTER(StProblem), I, P, ctypes.POINTER(P)]
     lib.st_setup_batch.restype = I
     lib.st_solve_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I,
@@ -305,6 +307,9 @@ class Solver:
                                            _dev_ptr(out, torch.float64, self.spec.N), float(tol),
                                            int(maxit), ctypes.byref(st)), "st_solve_transpose", ok)
         return out, st.as_dict()
+
+    def st_autotune(self, reps=3):
+        _check(self.lib.st_autotune(self.h, int(reps)), "st_autotune")
 
     def st_profile_begin(self, capacity=1 << 16):
         _check(self.lib.st_profile_begin(self.h, int(capacity)), "st_profile_begin")

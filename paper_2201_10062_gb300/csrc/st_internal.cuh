@@ -17,6 +17,7 @@ struct Geom {
   double tau, theta;
   const double *cx;     // [my][mx+1]  tau * a(x-face) / hx^2, faces i = 0..mx between nodes i-1, i
   const double *cy;     // [my+1][mx]  tau * a(y-face) / hy^2 (NULL in 1D)
+  int st_target;        // stencil launch: target number of blocks (0: default), set by autotune
 };
 
 // Spectral tables used by the preconditioner kernels.
@@ -231,7 +232,8 @@ struct PrecPlan {
   const float *twx_f, *twy_f;
   Spec<double> spec_d;
   Spec<float> spec_f;
-  int time_J_d, time_J_f;     // spatial columns per time-kernel block
+  int time_J_d, time_J_f;     // spatial columns per FFMA time-kernel block (0: default)
+  int dst_shift;              // spatial DST: sequences per block divided by 2^dst_shift
   int time_blocks_d, time_blocks_f;
   const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
@@ -266,6 +268,12 @@ template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
                         int tmode, double *partials, cudaStream_t st);
 int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32);
+int time_J_default(int n, bool fp32);
+cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
+                          cudaStream_t st);
+cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
+                          cudaStream_t st);
+bool time_J_fits(int n, int J, bool fp32);
 
 // mixed path: double-float (df) MINRES vectors, float32 preconditioned vectors
 cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, double *partials,

@@ -15,6 +15,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -333,13 +336,20 @@ int map_cuda(cudaError_t e) {
     if (_e != cudaSuccess) return map_cuda(_e); \
   } while (0)
 
+// Enough per-block partial sums for every launch shape the autotuner may pick: the stencil with
+// its largest block target and the time kernel with its narrowest column tile (16).
 int partials_needed(const Geom &g) {
-  int a = stencil_blocks(g);
-  int b = time_blocks_for(g, PrecPlan{}, false);
-  int c = time_blocks_for(g, PrecPlan{}, true);
-  int r = a;
+  Geom gt = g;
+  gt.st_target = 4864;
+  int r = stencil_blocks(gt);
+  const int a = stencil_blocks(g);
+  if (a > r) r = a;
+  const int b = time_blocks_for(g, PrecPlan{}, false);
+  const int c = time_blocks_for(g, PrecPlan{}, true);
+  const int d = (int)((g.m + 15) / 16);
   if (b > r) r = b;
   if (c > r) r = c;
+  if (d > r) r = d;
   if (r < kStreamBlocks) r = kStreamBlocks;
   return r;
 }
@@ -856,6 +866,118 @@ int st_profile_end(st_handle *h, st_kernel_time *out, int nclasses) {
   for (int c = 0; c < nclasses && c < KC_COUNT; ++c) out[c].launches = (int)p.launches[c];
   prof_free(p);
   return ST_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+struct Knobs {
+  int st_target, dst_shift, jd, jf;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, Knobs> g_tune_cache;
+}  // namespace
+
+int st_autotune(st_handle *h, int reps) {
+  if (!h || reps < 1 || reps > 100) return ST_ERR_ARG;
+  ST_TRY(cudaSetDevice(h->device));
+  const bool fp32 = h->mixed;
+  const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.n, (int)fp32,
+                                   (h->pp.sop ? 1 : 0) + (h->pp.pcr ? 2 : 0));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      h->g.st_target = it->second.st_target;
+      h->pp.dst_shift = it->second.dst_shift;
+      h->pp.time_J_d = it->second.jd;
+      h->pp.time_J_f = it->second.jf;
+      return ST_OK;
+    }
+  }
+  cudaStream_t st = h->stream;
+  const Geom &g = h->g;
+  cudaEvent_t e0, e1;
+  ST_TRY(cudaEventCreate(&e0));
+  ST_TRY(cudaEventCreate(&e1));
+  int rc = ST_OK;
+  auto timed = [&](auto &&launch) -> float {
+    if (launch() != cudaSuccess) return 1e30f;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r)
+      if (launch() != cudaSuccess) return 1e30f;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  cudaMemsetAsync(h->V[0], 0, g.N * sizeof(double), st);
+  cudaMemsetAsync(h->Z[0], 0, g.N * (fp32 ? sizeof(float) : sizeof(double)), st);
+  // 1. stencil: blocks per launch (time-chunk length)
+  {
+    const int cand[] = {608, 1216, 2432, 4864};
+    State s{};
+    s.active = 1;
+    s.beta = 1.0;
+    s.inv_beta = 1.0;
+    *h->hS = s;
+    cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, st);
+    float best = 1e30f;
+    int bt = 0;
+    for (int t : cand) {
+      h->g.st_target = t;
+      const float ms = timed([&]() -> cudaError_t {
+        if (fp32)
+          return launch_stencil_df(h->g, (const float *)h->Z[0], (df *)h->q, h->S, h->partials, st);
+        return launch_stencil<double>(h->g, SM_APPLY, h->V[0], h->q, nullptr, h->S, h->partials, 0,
+                                      st);
+      });
+      if (ms < best) {
+        best = ms;
+        bt = t;
+      }
+    }
+    h->g.st_target = bt;
+  }
+  // 2. spatial DST: sequences per block
+  if (!h->pp.pcr) {
+    float best = 1e30f;
+    int bs = 0;
+    for (int sh = 0; sh <= 2; ++sh) {
+      h->pp.dst_shift = sh;
+      const float ms = timed([&]() { return tune_run_dsts(h->g, h->pp, fp32, h->Z[0], st); });
+      if (ms < best) {
+        best = ms;
+        bs = sh;
+      }
+    }
+    h->pp.dst_shift = bs;
+  }
+  // 3. float32/float64 FFMA time kernel (the tensor-core kernel has a fixed tile): column tile
+  if (!h->pp.sop) {
+    const int cand[] = {16, 32, 48, 64};
+    float best = 1e30f;
+    int bj = 0;
+    for (int J : cand) {
+      if (!time_J_fits(g.n, J, fp32)) continue;
+      if (fp32) h->pp.time_J_f = J; else h->pp.time_J_d = J;
+      const float ms = timed([&]() { return tune_run_time(h->g, h->pp, fp32, h->Z[0], st); });
+      if (ms < best) {
+        best = ms;
+        bj = J;
+      }
+    }
+    if (fp32) h->pp.time_J_f = bj; else h->pp.time_J_d = bj;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) rc = map_cuda(le);
+  if (rc == ST_OK) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = Knobs{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f};
+  }
+  return rc;
 }
 
 const char *st_kernel_class_name(int c) {

@@ -421,9 +421,10 @@ size_t time_smem(int n, int J) {
 
 template <class Tc, class Tin, class Tout, bool XL, int LOGL>
 cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
-                         const Tc *tw, const State *S, int gk, cudaStream_t st) {
+                         const Tc *tw, const State *S, int gk, int pbshift, cudaStream_t st) {
   constexpr int L = 1 << LOGL;
-  const int PB = dst_pairs<Tc>(L);
+  int PB = dst_pairs<Tc>(L) >> pbshift;
+  if (PB < 1) PB = 1;
   const size_t sm = dst_smem<Tc>(L, PB);
   const long long blocks = (nlines + 2 * PB - 1) / (2 * PB);
   auto kern = k_dst_space<Tc, Tin, Tout, XL, LOGL>;
@@ -437,17 +438,18 @@ cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, in
 
 template <class Tc, class Tin, class Tout, bool XL>
 cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
-                       long long m, const Tc *tw, const State *S, int gk, cudaStream_t st) {
+                       long long m, const Tc *tw, const State *S, int gk, int pbshift,
+                       cudaStream_t st) {
   switch (L) {
-    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, gk, st);
-    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, gk, st);
+    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -484,8 +486,8 @@ int time_J(int n) {
 
 template <class Tc>
 cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, int tmode,
-                        int tkind, double *partials, int gk, cudaStream_t st) {
-  const int J = time_J<Tc>(g.n);
+                        int tkind, double *partials, int gk, int Jover, cudaStream_t st) {
+  const int J = Jover > 0 ? Jover : time_J<Tc>(g.n);
   const size_t sm = time_smem<Tc>(g.n, J);
   const long long blocks = (g.m + J - 1) / J;
   constexpr int KT = TimeTile<Tc>::KT, JT = TimeTile<Tc>::JT;
@@ -501,9 +503,19 @@ cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, i
 
 }  // namespace
 
-int time_blocks_for(const Geom &g, const PrecPlan &, bool fp32) {
-  const int J = fp32 ? time_J<float>(g.n) : time_J<double>(g.n);
+int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32) {
+  int J = fp32 ? pp.time_J_f : pp.time_J_d;
+  if (J <= 0) J = fp32 ? time_J<float>(g.n) : time_J<double>(g.n);
   return (int)((g.m + J - 1) / J);
+}
+
+int time_J_default(int n, bool fp32) { return fp32 ? time_J<float>(n) : time_J<double>(n); }
+
+bool time_J_fits(int n, int J, bool fp32) {
+  const int JT = fp32 ? TimeTile<float>::JT : TimeTile<double>::JT;
+  if (J < JT || J % JT) return false;
+  const size_t sm = fp32 ? time_smem<float>(n, J) : time_smem<double>(n, J);
+  return sm <= 200 * 1024;
 }
 
 template <class Tc>
@@ -540,7 +552,8 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
     k_copy_to<Tc, Tin><<<152 * 8, kNT, 0, st>>>(g.N, v, zc, S, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, st);
+    const int Jo = sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d;
+    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
     if (e != cudaSuccess) return e;
     const size_t sm = (size_t)8 * g.mx * sizeof(Tc);
     auto kern = k_pcr_ptheta<Tc>;
@@ -550,15 +563,15 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
     kern<<<g.n, kNT, sm, st>>>(zc, g.n, g.mx, g.cx, spec_of<Tc>(pp), S, tmode, partials, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, st);
+    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
   }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
   e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S, gk,
-                                      st);
+                                      pp.dst_shift, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          S, gk, st);
+                                          S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
@@ -566,15 +579,48 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
                        st);
   else
     e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials, gk,
-                        st);
+                        sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          S, gk, st);
+                                          S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
   return launch_dst<Tc, Tout, Tout, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
-                                          gk, st);
+                                          gk, pp.dst_shift, st);
+}
+
+// Autotuning helpers: the spatial DSTs (x then y, in place) and the FFMA time kernel alone,
+// ungated, with the knobs currently in pp.
+cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
+                          cudaStream_t st) {
+  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
+  cudaError_t e;
+  if (fp32) {
+    float *z = (float *)data;
+    e = launch_dst<float, float, float, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_f, nullptr,
+                                              GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim == 2)
+      e = launch_dst<float, float, float, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_f,
+                                                 nullptr, GK_NONE, pp.dst_shift, st);
+  } else {
+    double *z = (double *)data;
+    e = launch_dst<double, double, double, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_d,
+                                                 nullptr, GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim == 2)
+      e = launch_dst<double, double, double, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_d,
+                                                    nullptr, GK_NONE, pp.dst_shift, st);
+  }
+  return e;
+}
+
+cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
+                          cudaStream_t st) {
+  if (fp32)
+    return launch_time<float>((float *)data, g, pp.spec_f, nullptr, TM_NONE, 0, nullptr, GK_NONE,
+                              pp.time_J_f, st);
+  return launch_time<double>((double *)data, g, pp.spec_d, nullptr, TM_NONE, 0, nullptr, GK_NONE,
+                             pp.time_J_d, st);
 }
 
 template cudaError_t launch_prec<double, double, double>(const Geom &, const PrecPlan &,

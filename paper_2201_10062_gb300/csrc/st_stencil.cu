@@ -34,7 +34,8 @@ Tile tile_for(const Geom &g) {
   // chunks cover the first ceil(n/2) planes (each thread also does their mirror images)
   const int half = (g.n + 1) / 2;
   const long long tiles = (long long)t.gx * t.gy;
-  const long long target = 152LL * 8;  // 8 resident 256-thread blocks on each of 152 SMs
+  // default: 8 resident 256-thread blocks on each of 152 SMs; the autotuner may change it
+  const long long target = g.st_target > 0 ? g.st_target : 152LL * 8;
   long long nchunk = (target + tiles - 1) / tiles;
   if (nchunk < 1) nchunk = 1;
   if (nchunk > half) nchunk = half;

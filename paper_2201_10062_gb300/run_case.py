@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--autotune", action="store_true", help="tune launch shapes before solving")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,6 +49,8 @@ def main(argv=None):
     spec = P.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, args.prec,
                          args.precision)
     s = P.Solver(spec)
+    if args.autotune:
+        s.st_autotune()
     dev = s.device
     f = torch.tensor(w.f, device=dev)
     u0 = torch.tensor(w.u0, device=dev)

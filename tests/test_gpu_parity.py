@@ -295,3 +295,36 @@ def test_full_size_2d_varcoef_bdf2(pkg, precision):
     assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-8 * (1 + 1e-6)
     assert np.max(np.abs(u_h - w.u_exact)) < 1e-3
     s.close()
+
+
+# ------------------------------------------------------------------ autotuned launch shapes
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [(2, 63, 31, 65, "theta", 0.5, True), (2, 127, 127, 64, "theta", 1.0, True),
+                                  (1, 255, 1, 40, "bdf2", 1.0, True)],
+                         ids=["2d-63x31-n65", "2d-127-n64", "1d-255-n40-bdf2"])
+def test_autotune_keeps_results(pkg, case, precision):
+    """The tuned knobs only change launch shapes: the operator and preconditioner outputs stay
+    bit-identical, and the solve still meets the oracle's residual with the same iteration count
+    up to one (the dot-product partial sums are grouped differently)."""
+    dim, mx, my, n, scheme, theta, var = case
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=77)
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w, precision=precision))
+    v = _d(np.random.default_rng(5).standard_normal((p.n, p.m)))
+    op0, pr0 = s.st_apply_op(v).clone(), s.st_apply_prec(v).clone()
+    pf0 = s.st_apply_prec_f32(v).clone()
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0), None if w.u_prev is None else _d(w.u_prev))
+    u0, st0 = s.st_solve(fH, tol=1e-9, maxit=600)
+    u0 = u0.clone()
+    s.st_autotune(reps=2)
+    s.st_autotune(reps=2)  # second call is served from the per-shape cache
+    assert torch.equal(s.st_apply_op(v), op0)
+    assert torch.equal(s.st_apply_prec(v), pr0)
+    assert torch.equal(s.st_apply_prec_f32(v), pf0)
+    u1, st1 = s.st_solve(fH, tol=1e-9, maxit=600)
+    assert abs(st1["iterations"] - st0["iterations"]) <= 1, (st0, st1)
+    fH_or = H.rhs(p, w.f, w.u0, w.u_prev)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, _h(u1).reshape(p.n, p.m))
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-9 * (1 + 1e-6)
+    assert _rel2(_h(u1), _h(u0)) <= 1e-6
+    s.close()
