@@ -308,7 +308,7 @@ class Solver:
                                            int(maxit), ctypes.byref(st)), "st_solve_transpose", ok)
         return out, st.as_dict()
 
-    def st_autotune(self, reps=3):
+    def st_autotune(self, reps=5):
         _check(self.lib.st_autotune(self.h, int(reps)), "st_autotune")
 
     def st_profile_begin(self, capacity=1 << 16):

@@ -223,7 +223,7 @@ int st_setup_batch(const st_problem *probs, int count, void *stream, st_batch **
     int r = st_setup(&p, &b->h[i]);
     if (r) return fail(r);
     // launch shapes per (size, precision), cached across instances of the same shape
-    r = st_autotune(b->h[i], 3);
+    r = st_autotune(b->h[i], 5);
     if (r) return fail(r);
   }
   std::vector<State *> sp(count);

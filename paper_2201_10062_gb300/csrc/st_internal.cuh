@@ -17,6 +17,8 @@ struct Geom {
   double tau, theta;
   const double *cx;     // [my][mx+1]  tau * a(x-face) / hx^2, faces i = 0..mx between nodes i-1, i
   const double *cy;     // [my+1][mx]  tau * a(y-face) / hy^2 (NULL in 1D)
+  const df *cxd, *cyd;  // the same coefficients as double-float pairs (mixed-precision stencil)
+  df th_d, omth_d;      // theta and 1 - theta as double-float pairs
   int st_target;        // stencil launch: target number of blocks (0: default), set by autotune
 };
 
@@ -57,7 +59,22 @@ struct State {
   double rho;                          // last true relative residual
   int done, restart, total, outer, maxit_total;
   int pad2;
+  // double-float copies of the per-iteration scalars, refreshed by whoever sets the float64
+  // values, so that the double-float vector kernels read them without float64 instructions
+  df dfs[8];
 };
+
+enum { DFS_IB = 0, DFS_LA, DFS_LB, DFS_DZ, DFS_D1, DFS_D2, DFS_XC };
+
+__host__ __device__ inline void refresh_df(State *S) {
+  S->dfs[DFS_IB] = df_of_double(S->inv_beta);
+  S->dfs[DFS_LA] = df_of_double(S->lz_a);
+  S->dfs[DFS_LB] = df_of_double(S->lz_b);
+  S->dfs[DFS_DZ] = df_of_double(S->dz);
+  S->dfs[DFS_D1] = df_of_double(S->d1);
+  S->dfs[DFS_D2] = df_of_double(S->d2);
+  S->dfs[DFS_XC] = df_of_double(S->xc);
+}
 
 enum { CNT_STENCIL = 0, CNT_TIME = 1, CNT_RESID = 2, CNT_NORM = 3 };
 
@@ -120,6 +137,7 @@ __device__ inline void minres_init_scalars_dev(State *S, double E) {
   if (!(E >= 0.0) || !isfinite(E)) {
     S->status = ST_ERR_BREAKDOWN;
     S->finish = 1;
+    refresh_df(S);
     return;
   }
   const double b1 = sqrt(E);
@@ -137,6 +155,7 @@ __device__ inline void minres_init_scalars_dev(State *S, double E) {
   S->active = 1;  // `restart` stays set until the run's first stencil: the inverse transforms of
                   // this preconditioner pass are still gated on it
   if (b1 == 0.0) S->finish = 1;
+  refresh_df(S);
 }
 
 // One Givens step of MINRES (Paige-Saunders) once beta_{k+1}^2 = E is known.
@@ -146,6 +165,7 @@ __device__ inline void minres_givens_dev(State *S, double E) {
     S->finish = 1;
     S->xc = 0.0;
     S->dz = S->d1 = S->d2 = 0.0;
+    refresh_df(S);
     return;
   }
   const double bnext = sqrt(E);
@@ -161,6 +181,7 @@ __device__ inline void minres_givens_dev(State *S, double E) {
     S->finish = 1;
     S->xc = 0.0;
     S->dz = S->d1 = S->d2 = 0.0;
+    refresh_df(S);
     return;
   }
   const double c = gbar / rho, s = bnext / rho;
@@ -179,6 +200,7 @@ __device__ inline void minres_givens_dev(State *S, double E) {
   S->k = k;
   S->est = fabs(S->eta) / S->beta1;
   if (S->est <= S->target || bnext == 0.0 || k >= S->maxit) S->finish = 1;
+  refresh_df(S);
 }
 
 

@@ -85,32 +85,41 @@ __global__ void __launch_bounds__(kNTD, 2)
   // at e+1 and its negative at L-1-e (odd extension).  Index maps avoid divisions: len + 1 =
   // L/2 and PB are powers of two.
   if (XL) {
+    // lines 2pp and 2pp+1 are consecutive rows: one base pointer serves both
     for (int idx = tid; idx < (PB << logH); idx += kNTD) {
       const int pp = idx >> logH, e = idx & (half - 1);
       if (e >= len) continue;
       const int la = 2 * pp, lb = la + 1;
-      const Tc a = (la < nl) ? to_real<Tc>(in[(line0 + la) * len + e]) : Tc(0);
-      const Tc b = (lb < nl) ? to_real<Tc>(in[(line0 + lb) * len + e]) : Tc(0);
-      buf[pp * Ls + fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
-      buf[pp * Ls + fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
+      const Tin *p = in + (line0 + la) * len + e;
+      const Tc a = (la < nl) ? to_real<Tc>(p[0]) : Tc(0);
+      const Tc b = (lb < nl) ? to_real<Tc>(p[len]) : Tc(0);
+      cpx<Tc> *bq = buf + pp * Ls;
+      bq[fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
+      bq[fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
     }
   } else {
-    for (int idx = tid; idx < (len << logPB); idx += kNTD) {
-      const int e = idx >> logPB, pp = idx & (PB - 1);
-      const int la = 2 * pp, lb = la + 1;
-      Tc a = Tc(0), b = Tc(0);
-      if (la < nl) {
-        const int l = (int)line0 + la;
-        const int k = l / mx, i = l - k * mx;
-        a = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
-      }
-      if (lb < nl) {
-        const int l = (int)line0 + lb;
-        const int k = l / mx, i = l - k * mx;
-        b = to_real<Tc>(in[(long long)k * m + (long long)e * mx + i]);
-      }
-      buf[pp * Ls + fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
-      buf[pp * Ls + fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
+    // PB divides the block size, so every thread keeps one sequence (pair of columns) and walks
+    // its elements: the column decomposition (plane k, column i) is done once per thread.
+    const int pp = tid & (PB - 1), estep = kNTD >> logPB;
+    const int la = 2 * pp, lb = la + 1;
+    const Tin *pa = nullptr, *pb = nullptr;
+    if (la < nl) {
+      const int l = (int)line0 + la;
+      const int k = l / mx, i = l - k * mx;
+      pa = in + (long long)k * m + i;
+    }
+    if (lb < nl) {
+      const int l = (int)line0 + lb;
+      const int k = l / mx, i = l - k * mx;
+      pb = in + (long long)k * m + i;
+    }
+    cpx<Tc> *bq = buf + pp * Ls;
+    for (int e = tid >> logPB; e < len; e += estep) {
+      const long long off = (long long)e * mx;
+      const Tc a = pa ? to_real<Tc>(pa[off]) : Tc(0);
+      const Tc b = pb ? to_real<Tc>(pb[off]) : Tc(0);
+      bq[fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
+      bq[fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
     }
   }
   __syncthreads();
@@ -122,24 +131,30 @@ __global__ void __launch_bounds__(kNTD, 2)
       if (e >= len) continue;
       const cpx<Tc> Z = buf[pp * Ls + fft_pad<Tc>(e + 1)];
       const int la = 2 * pp, lb = la + 1;
-      if (la < nl) out[(line0 + la) * len + e] = (Tout)(-Z.y * sc);
-      if (lb < nl) out[(line0 + lb) * len + e] = (Tout)(Z.x * sc);
+      Tout *p = out + (line0 + la) * len + e;
+      if (la < nl) p[0] = (Tout)(-Z.y * sc);
+      if (lb < nl) p[len] = (Tout)(Z.x * sc);
     }
   } else {
-    for (int idx = tid; idx < (len << logPB); idx += kNTD) {
-      const int e = idx >> logPB, pp = idx & (PB - 1);
-      const cpx<Tc> Z = buf[pp * Ls + fft_pad<Tc>(e + 1)];
-      const int la = 2 * pp, lb = la + 1;
-      if (la < nl) {
-        const int l = (int)line0 + la;
-        const int k = l / mx, i = l - k * mx;
-        out[(long long)k * m + (long long)e * mx + i] = (Tout)(-Z.y * sc);
-      }
-      if (lb < nl) {
-        const int l = (int)line0 + lb;
-        const int k = l / mx, i = l - k * mx;
-        out[(long long)k * m + (long long)e * mx + i] = (Tout)(Z.x * sc);
-      }
+    const int pp = tid & (PB - 1), estep = kNTD >> logPB;
+    const int la = 2 * pp, lb = la + 1;
+    Tout *pa = nullptr, *pb = nullptr;
+    if (la < nl) {
+      const int l = (int)line0 + la;
+      const int k = l / mx, i = l - k * mx;
+      pa = out + (long long)k * m + i;
+    }
+    if (lb < nl) {
+      const int l = (int)line0 + lb;
+      const int k = l / mx, i = l - k * mx;
+      pb = out + (long long)k * m + i;
+    }
+    const cpx<Tc> *bq = buf + pp * Ls;
+    for (int e = tid >> logPB; e < len; e += estep) {
+      const cpx<Tc> Z = bq[fft_pad<Tc>(e + 1)];
+      const long long off = (long long)e * mx;
+      if (pa) pa[off] = (Tout)(-Z.y * sc);
+      if (pb) pb[off] = (Tout)(Z.x * sc);
     }
   }
 }

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
         S->alpha = tot;
         S->lz_a = tot / S->beta;
         S->lz_b = (S->k > 0) ? S->beta / S->beta_prev : 0.0;
+        refresh_df(S);
       } else {
         S->rnorm2 = tot;
         if (MODE == SM_RESID_OUTER) {
@@ -298,19 +299,18 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
   const int half = (n + 1) >> 1;
   const int k0 = blockIdx.z * kc;
   const int k1 = min(half, k0 + kc);
-  const double sd = S->inv_beta;
-  const df s = df_of_double(sd);
+  const df s = S->dfs[DFS_IB];
   acc_df D{0.f, 0.f};
   if (valid) {
     const long long p = (long long)j * mx + i;
-    const df cw = df_of_double(g.cx[(long long)j * (mx + 1) + i]);
-    const df ce = df_of_double(g.cx[(long long)j * (mx + 1) + i + 1]);
+    const df cw = g.cxd[(long long)j * (mx + 1) + i];
+    const df ce = g.cxd[(long long)j * (mx + 1) + i + 1];
     df cs{0.f, 0.f}, cn{0.f, 0.f};
     if (dim == 2) {
-      cs = df_of_double(g.cy[(long long)j * mx + i]);
-      cn = df_of_double(g.cy[(long long)(j + 1) * mx + i]);
+      cs = g.cyd[(long long)j * mx + i];
+      cn = g.cyd[(long long)(j + 1) * mx + i];
     }
-    const df th = df_of_double(g.theta), omth = df_of_double(1.0 - g.theta);
+    const df th = g.th_d, omth = g.omth_d;
     const bool theta = (g.scheme == ST_THETA);
     auto center = [&](int k) -> float { return __ldg(z + (long long)k * m + p); };
     auto stiff = [&](int k, float c) -> df {
@@ -397,10 +397,12 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
   double tot;
   if (last_block_reduce<kNT>(acc, partials, &S->counter[CNT_STENCIL], nb, bid, red, &tot) &&
       flat_tid() == 0) {
+    const double sd = S->inv_beta;
     const double alpha = tot * sd * sd;
     S->alpha = alpha;
     S->lz_a = alpha / S->beta;
     S->lz_b = (S->k > 0) ? S->beta / S->beta_prev : 0.0;
+    refresh_df(S);
   }
 }
 

@@ -9,12 +9,14 @@
 // hi*hi + hi*lo + lo*hi accumulate in float32 in tensor memory.  Columns of B are scaled by a
 // power of two so that fp16 keeps its range; S is scaled by 8.
 //
-// One persistent block per SM keeps A (both parities, both pieces, 128 KB for n = 256) in shared
-// memory and walks the column tiles.  One thread issues tcgen05.mma (M = 128, N = 32, K = 16,
-// A and B from shared-memory descriptors, no swizzle, K-major core matrices of 8 rows x 16
-// bytes), tcgen05.commit signals an mbarrier, and all warps read the accumulators with
-// tcgen05.ld.  Every wait on the mbarrier is bounded; on timeout the block records
-// ST_ERR_TIMEOUT in the MINRES state and stops issuing work.
+// One persistent block of 16 warps per SM keeps A (both parities, both pieces, 128 KB for
+// n = 256) in shared memory and walks column tiles of 32; the next tile's input is copied into
+// a staging buffer (cp.async) while the current one is transformed.  One thread issues
+// tcgen05.mma (M = 128, N = 32, K = 16, A and B from shared-memory descriptors, no swizzle,
+// K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals an mbarrier, and every
+// warp reads 32 rows x 16 columns of one parity's accumulators with tcgen05.ld.  Every wait on
+// the mbarrier is bounded; on timeout the block records ST_ERR_TIMEOUT in the MINRES state and
+// stops.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -24,7 +26,7 @@
 namespace st {
 namespace {
 
-constexpr int kNT = 256;
+constexpr int kNT = 512;         // 16 warps
 constexpr int kTN = 32;          // spatial columns per tile (MMA N)
 constexpr int kM = 128;          // MMA M (rows of S of one parity, zero padded)
 constexpr float kSScale = 8.0f;  // S is stored times 8
@@ -100,6 +102,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -110,32 +126,13 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// split v into fp16 hi + lo
-__device__ __forceinline__ void split_h(float v, __half &hi, __half &lo) {
-  hi = __float2half_rn(v);
-  lo = __float2half_rn(v - __half2float(hi));
-}
 
-// 1/p for time frequency k (1-based) and tau*mu (same closed forms as the float kernel)
-__device__ __forceinline__ float inv_symbol_f(const Spec<float> &sp, int k, float tmu) {
-  const float hk = sp.hk[k - 1], ck = sp.ck[k - 1], sk = sp.sk[k - 1];
-  if (sp.prec == ST_PREC_PTHETA) return 1.0f / (sp.lh[k - 1] + sp.lht[k - 1] * tmu);
-  float re, im;
-  if (sp.scheme == ST_THETA) {
-    re = hk + tmu * (sp.theta + (1.0f - sp.theta) * ck);
-    im = (-1.0f + (1.0f - sp.theta) * tmu) * sk;
-  } else {
-    re = hk * hk + tmu;
-    im = -sk * (1.0f + hk);
-  }
-  return rsqrtf(re * re + im * im);
-}
-
+// Shared-memory layout, offsets in bytes from the dynamic base.
 struct TcSmem {
-  // offsets in bytes from the dynamic shared-memory base
-  uint32_t sop, bop, ytile, colscale, colmax, tmu, mbar, tmem;
-  uint32_t total;
+  uint32_t sop, bop, ytile, stage, colscale, colinv, colmax, tmu, mbar, tmem, total;
 };
+
+constexpr int kYS = kTN + 1;  // padded row of the parity-split Y tile (conflict-free row writes)
 
 __host__ __device__ inline TcSmem tc_layout(int n) {
   const int h = n / 2;
@@ -146,8 +143,12 @@ __host__ __device__ inline TcSmem tc_layout(int n) {
   L.bop = o;
   o += 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
   L.ytile = o;
-  o += (uint32_t)n * kTN * 4u;  // float [n][32]
+  o += (uint32_t)n * kYS * 4u;  // float [parity][h][33]
+  L.stage = o;
+  o += (uint32_t)n * kTN * 4u;  // float [n][32]: raw input tile, filled by cp.async
   L.colscale = o;
+  o += kTN * 4u;
+  L.colinv = o;
   o += kTN * 4u;
   L.colmax = o;
   o += kTN * 4u;
@@ -161,48 +162,81 @@ __host__ __device__ inline TcSmem tc_layout(int n) {
   return L;
 }
 
-// Fold rows t and n-1-t of a float tile column, scale by a power of two per column and write the
-// fp16 pieces of both parities in canonical layout.  src(t, c) gives the value.
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const float *g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// fp16 (hi, lo) pieces of two floats, packed as half2 words
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t &hi, uint32_t &lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 f = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// Fold rows t and n-1-t of a float tile column (sum for odd k, difference for even k), scale each
+// column by a power of two so that its largest folded value lies in [2^13, 2^14), and write the
+// fp16 (hi, lo) pieces of both parities in canonical layout.  Thread (column c, block of 8 t)
+// keeps its folded values in registers between the maximum and the split, and stores each piece
+// as one 16-byte chunk (8 consecutive K elements of one row).  src(t, c) gives the value.
 template <class Src>
 __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, int n, Src src,
                                         int tid) {
-  const int h = n >> 1;
+  const int h = n >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
   unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
   float *colscale = reinterpret_cast<float *>(smem + L.colscale);
-  const int c = tid & (kTN - 1), rg = tid >> 5;  // 8 row groups
-  for (int i = tid; i < kTN; i += kNT) colmax[i] = 0u;
-  __syncthreads();
+  float *colinv = reinterpret_cast<float *>(smem + L.colinv);
+  const int c = tid & (kTN - 1), tb = tid >> 5;
+  if (tid < kTN) colmax[tid] = 0u;
+  float u[8], d[8];
   float mx = 0.f;
-  for (int t = rg; t < h; t += kNT / kTN) {
-    const float a = src(t, c), b = src(n - 1 - t, c);
-    mx = fmaxf(mx, fmaxf(fabsf(a + b), fabsf(a - b)));
+  if (tb < hb) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = tb * 8 + q;
+      const float a = src(t, c), b = src(n - 1 - t, c);
+      u[q] = a + b;
+      d[q] = a - b;
+      mx = fmaxf(mx, fmaxf(fabsf(u[q]), fabsf(d[q])));
+    }
   }
-  atomicMax(&colmax[c], __float_as_uint(mx));
+  __syncthreads();
+  if (tb < hb) atomicMax(&colmax[c], __float_as_uint(mx));
   __syncthreads();
   if (tid < kTN) {
     const float m = __uint_as_float(colmax[tid]);
     float s = 1.0f;
     if (m > 0.f && isfinite(m)) {
       int e;
-      frexpf(m, &e);           // m in [2^(e-1), 2^e)
+      frexpf(m, &e);             // m in [2^(e-1), 2^e)
       s = ldexpf(1.0f, 14 - e);  // scaled maximum below 2^14
     }
     colscale[tid] = s;
+    colinv[tid] = 1.0f / (s * kSScale);  // exact: a power of two
   }
   __syncthreads();
-  const float s = colscale[c];
-  unsigned char *bop = smem + L.bop;
-  const uint32_t piece = (uint32_t)kTN * h * 2u;
-  for (int t = rg; t < h; t += kNT / kTN) {
-    const float a = src(t, c), b = src(n - 1 - t, c);
-    __half uh, ul, dh, dl;
-    split_h((a + b) * s, uh, ul);
-    split_h((a - b) * s, dh, dl);
-    const uint32_t off = canon_off(c, t, h);
-    *reinterpret_cast<__half *>(bop + 0 * piece + off) = uh;  // parity 0 (odd k), hi
-    *reinterpret_cast<__half *>(bop + 1 * piece + off) = ul;  // parity 0, lo
-    *reinterpret_cast<__half *>(bop + 2 * piece + off) = dh;  // parity 1 (even k), hi
-    *reinterpret_cast<__half *>(bop + 3 * piece + off) = dl;  // parity 1, lo
+  if (tb < hb) {
+    const float s = colscale[c];
+    unsigned char *bop = smem + L.bop;
+    const uint32_t piece = (uint32_t)kTN * h * 2u;
+    uint32_t uh[4], ul[4], dh[4], dl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      split_h2(u[2 * q] * s, u[2 * q + 1] * s, uh[q], ul[q]);
+      split_h2(d[2 * q] * s, d[2 * q + 1] * s, dh[q], dl[q]);
+    }
+    const uint32_t off = canon_off(c, tb * 8, h);
+    *reinterpret_cast<uint4 *>(bop + 0 * piece + off) = make_uint4(uh[0], uh[1], uh[2], uh[3]);
+    *reinterpret_cast<uint4 *>(bop + 1 * piece + off) = make_uint4(ul[0], ul[1], ul[2], ul[3]);
+    *reinterpret_cast<uint4 *>(bop + 2 * piece + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+    *reinterpret_cast<uint4 *>(bop + 3 * piece + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
   }
 }
 
@@ -225,6 +259,66 @@ __device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L,
   mma_commit(smem_u32(smem + L.mbar));
 }
 
+// Per-row (time frequency k) constants of 1/p(k, tau mu), hoisted out of the column loop.
+struct SymRow {
+  float a, b, c;
+};
+
+__device__ __forceinline__ SymRow sym_row(const Spec<float> &sp, int k) {
+  SymRow r;
+  const float hk = sp.hk[k - 1], ck = sp.ck[k - 1], sk = sp.sk[k - 1];
+  if (sp.prec == ST_PREC_PTHETA) {
+    r.a = sp.lh[k - 1];
+    r.b = sp.lht[k - 1];
+    r.c = 0.f;
+  } else if (sp.scheme == ST_THETA) {
+    r.a = hk;
+    r.b = sp.theta + (1.0f - sp.theta) * ck;
+    r.c = sk;
+  } else {
+    r.a = hk * hk;
+    r.b = 1.0f;
+    r.c = -sk * (1.0f + hk);
+  }
+  return r;
+}
+
+// 1/p: theta:  re = (1 - cos x) + tmu (th + (1-th) cos x), im = (-1 + (1-th) tmu) sin x;
+// BDF2: re = (1 - cos x)^2 + tmu, im = -sin x (2 - cos x);  P_theta: 1/(lam_H + lam_Htheta tmu)
+__device__ __forceinline__ float inv_sym(const Spec<float> &sp, const SymRow &r, float tmu) {
+  if (sp.prec == ST_PREC_PTHETA) return 1.0f / (r.a + r.b * tmu);
+  float re, im;
+  if (sp.scheme == ST_THETA) {
+    re = r.a + tmu * r.b;
+    im = (-1.0f + (1.0f - sp.theta) * tmu) * r.c;
+  } else {
+    re = r.a + tmu;
+    im = r.c;
+  }
+  return rsqrtf(re * re + im * im);
+}
+
+// Load the raw [n][32] tile starting at column j0 into the stage buffer (asynchronous copies;
+// columns past the end are zeroed directly).
+__device__ __forceinline__ void prefetch_tile(unsigned char *smem, const TcSmem &L,
+                                              const float *data, int n, long long m, long long j0,
+                                              int tid) {
+  const int je = (int)min((long long)kTN, m - j0);
+  float *stage = reinterpret_cast<float *>(smem + L.stage);
+  const uint32_t sbase = smem_u32(stage);
+  for (int idx = tid; idx < n * kTN; idx += kNT) {
+    const int t = idx >> 5, c = idx & (kTN - 1);
+    if (c < je)
+      cp_async4(sbase + 4u * (uint32_t)idx, data + (long long)t * m + j0 + c);
+    else
+      stage[idx] = 0.f;
+  }
+  cp_async_commit();
+}
+
+// Per column tile: wait for the staged input, build B, start loading the next tile, MMA, scale
+// (energy), build B again from the scaled tile, MMA, and write the result back through the padded
+// tile with coalesced rows.
 __global__ void __launch_bounds__(kNT, 1)
     k_time_tc(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
               State *S, int tmode, double *__restrict__ partials, int gk) {
@@ -236,8 +330,13 @@ __global__ void __launch_bounds__(kNT, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
-  const float *colscale = reinterpret_cast<const float *>(smem + L.colscale);
+  const float *colinv = reinterpret_cast<const float *>(smem + L.colinv);
+  const float *stage = reinterpret_cast<const float *>(smem + L.stage);
   float *ytile = reinterpret_cast<float *>(smem + L.ytile);
+  float *tmus = reinterpret_cast<float *>(smem + L.tmu);
+  const long long ntiles = (m + kTN - 1) / kTN;
+  if ((long long)blockIdx.x < ntiles)
+    prefetch_tile(smem, L, data, n, m, (long long)blockIdx.x * kTN, tid);
   // A operands: straight copy of the precomputed canonical image
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(sop_g);
@@ -262,15 +361,16 @@ __global__ void __launch_bounds__(kNT, 1)
   uint32_t phase = 0;
   bool ok = true;
   float esum = 0.f, ecomp = 0.f;
-  const long long ntiles = (m + kTN - 1) / kTN;
-  const int P = warp >> 2;                      // parity block this warp reads
-  const int r = ((warp & 3) << 5) + lane;       // accumulator row = TMEM lane
-  const int krow = (P == 0) ? 2 * r + 1 : 2 * r + 2;  // 1-based time frequency of that row
-  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(P * kTN);
+  // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
+  const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
+  const int r = (q << 5) + lane;
+  const int c0 = ch * 16;
+  const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN + c0);
+  const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
+  float *yrow = ytile + (P * h + r) * kYS;  // this thread's row of the parity-split tile
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long j0 = tile * kTN;
     const int je = (int)min((long long)kTN, m - j0);
-    float *tmus = reinterpret_cast<float *>(smem + L.tmu);
     if (tid < kTN) {
       float t = 0.f;
       if (tid < je) {
@@ -280,41 +380,43 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       tmus[tid] = t;
     }
-    // ---- first transform: B from global data
-    build_b(smem, L, n,
-            [&](int t, int c) -> float {
-              return (c < je) ? data[(long long)t * m + j0 + c] : 0.f;
-            },
-            tid);
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- first transform: B from the staged input
+    build_b(smem, L, n, [&](int t, int c) -> float { return stage[t * kTN + c]; }, tid);
     fence_async_smem();
     __syncthreads();
     fence_after();
     if (tid == 0) issue_mmas(smem, L, h, tmem);
+    // the stage buffer is free: start loading the next tile while the tensor cores work
+    if (tile + gridDim.x < ntiles)
+      prefetch_tile(smem, L, data, n, m, (tile + gridDim.x) * kTN, tid);
     ok = __syncthreads_and(mbar_wait(smem_u32(mbar), phase) ? 1 : 0) != 0;
     phase ^= 1u;
     fence_after();
-    float v[32];
-    tmem_ld32(tl, v);
-    // unscale, spectral scaling, energy; scaled Y into the float tile
+    float v[16];
+    tmem_ld16(tl, v);
+    // unscale, spectral scaling, energy; scaled Y into the parity-split tile
     if (r < h) {
+      float rs = 0.f;
 #pragma unroll
-      for (int c = 0; c < kTN; ++c) {
-        const float y = v[c] / (colscale[c] * kSScale);
-        const float ip = inv_symbol_f(sp, krow, tmus[c]);
-        if (c < je) {
-          const float term = y * y * ip - ecomp;
-          const float t = esum + term;
-          ecomp = (t - esum) - term;
-          esum = t;
-        }
-        ytile[(krow - 1) * kTN + c] = y * ip;
+      for (int c = 0; c < 16; ++c) {
+        const float y = v[c] * colinv[c0 + c];
+        const float yi = y * inv_sym(sp, sr, tmus[c0 + c]);
+        if (c0 + c < je) rs = fmaf(y, yi, rs);
+        yrow[c0 + c] = yi;
       }
+      const float term = rs - ecomp;  // compensated running sum over rows and tiles
+      const float t = esum + term;
+      ecomp = (t - esum) - term;
+      esum = t;
     }
     fence_before();
     __syncthreads();
     fence_after();
-    // ---- second transform: B from the scaled tile
-    build_b(smem, L, n, [&](int t, int c) -> float { return ytile[t * kTN + c]; }, tid);
+    // ---- second transform: B from the scaled tile (row t = k - 1 lives in parity t & 1)
+    build_b(smem, L, n,
+            [&](int t, int c) -> float { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; }, tid);
     fence_async_smem();
     __syncthreads();
     fence_after();
@@ -322,17 +424,21 @@ __global__ void __launch_bounds__(kNT, 1)
     ok = __syncthreads_and((ok && mbar_wait(smem_u32(mbar), phase)) ? 1 : 0) != 0;
     phase ^= 1u;
     fence_after();
-    tmem_ld32(tl, v);
+    tmem_ld16(tl, v);
     if (r < h) {
-      float *row = data + (long long)(krow - 1) * m + j0;
 #pragma unroll
-      for (int c = 0; c < kTN; ++c)
-        if (c < je) row[c] = v[c] / (colscale[c] * kSScale);
+      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv[c0 + c];
     }
     fence_before();
     __syncthreads();
     fence_after();
+    // coalesced write-back: one warp per time row
+    for (int idx = tid; idx < n * kTN; idx += kNT) {
+      const int t = idx >> 5, c = idx & (kTN - 1);
+      if (c < je) data[(long long)t * m + j0 + c] = ytile[((t & 1) * h + (t >> 1)) * kYS + c];
+    }
   }
+  cp_async_wait_all();
   if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
   fence_before();
   __syncthreads();
@@ -356,7 +462,11 @@ __global__ void __launch_bounds__(kNT, 1)
 
 }  // namespace
 
-bool time_tc_supported(int n) { return n >= 32 && n <= 256 && (n % 32) == 0; }
+// n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
+// within the 227 KB a block may opt into
+bool time_tc_supported(int n) {
+  return n >= 32 && n <= 256 && (n % 32) == 0 && tc_layout(n).total + 1024u <= 227u * 1024u;
+}
 
 size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * (n / 2); }
 
@@ -396,15 +506,15 @@ int time_tc_grid() {
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st) {
-  const TcSmem L = tc_layout(g.n);
+  const uint32_t smem_bytes = tc_layout(g.n).total;
   cudaError_t e = cudaFuncSetAttribute(k_time_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L.total);
+                                       (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = (g.m + kTN - 1) / kTN;
   int grid = time_tc_grid();
   if (ntiles < grid) grid = (int)ntiles;
   prof_begin(KC_TIME, st);
-  k_time_tc<<<grid, kNT, L.total, st>>>(data, g.n, g.m, g.mx, sp,
+  k_time_tc<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
                                         reinterpret_cast<const __half *>(sop), S, tmode, partials,
                                         gk);
   prof_end(st);
