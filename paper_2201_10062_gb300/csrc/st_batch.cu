@@ -73,9 +73,9 @@ cudaError_t iteration(st_handle *h, int c, cudaStream_t st) {
   df *q = (df *)h->q;
   cudaError_t e;
   if ((e = launch_stencil_df(g, zc, q, h->S, h->partials, st)) != cudaSuccess) return e;
-  if ((e = launch_lanczos_df(g.N, q, V0, V1, h->S, st)) != cudaSuccess) return e;
-  if ((e = launch_prec<float, df, float>(g, h->pp, V1, zn, h->S, TM_ITER, h->partials, st)) !=
-      cudaSuccess)
+  // Lanczos step fused into the first transform of the preconditioner pass
+  if ((e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials,
+                                                 st)) != cudaSuccess)
     return e;
   return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
 }

@@ -77,6 +77,22 @@ __host__ __device__ __forceinline__ df df_mul_f(df a, float b) {
 // a*b + c
 __host__ __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 
+// running double-float sum (s, t): add p + e, with the high parts added error-free
+__host__ __device__ __forceinline__ void dacc_add(float &s, float &t, float p, float e) {
+  float ss, err;
+  two_sum(s, p, ss, err);
+  s = ss;
+  t += err + e;
+}
+
+// running double-float sum (s, t): add a * b
+__host__ __device__ __forceinline__ void dacc_prod(float &s, float &t, df a, df b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  dacc_add(s, t, p, e);
+}
+
 __host__ __device__ __forceinline__ df df_of_double(double x) {
   df r;
   r.hi = (float)x;

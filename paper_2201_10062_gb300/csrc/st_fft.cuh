@@ -6,6 +6,7 @@
 // registers and stores output q at (j div Ns) Ns R + (j mod Ns) + q Ns.  After the last pass
 // the sequence is in natural order.  Shared-memory slots are padded (one slot every 2^PADSHIFT
 // elements) so that the strided stores of the early passes hit at most two-way bank conflicts.
+// tw[t] = W_L^t for t < L/2.
 #pragma once
 
 namespace st {
@@ -113,67 +114,36 @@ struct Dft<T, 8> {
   }
 };
 
-// One Stockham pass on `count` sequences (each fft_padded_len(L) slots apart).  tw[t] =
-// W_L^t for t < L/2.  Work items are strided over `nthreads` threads starting at `tid`.
-template <class T, int R>
-__host__ __device__ __forceinline__ void stockham_pass(const cpx<T> *src, cpx<T> *dst,
-                                                       const cpx<T> *tw, int L, int logL, int Ns,
-                                                       int logNs, int count, int tid,
-                                                       int nthreads) {
-  constexpr int LOGR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
-  const int LR = L / R;
-  const int logLR = logL - LOGR;
-  const int Lp = fft_padded_len<T>(L);
-  const int twstep = L >> (logNs + LOGR);  // L / (Ns R)
-  for (int task = tid; task < count * LR; task += nthreads) {
-    const int pp = task >> logLR;
-    const int j = task & (LR - 1);
-    const cpx<T> *s = src + pp * Lp;
-    cpx<T> v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[fft_pad<T>(j + r * LR)];
-    const int k = j & (Ns - 1);
-    if (Ns > 1) {
-      const cpx<T> w1 = tw[k * twstep];
-      cpx<T> w = w1;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        v[r] = cmulc(v[r], w);
-        if (r + 1 < R) w = cmulc(w, w1);
-      }
-    }
-    Dft<T, R>::run(v);
-    const int idxD = ((j >> logNs) << (logNs + LOGR)) + k;
-    cpx<T> *d = dst + pp * Lp;
-#pragma unroll
-    for (int r = 0; r < R; ++r) d[fft_pad<T>(idxD + r * Ns)] = v[r];
-  }
-}
-
-// In-place Stockham pass over `count` sequences `stride` slots apart: every thread first loads
-// the R values of each of its 8/R work items (eight complex values per thread for every radix),
-// the block synchronises, then every thread transforms and stores.  Requires
-// count * L <= 8 * nthreads.
-template <class T, int R>
-__device__ __forceinline__ void stockham_pass_inplace(cpx<T> *buf, const cpx<T> *tw, int L,
-                                                      int logL, int Ns, int logNs, int count,
+// In-place Stockham pass over `count` sequences `stride` slots apart, with the length L = 2^LOGL,
+// the radix R and the span Ns = 2^LOGNS known at compile time: every thread first loads the R
+// values of each of its 8/R work items (eight complex values per thread for every radix), the
+// block synchronises, then every thread transforms and stores.  Requires count * L <= 8 *
+// nthreads.  The padded slot of element x is x + (x >> s) (s = PadShift); for every access of
+// a pass, pad(base + r * step) = pad(base) + r * step + ((r * step) >> s) holds (step = L/R for
+// loads, Ns for stores, base < step or a multiple of step * R), so each access is a base
+// register plus a compile-time offset.
+template <class T, int R, int LOGL, int LOGNS>
+__device__ __forceinline__ void stockham_pass_inplace(cpx<T> *buf, const cpx<T> *tw, int count,
                                                       int stride, int tid, int nthreads) {
   constexpr int LOGR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
   constexpr int TASKS = 8 / R;
-  const int LR = L / R;
-  const int logLR = logL - LOGR;
-  const int twstep = L >> (logNs + LOGR);
+  constexpr int L = 1 << LOGL;
+  constexpr int LR = L / R;
+  constexpr int LOGLR = LOGL - LOGR;
+  constexpr int NS = 1 << LOGNS;
+  constexpr int TWSTEP = L >> (LOGNS + LOGR);
+  constexpr int S = PadShift<T>::v;
   const int ntask = count * LR;
   cpx<T> v[TASKS][R];
 #pragma unroll
   for (int u = 0; u < TASKS; ++u) {
     const int task = tid + u * nthreads;
     if (task < ntask) {
-      const int pp = task >> logLR;
+      const int pp = task >> LOGLR;
       const int j = task & (LR - 1);
-      const cpx<T> *s = buf + pp * stride;
+      const cpx<T> *s = buf + pp * stride + (j + (j >> S));
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[u][r] = s[fft_pad<T>(j + r * LR)];
+      for (int r = 0; r < R; ++r) v[u][r] = s[r * LR + ((r * LR) >> S)];
     }
   }
   __syncthreads();
@@ -181,11 +151,11 @@ __device__ __forceinline__ void stockham_pass_inplace(cpx<T> *buf, const cpx<T> 
   for (int u = 0; u < TASKS; ++u) {
     const int task = tid + u * nthreads;
     if (task < ntask) {
-      const int pp = task >> logLR;
+      const int pp = task >> LOGLR;
       const int j = task & (LR - 1);
-      const int k = j & (Ns - 1);
-      if (Ns > 1) {
-        const cpx<T> w1 = tw[k * twstep];
+      const int k = j & (NS - 1);
+      if (NS > 1) {
+        const cpx<T> w1 = tw[k * TWSTEP];
         cpx<T> w = w1;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -194,10 +164,10 @@ __device__ __forceinline__ void stockham_pass_inplace(cpx<T> *buf, const cpx<T> 
         }
       }
       Dft<T, R>::run(v[u]);
-      const int idxD = ((j >> logNs) << (logNs + LOGR)) + k;
-      cpx<T> *d = buf + pp * stride;
+      const int idxD = ((j >> LOGNS) << (LOGNS + LOGR)) + k;
+      cpx<T> *d = buf + pp * stride + (idxD + (idxD >> S));
 #pragma unroll
-      for (int r = 0; r < R; ++r) d[fft_pad<T>(idxD + r * Ns)] = v[u][r];
+      for (int r = 0; r < R; ++r) d[r * NS + ((r * NS) >> S)] = v[u][r];
     }
   }
   __syncthreads();

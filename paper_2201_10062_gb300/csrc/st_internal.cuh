@@ -287,6 +287,9 @@ __device__ __forceinline__ bool gate_closed(const State *S, int gk) {
 }
 
 template <class Tc, class Tin, class Tout>
+cudaError_t launch_prec_lanczos(const Geom &g, const PrecPlan &pp, const Tin *q, const Tin *vk,
+                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st);
+template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
                         int tmode, double *partials, cudaStream_t st);
 int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32);
@@ -320,6 +323,56 @@ template <class Tc>
 __device__ __forceinline__ Tc to_real(float v) { return (Tc)v; }
 template <class Tc>
 __device__ __forceinline__ Tc to_real(df v) { return (Tc)v.hi; }
+
+// Element sources for the first stage of a preconditioner pass.  prepare() runs once per thread
+// after the gate; operator() returns element i in the transform type.
+template <class Tc, class Tin>
+struct SrcArray {
+  const Tin *p;
+  __device__ __forceinline__ void prepare(const State *) {}
+  __device__ __forceinline__ Tc operator()(long long i) const { return to_real<Tc>(p[i]); }
+};
+
+// The Lanczos step fused into the load: v_{k+1} = q - lz_a v_k - lz_b v_{k-1}, written over
+// v_{k-1} (every element is loaded exactly once) and returned for the transform.
+template <class Tc, class Tv>
+struct SrcLanczos;
+
+template <class Tc>
+struct SrcLanczos<Tc, double> {
+  const double *q, *vk;
+  double *vp;
+  double a, b;
+  __device__ __forceinline__ void prepare(const State *S) {
+    a = S->lz_a;
+    b = S->lz_b;
+  }
+  __device__ __forceinline__ Tc operator()(long long i) const {
+    const double v = q[i] - a * vk[i] - b * vp[i];
+    vp[i] = v;
+    return (Tc)v;
+  }
+};
+
+template <class Tc>
+struct SrcLanczos<Tc, df> {
+  const df *q, *vk;
+  df *vp;
+  df a, b;
+  __device__ __forceinline__ void prepare(const State *S) {
+    a = df_neg(S->dfs[DFS_LA]);
+    b = df_neg(S->dfs[DFS_LB]);
+  }
+  __device__ __forceinline__ Tc operator()(long long i) const {
+    const df qq = q[i];
+    float s = qq.hi, t = qq.lo;
+    dacc_prod(s, t, a, vk[i]);
+    dacc_prod(s, t, b, vp[i]);
+    const df v = df_from_sum(s, t);
+    vp[i] = v;
+    return to_real<Tc>(v);
+  }
+};
 
 // vector kernels
 cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,

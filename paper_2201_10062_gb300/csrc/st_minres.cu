@@ -113,19 +113,6 @@ namespace {
 // ------------------------------------------------------------------ double-float vectors
 // Mixed path: vhat, d and x are double-floats (hi + lo float32 pairs, ~46 significant bits);
 // the per-element arithmetic runs on the float32 pipes (see st_df.cuh).
-__device__ __forceinline__ void dacc_add(float &s, float &t, float p, float e) {
-  float ss, err;
-  two_sum(s, p, ss, err);
-  s = ss;
-  t += err + e;
-}
-__device__ __forceinline__ void dacc_prod(float &s, float &t, df a, df b) {
-  float p, e;
-  two_prod(a.hi, b.hi, p, e);
-  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  dacc_add(s, t, p, e);
-}
-
 __global__ void __launch_bounds__(kNT)
     k_lanczos_df(long long N, const df *__restrict__ q, const df *__restrict__ vk,
                  df *__restrict__ vprev, const State *S) {
@@ -577,9 +564,9 @@ cudaError_t launch_iteration(st_handle *h, int k, double *x) {
   cudaError_t e;
   e = launch_stencil<Tz>(g, SM_MINRES, zc, h->q, nullptr, h->S, h->partials, 0, st);
   if (e != cudaSuccess) return e;
-  e = launch_lanczos(g.N, h->q, h->V[c], h->V[o], h->S, st);
-  if (e != cudaSuccess) return e;
-  e = launch_prec<Tc, double, Tz>(g, h->pp, h->V[o], zn, h->S, TM_ITER, h->partials, st);
+  // Lanczos step (v_{k+1} over v_{k-1}) fused into the first transform of z_{k+1} = P^-1 v_{k+1}
+  e = launch_prec_lanczos<Tc, double, Tz>(g, h->pp, h->q, h->V[c], h->V[o], zn, h->S, h->partials,
+                                          st);
   if (e != cudaSuccess) return e;
   return launch_update<Tz>(g.N, zc, h->D[c], h->D[o], x, h->S, st);
 }
@@ -597,9 +584,7 @@ cudaError_t launch_iteration_mixed(st_handle *h, int k) {
   cudaError_t e;
   e = launch_stencil_df(g, zc, q, h->S, h->partials, st);
   if (e != cudaSuccess) return e;
-  e = launch_lanczos_df(g.N, q, V0, V1, h->S, st);
-  if (e != cudaSuccess) return e;
-  e = launch_prec<float, df, float>(g, h->pp, V1, zn, h->S, TM_ITER, h->partials, st);
+  e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st);
   if (e != cudaSuccess) return e;
   return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
 }

@@ -51,18 +51,19 @@ struct StockhamPasses {
     constexpr int REM = LOGL - LOGNS;
     if constexpr (REM > 0) {
       constexpr int LR = REM >= 3 ? 3 : REM;
-      stockham_pass_inplace<Tc, (1 << LR)>(buf, tws, 1 << LOGL, LOGL, 1 << LOGNS, LOGNS, PB, Ls,
-                                           tid, kNTD);
+      stockham_pass_inplace<Tc, (1 << LR), LOGL, LOGNS>(buf, tws, PB, Ls, tid, kNTD);
       StockhamPasses<Tc, LOGL, LOGNS + LR>::run(buf, tws, PB, Ls, tid);
     }
   }
 };
 
-template <class Tc, class Tin, class Tout, bool XL, int LOGL>
-__global__ void __launch_bounds__(kNTD, 2)
-    k_dst_space(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
+// float32 transforms: three 512-thread blocks per SM (at most 40 registers); float64: two
+template <class Tc, class Src, class Tout, bool XL, int LOGL>
+__global__ void __launch_bounds__(kNTD, sizeof(Tc) == 4 ? 3 : 2)
+    k_dst_space(Src src, Tout *out, int len, long long nlines, int mx, long long m,
                 const Tc *tw, int PB, const State *S, int gk) {
   if (gate_closed(S, gk)) return;
+  src.prepare(S);
   constexpr int logL = LOGL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 1 << logL;
@@ -90,9 +91,9 @@ __global__ void __launch_bounds__(kNTD, 2)
       const int pp = idx >> logH, e = idx & (half - 1);
       if (e >= len) continue;
       const int la = 2 * pp, lb = la + 1;
-      const Tin *p = in + (line0 + la) * len + e;
-      const Tc a = (la < nl) ? to_real<Tc>(p[0]) : Tc(0);
-      const Tc b = (lb < nl) ? to_real<Tc>(p[len]) : Tc(0);
+      const long long i0 = (line0 + la) * len + e;
+      const Tc a = (la < nl) ? src(i0) : Tc(0);
+      const Tc b = (lb < nl) ? src(i0 + len) : Tc(0);
       cpx<Tc> *bq = buf + pp * Ls;
       bq[fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
       bq[fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
@@ -102,22 +103,22 @@ __global__ void __launch_bounds__(kNTD, 2)
     // its elements: the column decomposition (plane k, column i) is done once per thread.
     const int pp = tid & (PB - 1), estep = kNTD >> logPB;
     const int la = 2 * pp, lb = la + 1;
-    const Tin *pa = nullptr, *pb = nullptr;
+    long long ia = -1, ib = -1;  // first element of each column line (-1: line absent)
     if (la < nl) {
       const int l = (int)line0 + la;
       const int k = l / mx, i = l - k * mx;
-      pa = in + (long long)k * m + i;
+      ia = (long long)k * m + i;
     }
     if (lb < nl) {
       const int l = (int)line0 + lb;
       const int k = l / mx, i = l - k * mx;
-      pb = in + (long long)k * m + i;
+      ib = (long long)k * m + i;
     }
     cpx<Tc> *bq = buf + pp * Ls;
     for (int e = tid >> logPB; e < len; e += estep) {
       const long long off = (long long)e * mx;
-      const Tc a = pa ? to_real<Tc>(pa[off]) : Tc(0);
-      const Tc b = pb ? to_real<Tc>(pb[off]) : Tc(0);
+      const Tc a = (ia >= 0) ? src(ia + off) : Tc(0);
+      const Tc b = (ib >= 0) ? src(ib + off) : Tc(0);
       bq[fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
       bq[fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
     }
@@ -406,13 +407,14 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
-// z = convert(v) (float64 or double-float to the transform type), elementwise
-template <class Tc, class Tin>
-__global__ void k_copy_to(long long N, const Tin *v, Tc *z, const State *S, int gk) {
+// z = source elements in the transform type (a conversion, or the fused Lanczos step)
+template <class Tc, class Src>
+__global__ void k_copy_to(long long N, Src src, Tc *z, const State *S, int gk) {
   if (gate_closed(S, gk)) return;
+  src.prepare(S);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
        e += (long long)gridDim.x * blockDim.x)
-    z[e] = to_real<Tc>(v[e]);
+    z[e] = src(e);
 }
 
 template <class Tc>
@@ -434,15 +436,15 @@ size_t time_smem(int n, int J) {
   return ((size_t)2 * n * J + 2 * (n + 1) + J) * sizeof(Tc);
 }
 
-template <class Tc, class Tin, class Tout, bool XL, int LOGL>
-cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, int mx, long long m,
+template <class Tc, class Src, class Tout, bool XL, int LOGL>
+cudaError_t launch_dst_l(Src in, Tout *out, int len, long long nlines, int mx, long long m,
                          const Tc *tw, const State *S, int gk, int pbshift, cudaStream_t st) {
   constexpr int L = 1 << LOGL;
   int PB = dst_pairs<Tc>(L) >> pbshift;
   if (PB < 1) PB = 1;
   const size_t sm = dst_smem<Tc>(L, PB);
   const long long blocks = (nlines + 2 * PB - 1) / (2 * PB);
-  auto kern = k_dst_space<Tc, Tin, Tout, XL, LOGL>;
+  auto kern = k_dst_space<Tc, Src, Tout, XL, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   prof_begin(XL ? KC_DSTX : KC_DSTY, st);
@@ -451,20 +453,20 @@ cudaError_t launch_dst_l(const Tin *in, Tout *out, int len, long long nlines, in
   return cudaGetLastError();
 }
 
-template <class Tc, class Tin, class Tout, bool XL>
-cudaError_t launch_dst(const Tin *in, Tout *out, int len, int L, long long nlines, int mx,
+template <class Tc, class Src, class Tout, bool XL>
+cudaError_t launch_dst(Src in, Tout *out, int len, int L, long long nlines, int mx,
                        long long m, const Tc *tw, const State *S, int gk, int pbshift,
                        cudaStream_t st) {
   switch (L) {
-    case 8: return launch_dst_l<Tc, Tin, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 16: return launch_dst_l<Tc, Tin, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 32: return launch_dst_l<Tc, Tin, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 64: return launch_dst_l<Tc, Tin, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 128: return launch_dst_l<Tc, Tin, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 256: return launch_dst_l<Tc, Tin, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 512: return launch_dst_l<Tc, Tin, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 1024: return launch_dst_l<Tc, Tin, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
-    case 2048: return launch_dst_l<Tc, Tin, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 8: return launch_dst_l<Tc, Src, Tout, XL, 3>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 16: return launch_dst_l<Tc, Src, Tout, XL, 4>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 32: return launch_dst_l<Tc, Src, Tout, XL, 5>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 64: return launch_dst_l<Tc, Src, Tout, XL, 6>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 128: return launch_dst_l<Tc, Src, Tout, XL, 7>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 256: return launch_dst_l<Tc, Src, Tout, XL, 8>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 512: return launch_dst_l<Tc, Src, Tout, XL, 9>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 1024: return launch_dst_l<Tc, Src, Tout, XL, 10>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
+    case 2048: return launch_dst_l<Tc, Src, Tout, XL, 11>(in, out, len, nlines, mx, m, tw, S, gk, pbshift, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -554,17 +556,19 @@ const Spec<float> &spec_of<float>(const PrecPlan &pp) {
   return pp.spec_f;
 }
 
-template <class Tc, class Tin, class Tout>
-cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
-                        int tmode, double *partials, cudaStream_t st) {
+// The stages of one preconditioner pass; `src` feeds the first one.
+template <class Tc, class Src, class Tout>
+cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, State *S, int tmode,
+                        double *partials, cudaStream_t st) {
   static_assert(sizeof(Tc) == sizeof(Tout), "in-place stages need Tout == Tc");
+  using Inner = SrcArray<Tc, Tout>;
   const int gk = gate_kind_of(tmode);
   cudaError_t e;
   if (pp.pcr) {
     // P_theta with a varying 1D coefficient: time DST, tridiagonal solves, time DST
     Tc *zc = reinterpret_cast<Tc *>(z);
     prof_begin(KC_AUX, st);
-    k_copy_to<Tc, Tin><<<152 * 8, kNT, 0, st>>>(g.N, v, zc, S, gk);
+    k_copy_to<Tc, Src><<<152 * 8, kNT, 0, st>>>(g.N, src, zc, S, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Jo = sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d;
@@ -581,12 +585,12 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
     return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
   }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
-  e = launch_dst<Tc, Tin, Tout, true>(v, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S, gk,
-                                      pp.dst_shift, st);
+  e = launch_dst<Tc, Src, Tout, true>(src, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
+                                      gk, pp.dst_shift, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
-    e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          S, gk, pp.dst_shift, st);
+    e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
+                                           tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
@@ -597,12 +601,30 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
                         sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
-    e = launch_dst<Tc, Tout, Tout, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, tw_of<Tc>(pp, false),
-                                          S, gk, pp.dst_shift, st);
+    e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
+                                           tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
-  return launch_dst<Tc, Tout, Tout, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
-                                          gk, pp.dst_shift, st);
+  return launch_dst<Tc, Inner, Tout, true>(Inner{z}, z, g.mx, pp.Lx, nx, g.mx, g.m,
+                                           tw_of<Tc>(pp, true), S, gk, pp.dst_shift, st);
+}
+
+template <class Tc, class Tin, class Tout>
+cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
+                        int tmode, double *partials, cudaStream_t st) {
+  return prec_stages<Tc>(g, pp, SrcArray<Tc, Tin>{v}, z, S, tmode, partials, st);
+}
+
+// One MINRES iteration's preconditioner pass with the Lanczos step fused into its first stage:
+// vnext <- q - lz_a vk - lz_b vnext, z <- P^-1 vnext.
+template <class Tc, class Tin, class Tout>
+cudaError_t launch_prec_lanczos(const Geom &g, const PrecPlan &pp, const Tin *q, const Tin *vk,
+                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st) {
+  SrcLanczos<Tc, Tin> src{};
+  src.q = q;
+  src.vk = vk;
+  src.vp = vnext;
+  return prec_stages<Tc>(g, pp, src, z, S, TM_ITER, partials, st);
 }
 
 // Autotuning helpers: the spatial DSTs (x then y, in place) and the FFMA time kernel alone,
@@ -613,18 +635,20 @@ cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *da
   cudaError_t e;
   if (fp32) {
     float *z = (float *)data;
-    e = launch_dst<float, float, float, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_f, nullptr,
-                                              GK_NONE, pp.dst_shift, st);
+    using A = SrcArray<float, float>;
+    e = launch_dst<float, A, float, true>(A{z}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_f, nullptr,
+                                          GK_NONE, pp.dst_shift, st);
     if (e == cudaSuccess && g.dim == 2)
-      e = launch_dst<float, float, float, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_f,
-                                                 nullptr, GK_NONE, pp.dst_shift, st);
+      e = launch_dst<float, A, float, false>(A{z}, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_f,
+                                             nullptr, GK_NONE, pp.dst_shift, st);
   } else {
     double *z = (double *)data;
-    e = launch_dst<double, double, double, true>(z, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_d,
-                                                 nullptr, GK_NONE, pp.dst_shift, st);
+    using A = SrcArray<double, double>;
+    e = launch_dst<double, A, double, true>(A{z}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_d,
+                                            nullptr, GK_NONE, pp.dst_shift, st);
     if (e == cudaSuccess && g.dim == 2)
-      e = launch_dst<double, double, double, false>(z, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_d,
-                                                    nullptr, GK_NONE, pp.dst_shift, st);
+      e = launch_dst<double, A, double, false>(A{z}, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_d,
+                                               nullptr, GK_NONE, pp.dst_shift, st);
   }
   return e;
 }
@@ -646,5 +670,16 @@ template cudaError_t launch_prec<float, double, float>(const Geom &, const PrecP
                                                        double *, cudaStream_t);
 template cudaError_t launch_prec<float, df, float>(const Geom &, const PrecPlan &, const df *,
                                                    float *, State *, int, double *, cudaStream_t);
+template cudaError_t launch_prec_lanczos<double, double, double>(const Geom &, const PrecPlan &,
+                                                                 const double *, const double *,
+                                                                 double *, double *, State *,
+                                                                 double *, cudaStream_t);
+template cudaError_t launch_prec_lanczos<float, double, float>(const Geom &, const PrecPlan &,
+                                                               const double *, const double *,
+                                                               double *, float *, State *,
+                                                               double *, cudaStream_t);
+template cudaError_t launch_prec_lanczos<float, df, float>(const Geom &, const PrecPlan &,
+                                                           const df *, const df *, df *, float *,
+                                                           State *, double *, cudaStream_t);
 
 }  // namespace st

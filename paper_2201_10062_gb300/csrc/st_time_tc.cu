@@ -10,13 +10,15 @@
 // power of two so that fp16 keeps its range; S is scaled by 8.
 //
 // One persistent block of 16 warps per SM keeps A (both parities, both pieces, 128 KB for
-// n = 256) in shared memory and walks column tiles of 32; the next tile's input is copied into
-// a staging buffer (cp.async) while the current one is transformed.  One thread issues
-// tcgen05.mma (M = 128, N = 32, K = 16, A and B from shared-memory descriptors, no swizzle,
-// K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals an mbarrier, and every
-// warp reads 32 rows x 16 columns of one parity's accumulators with tcgen05.ld.  Every wait on
-// the mbarrier is bounded; on timeout the block records ST_ERR_TIMEOUT in the MINRES state and
-// stops.
+// n = 256) in shared memory and walks column tiles of 32 as a two-stage software pipeline: the
+// two transforms have their own B operand buffer, tensor-memory accumulator and mbarrier, so the
+// second transform of tile i-1 runs on the tensor cores while tile i's first operand is built,
+// and the first transform of tile i runs while tile i-1 is scaled back and written out.  One
+// thread issues tcgen05.mma (M = 128, N = 32, K = 16, A and B from shared-memory descriptors, no
+// swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the mbarrier, and
+// every warp reads 32 rows x 16 columns of one parity's accumulators with tcgen05.ld.  Every
+// wait on an mbarrier is bounded; on timeout the block records ST_ERR_TIMEOUT in the MINRES
+// state and stops.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -129,47 +131,43 @@ __device__ __forceinline__ void fence_async_smem() {
 
 // Shared-memory layout, offsets in bytes from the dynamic base.
 struct TcSmem {
-  uint32_t sop, bop, ytile, stage, colscale, colinv, colmax, tmu, mbar, tmem, total;
+  uint32_t sop, bop1, bop2, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar1, mbar2, tmem;
+  uint32_t total;
 };
 
 constexpr int kYS = kTN + 1;  // padded row of the parity-split Y tile (conflict-free row writes)
 
 __host__ __device__ inline TcSmem tc_layout(int n) {
   const int h = n / 2;
+  const uint32_t bop = 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
   TcSmem L;
   uint32_t o = 0;
   L.sop = o;
   o += 2u * 2u * kM * h * 2u;  // [parity][piece][128][h] fp16
-  L.bop = o;
-  o += 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
+  L.bop1 = o;                  // operand of the first transform
+  o += bop;
+  L.bop2 = o;                  // operand of the second transform
+  o += bop;
   L.ytile = o;
   o += (uint32_t)n * kYS * 4u;  // float [parity][h][33]
-  L.stage = o;
-  o += (uint32_t)n * kTN * 4u;  // float [n][32]: raw input tile, filled by cp.async
   L.colscale = o;
   o += kTN * 4u;
-  L.colinv = o;
+  L.colinv1 = o;
+  o += kTN * 4u;
+  L.colinv2 = o;
   o += kTN * 4u;
   L.colmax = o;
   o += kTN * 4u;
   L.tmu = o;
   o += kTN * 4u;
-  L.mbar = o;
-  o += 16;
+  L.mbar1 = o;
+  o += 8;
+  L.mbar2 = o;
+  o += 8;
   L.tmem = o;
   o += 16;
   L.total = o;
   return L;
-}
-
-__device__ __forceinline__ void cp_async4(uint32_t saddr, const float *g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // fp16 (hi, lo) pieces of two floats, packed as half2 words
@@ -183,16 +181,17 @@ __device__ __forceinline__ void split_h2(float a, float b, uint32_t &hi, uint32_
 
 // Fold rows t and n-1-t of a float tile column (sum for odd k, difference for even k), scale each
 // column by a power of two so that its largest folded value lies in [2^13, 2^14), and write the
-// fp16 (hi, lo) pieces of both parities in canonical layout.  Thread (column c, block of 8 t)
-// keeps its folded values in registers between the maximum and the split, and stores each piece
-// as one 16-byte chunk (8 consecutive K elements of one row).  src(t, c) gives the value.
+// fp16 (hi, lo) pieces of both parities in canonical layout at `bop`, with 1/(scale * 8) in
+// `colinv`.  Thread (column c, block of 8 t) keeps its folded values in registers between the
+// maximum and the split, and stores each piece as one 16-byte chunk (8 consecutive K elements
+// of one row).  src(t, c) gives the value.
 template <class Src>
-__device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, int n, Src src,
-                                        int tid) {
+__device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
+                                        uint32_t colinv_off, int n, Src src, int tid) {
   const int h = n >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
   unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
   float *colscale = reinterpret_cast<float *>(smem + L.colscale);
-  float *colinv = reinterpret_cast<float *>(smem + L.colinv);
+  float *colinv = reinterpret_cast<float *>(smem + colinv_off);
   const int c = tid & (kTN - 1), tb = tid >> 5;
   if (tid < kTN) colmax[tid] = 0u;
   float u[8], d[8];
@@ -224,7 +223,7 @@ __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, in
   __syncthreads();
   if (tb < hb) {
     const float s = colscale[c];
-    unsigned char *bop = smem + L.bop;
+    unsigned char *bop = smem + bop_off;
     const uint32_t piece = (uint32_t)kTN * h * 2u;
     uint32_t uh[4], ul[4], dh[4], dl[4];
 #pragma unroll
@@ -240,13 +239,14 @@ __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, in
   }
 }
 
-// Issue the 2 parities x (h/16) K-steps x 3 piece products and commit to the mbarrier.
-__device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L, int h,
-                                           uint32_t tmem) {
-  const uint32_t sbase = smem_u32(smem + L.sop), bbase = smem_u32(smem + L.bop);
+// Issue the 2 parities x (h/16) K-steps x 3 piece products from the operand at `bop_off` into
+// the accumulators at tensor-memory column `dcol`, and commit to `mbar`.
+__device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
+                                           int h, uint32_t dcol, uint32_t mbar) {
+  const uint32_t sbase = smem_u32(smem + L.sop), bbase = smem_u32(smem + bop_off);
   const uint32_t apiece = (uint32_t)kM * h * 2u, bpiece = (uint32_t)kTN * h * 2u;
   for (int P = 0; P < 2; ++P) {
-    const uint32_t d = tmem + (uint32_t)(P * kTN);
+    const uint32_t d = dcol + (uint32_t)(P * kTN);
     const uint32_t a_hi = sbase + (2 * P) * apiece, a_lo = a_hi + apiece;
     const uint32_t b_hi = bbase + (2 * P) * bpiece, b_lo = b_hi + bpiece;
     for (int ks = 0; ks < h / 16; ++ks) {
@@ -256,7 +256,7 @@ __device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L,
       mma_f16(d, make_desc(a_lo + koff, h), make_desc(b_hi + koff, h), 1u);
     }
   }
-  mma_commit(smem_u32(smem + L.mbar));
+  mma_commit(mbar);
 }
 
 // Per-row (time frequency k) constants of 1/p(k, tau mu), hoisted out of the column loop.
@@ -298,27 +298,6 @@ __device__ __forceinline__ float inv_sym(const Spec<float> &sp, const SymRow &r,
   return rsqrtf(re * re + im * im);
 }
 
-// Load the raw [n][32] tile starting at column j0 into the stage buffer (asynchronous copies;
-// columns past the end are zeroed directly).
-__device__ __forceinline__ void prefetch_tile(unsigned char *smem, const TcSmem &L,
-                                              const float *data, int n, long long m, long long j0,
-                                              int tid) {
-  const int je = (int)min((long long)kTN, m - j0);
-  float *stage = reinterpret_cast<float *>(smem + L.stage);
-  const uint32_t sbase = smem_u32(stage);
-  for (int idx = tid; idx < n * kTN; idx += kNT) {
-    const int t = idx >> 5, c = idx & (kTN - 1);
-    if (c < je)
-      cp_async4(sbase + 4u * (uint32_t)idx, data + (long long)t * m + j0 + c);
-    else
-      stage[idx] = 0.f;
-  }
-  cp_async_commit();
-}
-
-// Per column tile: wait for the staged input, build B, start loading the next tile, MMA, scale
-// (energy), build B again from the scaled tile, MMA, and write the result back through the padded
-// tile with coalesced rows.
 __global__ void __launch_bounds__(kNT, 1)
     k_time_tc(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
               State *S, int tmode, double *__restrict__ partials, int gk) {
@@ -328,15 +307,13 @@ __global__ void __launch_bounds__(kNT, 1)
   const int h = n >> 1;
   const TcSmem L = tc_layout(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
-  const float *colinv = reinterpret_cast<const float *>(smem + L.colinv);
-  const float *stage = reinterpret_cast<const float *>(smem + L.stage);
+  const float *colinv1 = reinterpret_cast<const float *>(smem + L.colinv1);
+  const float *colinv2 = reinterpret_cast<const float *>(smem + L.colinv2);
   float *ytile = reinterpret_cast<float *>(smem + L.ytile);
   float *tmus = reinterpret_cast<float *>(smem + L.tmu);
+  const uint32_t mbar1 = smem_u32(smem + L.mbar1), mbar2 = smem_u32(smem + L.mbar2);
   const long long ntiles = (m + kTN - 1) / kTN;
-  if ((long long)blockIdx.x < ntiles)
-    prefetch_tile(smem, L, data, n, m, (long long)blockIdx.x * kTN, tid);
   // A operands: straight copy of the precomputed canonical image
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(sop_g);
@@ -345,11 +322,12 @@ __global__ void __launch_bounds__(kNT, 1)
     for (int i = tid; i < cnt; i += kNT) dst[i] = src[i];
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar2) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
                      smem_u32(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -358,16 +336,45 @@ __global__ void __launch_bounds__(kNT, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t phase = 0;
+  const uint32_t dcol1 = tmem, dcol2 = tmem + 2u * kTN;  // 64 accumulator columns each
+  uint32_t ph1 = 0, ph2 = 0;
   bool ok = true;
   float esum = 0.f, ecomp = 0.f;
   // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
   const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
   const int r = (q << 5) + lane;
   const int c0 = ch * 16;
-  const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN + c0);
+  const uint32_t lanes = (uint32_t)(q * 32) << 16, cview = (uint32_t)(P * kTN + c0);
   const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
   float *yrow = ytile + (P * h + r) * kYS;  // this thread's row of the parity-split tile
+  auto ycell = [&](int t, int c) -> float & { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
+  // second transform of the previous tile: accumulators -> Y tile (unscaled) -> columns of data
+  // (every issued MMA batch is waited for, with the bounded wait, before its resources are reused
+  // or released)
+  auto finish_second = [&](long long pj0, int pje) {
+    const bool w = __syncthreads_and(mbar_wait(mbar2, ph2) ? 1 : 0) != 0;
+    ok = ok && w;
+    ph2 ^= 1u;
+    fence_after();
+    float v[16];
+    tmem_ld16(dcol2 + lanes + cview, v);
+    if (r < h) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv2[c0 + c];
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // coalesced write-back: one warp per time row
+    for (int idx = tid; idx < n * kTN; idx += kNT) {
+      const int t = idx >> 5, c = idx & (kTN - 1);
+      if (c < pje) data[(long long)t * m + pj0 + c] = ycell(t, c);
+    }
+    __syncthreads();
+  };
+  bool pend = false;  // a second transform is in flight
+  long long pj0 = 0;
+  int pje = 0;
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long j0 = tile * kTN;
     const int je = (int)min((long long)kTN, m - j0);
@@ -380,71 +387,62 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       tmus[tid] = t;
     }
-    cp_async_wait_all();
-    __syncthreads();
-    // ---- first transform: B from the staged input
-    build_b(smem, L, n, [&](int t, int c) -> float { return stage[t * kTN + c]; }, tid);
+    // 1. first operand from global memory (the previous tile's second transform is running)
+    build_b(smem, L, L.bop1, L.colinv1, n,
+            [&](int t, int c) -> float { return (c < je) ? data[(long long)t * m + j0 + c] : 0.f; },
+            tid);
     fence_async_smem();
     __syncthreads();
     fence_after();
-    if (tid == 0) issue_mmas(smem, L, h, tmem);
-    // the stage buffer is free: start loading the next tile while the tensor cores work
-    if (tile + gridDim.x < ntiles)
-      prefetch_tile(smem, L, data, n, m, (tile + gridDim.x) * kTN, tid);
-    ok = __syncthreads_and(mbar_wait(smem_u32(mbar), phase) ? 1 : 0) != 0;
-    phase ^= 1u;
+    if (tid == 0) issue_mmas(smem, L, L.bop1, h, dcol1, mbar1);
+    // 2. while the first transform runs: finish the previous tile
+    if (pend) finish_second(pj0, pje);
+    // 3. first epilogue: unscale, spectral scaling, energy; scaled Y into the parity-split tile
+    {
+      const bool w = __syncthreads_and(mbar_wait(mbar1, ph1) ? 1 : 0) != 0;
+      ok = ok && w;
+    }
+    ph1 ^= 1u;
     fence_after();
-    float v[16];
-    tmem_ld16(tl, v);
-    // unscale, spectral scaling, energy; scaled Y into the parity-split tile
-    if (r < h) {
-      float rs = 0.f;
+    {
+      float v[16];
+      tmem_ld16(dcol1 + lanes + cview, v);
+      if (r < h) {
+        float rs = 0.f;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const float y = v[c] * colinv[c0 + c];
-        const float yi = y * inv_sym(sp, sr, tmus[c0 + c]);
-        if (c0 + c < je) rs = fmaf(y, yi, rs);
-        yrow[c0 + c] = yi;
+        for (int c = 0; c < 16; ++c) {
+          const float y = v[c] * colinv1[c0 + c];
+          const float yi = y * inv_sym(sp, sr, tmus[c0 + c]);
+          if (c0 + c < je) rs = fmaf(y, yi, rs);
+          yrow[c0 + c] = yi;
+        }
+        const float term = rs - ecomp;  // compensated running sum over rows and tiles
+        const float t = esum + term;
+        ecomp = (t - esum) - term;
+        esum = t;
       }
-      const float term = rs - ecomp;  // compensated running sum over rows and tiles
-      const float t = esum + term;
-      ecomp = (t - esum) - term;
-      esum = t;
     }
     fence_before();
     __syncthreads();
     fence_after();
-    // ---- second transform: B from the scaled tile (row t = k - 1 lives in parity t & 1)
-    build_b(smem, L, n,
-            [&](int t, int c) -> float { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; }, tid);
+    // 4. second operand from the scaled tile (row t = k - 1 lives in parity t & 1); start it
+    build_b(smem, L, L.bop2, L.colinv2, n, [&](int t, int c) -> float { return ycell(t, c); },
+            tid);
     fence_async_smem();
     __syncthreads();
     fence_after();
-    if (tid == 0 && ok) issue_mmas(smem, L, h, tmem);
-    ok = __syncthreads_and((ok && mbar_wait(smem_u32(mbar), phase)) ? 1 : 0) != 0;
-    phase ^= 1u;
-    fence_after();
-    tmem_ld16(tl, v);
-    if (r < h) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv[c0 + c];
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // coalesced write-back: one warp per time row
-    for (int idx = tid; idx < n * kTN; idx += kNT) {
-      const int t = idx >> 5, c = idx & (kTN - 1);
-      if (c < je) data[(long long)t * m + j0 + c] = ytile[((t & 1) * h + (t >> 1)) * kYS + c];
-    }
+    if (tid == 0 && ok) issue_mmas(smem, L, L.bop2, h, dcol2, mbar2);
+    pend = ok;
+    pj0 = j0;
+    pje = je;
   }
-  cp_async_wait_all();
+  if (pend) finish_second(pj0, pje);
   if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
   fence_before();
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
   }
   if (tmode != TM_NONE) {
     const double e = (double)esum - (double)ecomp;
