@@ -279,7 +279,7 @@ __device__ __forceinline__ df tauK_df(const float *__restrict__ b, long long p, 
   return A.get();
 }
 
-__global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restrict__ z,
+__global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__restrict__ z,
                                                     df *__restrict__ out, State *S,
                                                     double *__restrict__ partials, int kc) {
   __shared__ double red[32];
@@ -350,10 +350,58 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
       if (theta) bK0 = stiff(kb, b0);
       else if (kb > 0) b1 = center(kb - 1);
     }
-    for (int kA = k0; kA < k1; ++kA) {
+    // The loads of iteration kA + 1 (five-point planes of both walks) are issued before the
+    // arithmetic of iteration kA, so their latency overlaps it.
+    struct P5 {
+      float c, w, e, s, n;
+    };
+    auto load5 = [&](int k) -> P5 {
+      const float *b = z + (long long)k * m + p;
+      P5 r;
+      r.c = __ldg(b);
+      r.w = i > 0 ? __ldg(b - 1) : 0.f;
+      r.e = i < mx - 1 ? __ldg(b + 1) : 0.f;
+      r.s = (dim == 2 && j > 0) ? __ldg(b - mx) : 0.f;
+      r.n = (dim == 2 && j < my - 1) ? __ldg(b + mx) : 0.f;
+      return r;
+    };
+    // tau K at a plane, same face order as tauK_df
+    auto stiff5 = [&](const P5 &q, float c) -> df {
+      acc_df A{0.f, 0.f};
+      face_term(A, cw, c, q.w);
+      face_term(A, ce, c, q.e);
+      if (dim == 2) {
+        face_term(A, cs, c, q.s);
+        face_term(A, cn, c, q.n);
+      }
+      return A.get();
+    };
+    // planes read by iteration kA: A-walk plane kA; mirrored walk plane kB - 1 (theta) or kB
+    // plus the centre of kB - 2 (BDF2)
+    auto planes = [&](int kA, P5 &A, P5 &B, float &C) {
       const int kB = n - 1 - kA;
-      const float cA = center(kA);
-      const df KA = stiff(kA, cA);
+      A = load5(kA);
+      B = P5{0.f, 0.f, 0.f, 0.f, 0.f};
+      C = 0.f;
+      if (kB != kA) {
+        if (theta) {
+          if (kB > 0) B = load5(kB - 1);
+        } else {
+          B = load5(kB);
+          if (kB > 1) C = __ldg(z + (long long)(kB - 2) * m + p);
+        }
+      }
+    };
+    P5 pA{0.f, 0.f, 0.f, 0.f, 0.f}, pB = pA;
+    float pC = 0.f;
+    if (k0 < k1) planes(k0, pA, pB, pC);
+    for (int kA = k0; kA < k1; ++kA) {
+      P5 nA{0.f, 0.f, 0.f, 0.f, 0.f}, nB = nA;
+      float nC = 0.f;
+      if (kA + 1 < k1) planes(kA + 1, nA, nB, nC);
+      const int kB = n - 1 - kA;
+      const float cA = pA.c;
+      const df KA = stiff5(pA, cA);
       const df yA = combine(cA, a1, a2, KA, aK1);
       if (theta) {
         aK1 = KA;
@@ -369,15 +417,15 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
           float nb = 0.f;
           df nK = zero;
           if (kB > 0) {
-            nb = center(kB - 1);
-            nK = stiff(kB - 1, nb);
+            nb = pB.c;
+            nK = stiff5(pB, nb);
           }
           yB = combine(b0, nb, 0.f, bK0, nK);
           b0 = nb;
           bK0 = nK;
         } else {
-          const df KB = stiff(kB, b0);
-          const float nb2 = (kB > 1) ? center(kB - 2) : 0.f;
+          const df KB = stiff5(pB, b0);
+          const float nb2 = (kB > 1) ? pC : 0.f;
           yB = combine(b0, b1, nb2, KB, zero);
           b0 = b1;
           b1 = nb2;
@@ -389,6 +437,9 @@ __global__ void __launch_bounds__(kNT) k_stencil_df(Geom g, const float *__restr
         out[(long long)kA * m + p] = df_mul(s, yB);
         D.add_prod(yB, cA);
       }
+      pA = nA;
+      pB = nB;
+      pC = nC;
     }
   }
   const double acc = (double)D.s + (double)D.t;
