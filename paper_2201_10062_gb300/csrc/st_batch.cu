@@ -77,7 +77,7 @@ cudaError_t iteration(st_handle *h, int c, cudaStream_t st) {
   if ((e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials,
                                                  st)) != cudaSuccess)
     return e;
-  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
+  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, 0, st);
 }
 
 // refinement block: x (float64) <- x (df); r <- Y f_H - Y T x with decision; restart if asked

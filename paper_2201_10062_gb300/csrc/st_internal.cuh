@@ -288,7 +288,8 @@ __device__ __forceinline__ bool gate_closed(const State *S, int gk) {
 
 template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec_lanczos(const Geom &g, const PrecPlan &pp, const Tin *q, const Tin *vk,
-                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st);
+                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st,
+                                cudaEvent_t after_time = nullptr);
 template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z, State *S,
                         int tmode, double *partials, cudaStream_t st);
@@ -311,8 +312,10 @@ cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const 
                                State *S, double *partials, cudaStream_t st);
 cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
                               cudaStream_t st);
+// kidx > 0: run only if the Givens step of iteration kidx happened (S->k >= kidx); kidx = 0:
+// run while the MINRES run is active
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, cudaStream_t st);
+                             State *S, int kidx, cudaStream_t st);
 cudaError_t launch_flip_to_df(const Geom &g, const double *src, df *dst, cudaStream_t st);
 cudaError_t launch_df_to_double(long long N, const df *src, double *dst, cudaStream_t st);
 
@@ -409,6 +412,10 @@ struct st_handle {
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)
+  // ST_MIXED: the solution/direction update of iteration k runs on a side stream, concurrently
+  // with the inverse transforms of iteration k and the stencil of iteration k + 1
+  cudaStream_t ustream;
+  cudaEvent_t ev_givens[2], ev_update[2];  // indexed by the parity of k
 };
 
 

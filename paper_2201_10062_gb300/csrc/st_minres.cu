@@ -130,8 +130,11 @@ __global__ void __launch_bounds__(kNT)
 
 __global__ void __launch_bounds__(kNT)
     k_update_df(long long N, const float *__restrict__ z, const df *__restrict__ d1,
-                df *__restrict__ d2, df *__restrict__ x, const State *S) {
-  if (!S->active) return;
+                df *__restrict__ d2, df *__restrict__ x, const State *S, int kidx) {
+  // kidx > 0: the update of iteration kidx, launched on a side stream after its Givens step;
+  // it runs iff that step happened (the concurrent stencil of the next iteration may already
+  // have cleared `active`)
+  if (kidx > 0 ? S->k < kidx : !S->active) return;
   const df cz = S->dfs[DFS_DZ], c1 = S->dfs[DFS_D1], c2 = S->dfs[DFS_D2], cx = S->dfs[DFS_XC];
   for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
        i += (long long)gridDim.x * kNT) {
@@ -232,9 +235,9 @@ cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_o
 }
 
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, cudaStream_t st) {
+                             State *S, int kidx, cudaStream_t st) {
   prof_begin(KC_UPDATE, st);
-  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S);
+  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S, kidx);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -549,6 +552,11 @@ void free_handle(st_handle *h) {
   cudaFree(h->gfx);
   cudaFree(h->gfy);
   if (h->hS) cudaFreeHost(h->hS);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_givens[i]) cudaEventDestroy(h->ev_givens[i]);
+    if (h->ev_update[i]) cudaEventDestroy(h->ev_update[i]);
+  }
+  if (h->ustream) cudaStreamDestroy(h->ustream);
   prof_free(h->prof);
   delete h;
 }
@@ -584,9 +592,18 @@ cudaError_t launch_iteration_mixed(st_handle *h, int k) {
   cudaError_t e;
   e = launch_stencil_df(g, zc, q, h->S, h->partials, st);
   if (e != cudaSuccess) return e;
-  e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st);
+  // the preconditioner pass writes z_{k+1} over z_{k-1}, which the update of iteration k-1 (side
+  // stream) reads
+  if (k > 1 && (e = cudaStreamWaitEvent(st, h->ev_update[c], 0)) != cudaSuccess) return e;
+  e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st,
+                                            h->ev_givens[o]);
   if (e != cudaSuccess) return e;
-  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
+  // d_k, x: after the Givens step of this iteration, concurrently with the inverse transforms
+  // and the next stencil
+  if ((e = cudaStreamWaitEvent(h->ustream, h->ev_givens[o], 0)) != cudaSuccess) return e;
+  if ((e = launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, k, h->ustream)) != cudaSuccess)
+    return e;
+  return cudaEventRecord(h->ev_update[o], h->ustream);
 }
 
 int sync_state(st_handle *h) {
@@ -739,6 +756,7 @@ int mixed_iterate(st_handle *h) {
   for (;;) {
     const int k0 = h->hS->k;
     for (int i = 1; i <= chunk; ++i) ST_TRY(launch_iteration_mixed(h, k0 + i));
+    ST_TRY(cudaStreamWaitEvent(h->stream, h->ev_update[(k0 + chunk) & 1], 0));
     int r = sync_state(h);
     if (r) return r;
     const State &s = *h->hS;
@@ -1055,6 +1073,13 @@ int st_setup(const st_problem *prob, st_handle **out) {
   if (e == cudaSuccess)
     e = cudaMalloc(&h->gfy, ((size_t)g.my + 1) * g.mx * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&h->hS, sizeof(State));
+  if (e == cudaSuccess && h->mixed) {
+    e = cudaStreamCreateWithFlags(&h->ustream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&h->ev_givens[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_update[i], cudaEventDisableTiming);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemset(h->S, 0, sizeof(State));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(map_cuda(e));

@@ -557,9 +557,11 @@ const Spec<float> &spec_of<float>(const PrecPlan &pp) {
 }
 
 // The stages of one preconditioner pass; `src` feeds the first one.
+// after_time (optional) is recorded once the time kernel (which performs the MINRES scalar step)
+// has been enqueued.
 template <class Tc, class Src, class Tout>
 cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, State *S, int tmode,
-                        double *partials, cudaStream_t st) {
+                        double *partials, cudaStream_t st, cudaEvent_t after_time = nullptr) {
   static_assert(sizeof(Tc) == sizeof(Tout), "in-place stages need Tout == Tc");
   using Inner = SrcArray<Tc, Tout>;
   const int gk = gate_kind_of(tmode);
@@ -582,6 +584,7 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
     kern<<<g.n, kNT, sm, st>>>(zc, g.n, g.mx, g.cx, spec_of<Tc>(pp), S, tmode, partials, gk);
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
     return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
   }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
@@ -600,6 +603,7 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
     e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials, gk,
                         sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d, st);
   if (e != cudaSuccess) return e;
+  if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
   if (g.dim == 2) {
     e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
                                            tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
@@ -619,12 +623,13 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
 // vnext <- q - lz_a vk - lz_b vnext, z <- P^-1 vnext.
 template <class Tc, class Tin, class Tout>
 cudaError_t launch_prec_lanczos(const Geom &g, const PrecPlan &pp, const Tin *q, const Tin *vk,
-                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st) {
+                                Tin *vnext, Tout *z, State *S, double *partials, cudaStream_t st,
+                                cudaEvent_t after_time) {
   SrcLanczos<Tc, Tin> src{};
   src.q = q;
   src.vk = vk;
   src.vp = vnext;
-  return prec_stages<Tc>(g, pp, src, z, S, TM_ITER, partials, st);
+  return prec_stages<Tc>(g, pp, src, z, S, TM_ITER, partials, st, after_time);
 }
 
 // Autotuning helpers: the spatial DSTs (x then y, in place) and the FFMA time kernel alone,
@@ -673,13 +678,16 @@ template cudaError_t launch_prec<float, df, float>(const Geom &, const PrecPlan 
 template cudaError_t launch_prec_lanczos<double, double, double>(const Geom &, const PrecPlan &,
                                                                  const double *, const double *,
                                                                  double *, double *, State *,
-                                                                 double *, cudaStream_t);
+                                                                 double *, cudaStream_t,
+                                                                 cudaEvent_t);
 template cudaError_t launch_prec_lanczos<float, double, float>(const Geom &, const PrecPlan &,
                                                                const double *, const double *,
                                                                double *, float *, State *,
-                                                               double *, cudaStream_t);
+                                                               double *, cudaStream_t,
+                                                               cudaEvent_t);
 template cudaError_t launch_prec_lanczos<float, df, float>(const Geom &, const PrecPlan &,
                                                            const df *, const df *, df *, float *,
-                                                           State *, double *, cudaStream_t);
+                                                           State *, double *, cudaStream_t,
+                                                           cudaEvent_t);
 
 }  // namespace st
