@@ -412,8 +412,9 @@ struct st_handle {
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)
-  // ST_MIXED: the solution/direction update of iteration k runs on a side stream, concurrently
-  // with the inverse transforms of iteration k and the stencil of iteration k + 1
+  // ST_MIXED with ST_OVERLAP_UPDATE=1: the solution/direction update of iteration k runs on this
+  // side stream, concurrently with the inverse transforms of iteration k and the stencil of
+  // iteration k + 1 (null: serial order on the caller's stream)
   cudaStream_t ustream;
   cudaEvent_t ev_givens[2], ev_update[2];  // indexed by the parity of k
 };

@@ -328,3 +328,26 @@ def test_autotune_keeps_results(pkg, case, precision):
     assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-9 * (1 + 1e-6)
     assert _rel2(_h(u1), _h(u0)) <= 1e-6
     s.close()
+
+
+# ------------------------------------------------------------------ update on a side stream
+def test_overlapped_update_matches_serial(pkg, monkeypatch):
+    """ST_OVERLAP_UPDATE=1 moves the mixed solve's update to a side stream (event-ordered): same
+    iterations and the same solution as the serial order, and the oracle's residual."""
+    w = W.small_case(2, 63, 63, 40, scheme="theta", theta=0.5, varcoef=True, seed=90)
+    p = H.Problem.from_workload(w)
+    spec = _spec(pkg, w, precision="mixed")
+    s0 = pkg.Solver(spec)
+    fH = s0.st_assemble_rhs(_d(w.f), _d(w.u0))
+    u0, st0 = s0.st_solve(fH, tol=1e-9, maxit=600)
+    u0 = u0.clone()
+    s0.close()
+    monkeypatch.setenv("ST_OVERLAP_UPDATE", "1")
+    s1 = pkg.Solver(spec)
+    u1, st1 = s1.st_solve(fH, tol=1e-9, maxit=600)
+    assert st1["iterations"] == st0["iterations"] and st1["outer_steps"] == st0["outer_steps"]
+    assert torch.equal(u1, u0)
+    fH_or = H.rhs(p, w.f, w.u0)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, _h(u1).reshape(p.n, p.m))
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-9 * (1 + 1e-6)
+    s1.close()
