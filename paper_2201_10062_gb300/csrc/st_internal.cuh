@@ -260,6 +260,7 @@ struct PrecPlan {
   const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
   const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
+  const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D mixed), or null
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
 };
 
@@ -269,6 +270,9 @@ void time_tc_build_sop(int n, unsigned short *out);
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st);
+bool dst_tc_supported(int len);
+cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st);
 
 // energy mode of the time kernel's last block
 enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2, TM_RESTART = 3 };

@@ -384,6 +384,7 @@ size_t workspace_bytes(const Geom &g, bool mixed) {
   b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
   b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(df) + 256;  // df faces
   if (mixed && time_tc_supported(g.n)) b += time_tc_sop_halves(g.n) * 2;
+  if (mixed && g.dim == 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
   return b;
 }
 
@@ -500,7 +501,15 @@ int build_tables(st_handle *h) {
   for (size_t i = 0; i < cx.size(); ++i) cdf[i] = df_of_double(cx[i]);
   for (size_t i = 0; i < cy.size(); ++i) cdf[cx.size() + i] = df_of_double(cy[i]);
   const size_t o_cdf = (o_sop + sop.size() * sizeof(unsigned short) + 255) / 256 * 256;
-  const size_t bytes = o_cdf + cdf.size() * sizeof(df);
+  // fp16 S_my image for the tensor-core y-DST (2D, mixed precision, supported my)
+  std::vector<unsigned short> sopy;
+  if (p.precision == ST_MIXED && g.dim == 2 && dst_tc_supported(g.my) &&
+      !(no_tc && no_tc[0] == '1')) {
+    sopy.resize(time_tc_sop_halves(g.my));
+    time_tc_build_sop(g.my, sopy.data());
+  }
+  const size_t o_sopy = (o_cdf + cdf.size() * sizeof(df) + 255) / 256 * 256;
+  const size_t bytes = o_sopy + sopy.size() * sizeof(unsigned short);
   ST_TRY(cudaMalloc(&h->tables, bytes));
   ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice));
@@ -509,6 +518,9 @@ int build_tables(st_handle *h) {
                       cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + o_cdf, cdf.data(), cdf.size() * sizeof(df),
                     cudaMemcpyHostToDevice));
+  if (!sopy.empty())
+    ST_TRY(cudaMemcpy((char *)h->tables + o_sopy, sopy.data(),
+                      sopy.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
   const double *D = (const double *)h->tables;
   const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
   h->g.cx = D + o_cx;
@@ -522,6 +534,8 @@ int build_tables(st_handle *h) {
   pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr) ? 1 : 0;
   pp.sop = (sop.empty() || pp.pcr) ? nullptr
                        : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
+  pp.sop_y = sopy.empty() ? nullptr
+                          : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopy);
   pp.Lx = Lx;
   pp.Ly = Ly;
   pp.twx_d = D + o_twx;

@@ -592,8 +592,11 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
                                       gk, pp.dst_shift, st);
   if (e != cudaSuccess) return e;
   if (g.dim == 2) {
-    e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
-                                           tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
+    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
+      e = launch_dst_tc_y(reinterpret_cast<float *>(z), g, pp.sop_y, S, gk, st);
+    else
+      e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
+                                             tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
@@ -605,8 +608,11 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
   if (e != cudaSuccess) return e;
   if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
   if (g.dim == 2) {
-    e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
-                                           tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
+    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
+      e = launch_dst_tc_y(reinterpret_cast<float *>(z), g, pp.sop_y, S, gk, st);
+    else
+      e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
+                                             tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
   }
   return launch_dst<Tc, Inner, Tout, true>(Inner{z}, z, g.mx, pp.Lx, nx, g.mx, g.m,

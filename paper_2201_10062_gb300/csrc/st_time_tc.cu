@@ -132,6 +132,7 @@ __device__ __forceinline__ void fence_async_smem() {
 // Shared-memory layout, offsets in bytes from the dynamic base.
 struct TcSmem {
   uint32_t sop, bop1, bop2, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar1, mbar2, tmem;
+  uint32_t stage;  // spatial-DST kernel only: staged input tile
   uint32_t total;
 };
 
@@ -166,8 +167,47 @@ __host__ __device__ inline TcSmem tc_layout(int n) {
   o += 8;
   L.tmem = o;
   o += 16;
+  L.stage = 0;
   L.total = o;
   return L;
+}
+
+// Layout of the spatial-DST kernel for lines of `len` values (h = (len+1)/2 folded rows):
+// [A operands][B operand][Y tile][staged input][column scales][mbarrier][tmem address]
+__host__ __device__ inline TcSmem dst_layout(int len) {
+  const int h = (len + 1) / 2;
+  TcSmem L{};
+  uint32_t o = 0;
+  L.sop = o;
+  o += 2u * 2u * kM * h * 2u;
+  L.bop1 = o;
+  o += 2u * 2u * kTN * h * 2u;
+  L.ytile = o;
+  o += 2u * h * kYS * 4u;  // float [parity][h][33]
+  L.stage = o;
+  o += (uint32_t)len * kTN * 4u;  // float [len][32]
+  L.colscale = o;
+  o += kTN * 4u;
+  L.colinv1 = o;
+  o += kTN * 4u;
+  L.colmax = o;
+  o += kTN * 4u;
+  L.mbar1 = o;
+  o += 8;
+  L.tmem = o;
+  o += 8;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const float *g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // fp16 (hi, lo) pieces of two floats, packed as half2 words
@@ -185,10 +225,12 @@ __device__ __forceinline__ void split_h2(float a, float b, uint32_t &hi, uint32_
 // `colinv`.  Thread (column c, block of 8 t) keeps its folded values in registers between the
 // maximum and the split, and stores each piece as one 16-byte chunk (8 consecutive K elements
 // of one row).  src(t, c) gives the value.
+// For odd n the middle element (t = n-1-t) pairs with nothing: U = x_t, and D is multiplied by
+// zero columns of A (sin(pi k (n+1)/2 / (n+1)) = 0 for even k).
 template <class Src>
 __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
                                         uint32_t colinv_off, int n, Src src, int tid) {
-  const int h = n >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
+  const int h = (n + 1) >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
   unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
   float *colscale = reinterpret_cast<float *>(smem + L.colscale);
   float *colinv = reinterpret_cast<float *>(smem + colinv_off);
@@ -200,7 +242,7 @@ __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, ui
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int t = tb * 8 + q;
-      const float a = src(t, c), b = src(n - 1 - t, c);
+      const float a = src(t, c), b = (n - 1 - t == t) ? 0.f : src(n - 1 - t, c);
       u[q] = a + b;
       d[q] = a - b;
       mx = fmaxf(mx, fmaxf(fabsf(u[q]), fabsf(d[q])));
@@ -458,6 +500,118 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
+// Spatial DST-I along y on the tensor cores (float32 transforms of the mixed-precision
+// preconditioner, Sec. 3.1.1 steps 1 and 3 along y), in place: the lines of one time level at
+// fixed x are len = my values mx apart, and a tile is 32 adjacent lines (x0..x0+31) of one time
+// level.  Same folded two-parity product as the time kernel, with S_len: one transform, no
+// scaling.  The next tile's input is staged by cp.async while the current one is transformed.
+__global__ void __launch_bounds__(kNT, 1)
+    k_dst_tc_y(float *data, int len, int mx, long long m, long long nplanes,
+               const __half *sop_g, State *S, int gk) {
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = (len + 1) >> 1;
+  const TcSmem L = dst_layout(len);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+  const float *colinv = reinterpret_cast<const float *>(smem + L.colinv1);
+  float *stage = reinterpret_cast<float *>(smem + L.stage);
+  float *ytile = reinterpret_cast<float *>(smem + L.ytile);
+  const uint32_t mbar = smem_u32(smem + L.mbar1);
+  const int tpp = (mx + kTN - 1) / kTN;  // tiles per time level
+  const long long ntiles = nplanes * tpp;
+  auto tile_at = [&](long long tile, long long &base, int &je) {
+    const long long t = tile / tpp;
+    const int x0 = (int)(tile - t * tpp) * kTN;
+    base = t * m + x0;
+    je = min(kTN, mx - x0);
+  };
+  auto prefetch = [&](long long tile) {
+    long long base;
+    int je;
+    tile_at(tile, base, je);
+    const uint32_t sbase = smem_u32(stage);
+    for (int idx = tid; idx < len * kTN; idx += kNT) {
+      const int e = idx >> 5, c = idx & (kTN - 1);
+      if (c < je)
+        cp_async4(sbase + 4u * (uint32_t)idx, data + base + (long long)e * mx + c);
+      else
+        stage[idx] = 0.f;
+    }
+    cp_async_commit();
+  };
+  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x);
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(sop_g);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem + L.sop);
+    const int cnt = (int)((2u * 2u * kM * h * 2u) / 16u);
+    for (int i = tid; i < cnt; i += kNT) dst[i] = src[i];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t phase = 0;
+  bool ok = true;
+  // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
+  const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
+  const int r = (q << 5) + lane;
+  const int c0 = ch * 16;
+  const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN + c0);
+  const bool row_ok = r < h && (P == 0 ? 2 * r + 1 : 2 * r + 2) <= len;
+  float *yrow = ytile + (P * h + r) * kYS;
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    long long base;
+    int je;
+    tile_at(tile, base, je);
+    cp_async_wait_all();
+    __syncthreads();
+    build_b(smem, L, L.bop1, L.colinv1, len,
+            [&](int t, int c) -> float { return stage[t * kTN + c]; }, tid);
+    fence_async_smem();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) issue_mmas(smem, L, L.bop1, h, tmem, mbar);
+    // the stage buffer is free: load the next tile while the tensor cores work
+    if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+    fence_after();
+    float v[16];
+    tmem_ld16(tl, v);
+    if (row_ok) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv[c0 + c];
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // coalesced write-back: output row e holds coefficient k = e + 1 (parity e & 1)
+    for (int idx = tid; idx < len * kTN; idx += kNT) {
+      const int e = idx >> 5, c = idx & (kTN - 1);
+      if (c < je) data[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+    }
+  }
+  cp_async_wait_all();
+  if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  }
+}
+
 }  // namespace
 
 // n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
@@ -466,20 +620,23 @@ bool time_tc_supported(int n) {
   return n >= 32 && n <= 256 && (n % 32) == 0 && tc_layout(n).total + 1024u <= 227u * 1024u;
 }
 
-size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * (n / 2); }
+size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * ((n + 1) / 2); }
 
-// Host: canonical fp16 image of 8 S_P (hi, lo) for both parities.
-void time_tc_build_sop(int n, unsigned short *out) {
-  const int h = n / 2;
+// Host: canonical fp16 image of 8 S_len restricted to each parity of k (rows k = 2r+1 and 2r+2,
+// k <= len; columns t = 1..h, h = (len+1)/2), hi and lo pieces.  Serves the time kernel
+// (len = n, even) and the spatial kernel (len = my, odd).
+void time_tc_build_sop(int len, unsigned short *out) {
+  const int h = (len + 1) / 2;
   const double PI = 3.14159265358979323846;
-  const double sn = std::sqrt(2.0 / (n + 1));
+  const double sn = std::sqrt(2.0 / (len + 1));
   const size_t piece = (size_t)kM * h;  // halves per piece
   for (size_t i = 0; i < 4 * piece; ++i) out[i] = 0;
   for (int P = 0; P < 2; ++P)
     for (int r = 0; r < h; ++r) {
       const int k = (P == 0) ? 2 * r + 1 : 2 * r + 2;
+      if (k > len) continue;
       for (int t = 0; t < h; ++t) {
-        const double v = kSScale * sn * std::sin(PI * (double)k * (t + 1) / (n + 1));
+        const double v = kSScale * sn * std::sin(PI * (double)k * (t + 1) / (len + 1));
         const __half hi = __float2half_rn((float)v);
         const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
         const uint32_t off = canon_off(r, t, h) / 2;  // in halves
@@ -488,6 +645,14 @@ void time_tc_build_sop(int n, unsigned short *out) {
         out[(2 * P + 1) * piece + off] = rl.x;
       }
     }
+}
+
+// len + 1 in {32, 64, 128, 256} (h = 16..128 folded rows, a multiple of the MMA K step) and the
+// layout within 227 KB with 1 KB of static shared memory
+bool dst_tc_supported(int len) {
+  const int L1 = len + 1;
+  return (L1 == 32 || L1 == 64 || L1 == 128 || L1 == 256) &&
+         dst_layout(len).total + 1024u <= 227u * 1024u;
 }
 
 int time_tc_grid() {
@@ -515,6 +680,22 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
   k_time_tc<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
                                         reinterpret_cast<const __half *>(sop), S, tmode, partials,
                                         gk);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st) {
+  const uint32_t smem_bytes = dst_layout(g.my).total;
+  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)g.n * ((g.mx + kTN - 1) / kTN);
+  int grid = time_tc_grid();
+  if (ntiles < grid) grid = (int)ntiles;
+  prof_begin(KC_DSTY, st);
+  k_dst_tc_y<<<grid, kNT, smem_bytes, st>>>(data, g.my, g.mx, g.m, (long long)g.n,
+                                            reinterpret_cast<const __half *>(sop), S, gk);
   prof_end(st);
   return cudaGetLastError();
 }

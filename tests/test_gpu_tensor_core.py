@@ -1,5 +1,6 @@
-"""The tensor-core (tcgen05) time-DST kernel of the mixed-precision preconditioner against the
-oracle and against the float32 FFMA kernel it replaces, on the lengths it supports."""
+"""The tensor-core (tcgen05) kernels of the mixed-precision preconditioner (time DST with the
+spectral scaling; spatial DST along y) against the oracle and against the float32 FFMA /
+shared-memory FFT kernels they replace (ST_DISABLE_TENSOR_CORES=1), on the lengths they support."""
 import os
 
 import numpy as np
@@ -28,14 +29,16 @@ def _rel2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-# n supported by the tensor-core path (multiples of 32 up to 256); spatial sizes with ragged
-# 32-column tiles (m = 63, 15*31, 63*63, 127*127)
+# n supported by the tensor-core time path (multiples of 32 up to 256) and my + 1 in
+# {32, ..., 256} for the tensor-core y-DST; spatial sizes with ragged 32-column tiles
+# (m = 63, 15*31, 63*63, 127*127, 31*255); the last case keeps the FFMA time kernel (n = 40)
 @pytest.mark.parametrize("dim,mx,my,n,scheme,theta", [
     (1, 63, 1, 32, "theta", 1.0),
     (2, 15, 31, 64, "theta", 0.5),
     (2, 63, 63, 128, "bdf2", 1.0),
     (2, 127, 127, 256, "theta", 0.5),
     (2, 31, 31, 96, "theta", 0.3),
+    (2, 31, 255, 40, "theta", 0.5),
 ])
 def test_tc_time_dst_matches_oracle_and_ffma(pkg, dim, mx, my, n, scheme, theta):
     w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=True, seed=n + mx)
