@@ -19,6 +19,7 @@ struct Geom {
   const double *cy;     // [my+1][mx]  tau * a(y-face) / hy^2 (NULL in 1D)
   const df *cxd, *cyd;  // the same coefficients as double-float pairs (mixed-precision stencil)
   df th_d, omth_d;      // theta and 1 - theta as double-float pairs
+  int th_exact;         // theta in {0, 1/2, 1}: products with theta, 1 - theta are exact scalings
   int st_target;        // stencil launch: target number of blocks (0: default), set by autotune
 };
 

@@ -530,6 +530,7 @@ int build_tables(st_handle *h) {
   h->g.cyd = (g.dim == 2) ? CD + cx.size() : nullptr;
   h->g.th_d = df_of_double(h->g.theta);
   h->g.omth_d = df_of_double(1.0 - h->g.theta);
+  h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
   PrecPlan &pp = h->pp;
   pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr) ? 1 : 0;
   pp.sop = (sop.empty() || pp.pcr) ? nullptr
@@ -660,17 +661,35 @@ int minres_start(st_handle *h, double target, int maxit) {
 }
 
 // Run iterations until the device sets finish (or deactivates); returns with hS current.
+// Iterations to enqueue before the next host check.  Iterations enqueued past convergence are
+// gated no-ops on the device but still cost their launches, so once a chunk has shown the
+// convergence rate of the estimate, the next chunk is the count that rate needs to reach the
+// target, plus one (between 2 and 16); until then the schedule doubles from 4.
+int next_chunk(int chunk, int dk, double est0, double est1, double target) {
+  if (dk > 0 && est0 > 0.0 && est1 > 0.0 && est1 < est0 && target > 0.0) {
+    if (est1 <= target) return 2;
+    const double rate = std::log(est1 / est0) / dk;  // log decrease per iteration (< 0)
+    const double need = std::log(target / est1) / rate;
+    const int c = (int)std::ceil(need) + 1;
+    return c < 2 ? 2 : (c > 16 ? 16 : c);
+  }
+  return chunk < 16 ? 2 * chunk : 16;
+}
+
 template <class Tz, class Tc>
 int minres_iterate(st_handle *h, double *x) {
   int chunk = 4;
+  bool known = false;  // hS holds the state of the last check (k, est)
   for (;;) {
     const int k0 = h->hS->k;
+    const double est0 = known ? h->hS->est : 0.0;
     for (int i = 1; i <= chunk; ++i) ST_TRY((launch_iteration<Tz, Tc>(h, k0 + i, x)));
     int r = sync_state(h);
     if (r) return r;
     const State &s = *h->hS;
     if (s.status != 0 || s.finish || !s.active) return ST_OK;
-    if (chunk < 16) chunk *= 2;
+    chunk = next_chunk(chunk, s.k - k0, est0, s.est, s.target);
+    known = true;
   }
 }
 
@@ -772,15 +791,18 @@ int mixed_start(st_handle *h, double target, int maxit) {
 
 int mixed_iterate(st_handle *h) {
   int chunk = 4;
+  bool known = false;
   for (;;) {
     const int k0 = h->hS->k;
+    const double est0 = known ? h->hS->est : 0.0;
     for (int i = 1; i <= chunk; ++i) ST_TRY(launch_iteration_mixed(h, k0 + i));
     if (h->ustream) ST_TRY(cudaStreamWaitEvent(h->stream, h->ev_update[(k0 + chunk) & 1], 0));
     int r = sync_state(h);
     if (r) return r;
     const State &s = *h->hS;
     if (s.status != 0 || s.finish || !s.active) return ST_OK;
-    if (chunk < 16) chunk *= 2;
+    chunk = next_chunk(chunk, s.k - k0, est0, s.est, s.target);
+    known = true;
   }
 }
 

@@ -322,8 +322,15 @@ __global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__re
         float dh, dl;
         two_sum(c, -c1, dh, dl);
         A.add(dh, dl);
-        A.add_prod(th, Kc);
-        A.add_prod(omth, K1);
+        if (g.th_exact) {
+          // theta and 1 - theta are 0, 1/2 or 1: the products are exact scalings (the same
+          // values add_prod gives), and a zero weight adds nothing
+          A.add(th.hi * Kc.hi, th.hi * Kc.lo);
+          if (omth.hi != 0.f) A.add(omth.hi * K1.hi, omth.hi * K1.lo);
+        } else {
+          A.add_prod(th, Kc);
+          A.add_prod(omth, K1);
+        }
       } else {
         float pp, e;
         two_prod(1.5f, c, pp, e);
