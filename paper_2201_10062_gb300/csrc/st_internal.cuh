@@ -356,7 +356,9 @@ struct SrcLanczos<Tc, double> {
     b = S->lz_b;
   }
   __device__ __forceinline__ Tc operator()(long long i) const {
-    const double v = q[i] - a * vk[i] - b * vp[i];
+    // q and v_k are read-only in this pass: read-only-cache loads, free to move ahead of the
+    // stores to v_{k-1}
+    const double v = __ldg(q + i) - a * __ldg(vk + i) - b * vp[i];
     vp[i] = v;
     return (Tc)v;
   }
@@ -372,9 +374,11 @@ struct SrcLanczos<Tc, df> {
     b = df_neg(S->dfs[DFS_LB]);
   }
   __device__ __forceinline__ Tc operator()(long long i) const {
-    const df qq = q[i];
-    float s = qq.hi, t = qq.lo;
-    dacc_prod(s, t, a, vk[i]);
+    // q and v_k are read-only in this pass (see the float64 source)
+    const float2 q2 = __ldg(reinterpret_cast<const float2 *>(q) + i);
+    const float2 v2 = __ldg(reinterpret_cast<const float2 *>(vk) + i);
+    float s = q2.x, t = q2.y;
+    dacc_prod(s, t, a, df{v2.x, v2.y});
     dacc_prod(s, t, b, vp[i]);
     const df v = df_from_sum(s, t);
     vp[i] = v;
