@@ -315,8 +315,6 @@ cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const dou
 // done; r = Y f_H - Y T x into r_out and, in the last block, the done/restart decision
 cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const double *fH,
                                State *S, double *partials, cudaStream_t st);
-cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
-                              cudaStream_t st);
 // kidx > 0: run only if the Givens step of iteration kidx happened (S->k >= kidx); kidx = 0:
 // run while the MINRES run is active
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
@@ -387,8 +385,6 @@ struct SrcLanczos<Tc, df> {
 };
 
 // vector kernels
-cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,
-                           State *S, cudaStream_t st);
 template <class Tz>
 cudaError_t launch_update(long long N, const Tz *z, const double *d1, double *d2_out, double *x,
                           State *S, cudaStream_t st);

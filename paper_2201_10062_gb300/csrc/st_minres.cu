@@ -2,14 +2,16 @@
 // the preconditioned MINRES loop (Paige-Saunders recurrences with device-resident scalars) and
 // the mixed-precision iterative refinement around it.
 //
-// One MINRES iteration k (1-based) is four launches on the handle's stream:
+// One MINRES iteration k (1-based) is, on the handle's stream:
 //   1. stencil:  p = Y T z_k / beta_k and alpha_k = <p, z_k/beta_k>            (st_stencil.cu)
-//   2. lanczos:  vhat_{k+1} = p - (alpha_k/beta_k) vhat_k - (beta_k/beta_{k-1}) vhat_{k-1}
-//   3. prec:     z_{k+1} = P^-1 vhat_{k+1}, beta_{k+1}^2 = <vhat_{k+1}, z_{k+1}>, Givens step (st_prec.cu)
-//   4. update:   d_k = (z_k/beta_k - delta d_{k-1} - eps d_{k-2})/rho,  x += c eta d_k
-// Scalars never leave the device inside the loop; the host reads the state every few
-// iterations to learn whether the device-side stopping test has fired.  Kernels launched after
-// that point return at entry, so the host may run ahead by a few iterations at no cost.
+//   2. prec:     vhat_{k+1} = p - (alpha_k/beta_k) vhat_k - (beta_k/beta_{k-1}) vhat_{k-1}
+//                fused into the load of the first spatial DST, then z_{k+1} = P^-1 vhat_{k+1},
+//                beta_{k+1}^2 = <vhat_{k+1}, z_{k+1}> and the Givens step (st_prec.cu,
+//                st_time_tc.cu)
+//   3. update:   d_k = (z_k/beta_k - delta d_{k-1} - eps d_{k-2})/rho,  x += c eta d_k
+// Scalars never leave the device inside the loop; the host reads the state after each chunk of
+// iterations to learn whether the device-side stopping test has fired, and sizes the next chunk
+// from the observed convergence rate.  Kernels launched after that point return at entry.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -30,29 +32,6 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kStreamBlocks = 152 * 8;
-
-__global__ void __launch_bounds__(kNT)
-    k_lanczos(long long N, const double *__restrict__ q, const double *__restrict__ vk,
-              double *__restrict__ vprev, const State *S) {
-  if (!S->active) return;
-  const double a = S->lz_a, b = S->lz_b;
-  const long long N2 = N >> 1;
-  const double2 *q2 = reinterpret_cast<const double2 *>(q);
-  const double2 *v2 = reinterpret_cast<const double2 *>(vk);
-  double2 *p2 = reinterpret_cast<double2 *>(vprev);
-  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N2;
-       i += (long long)gridDim.x * kNT) {
-    const double2 qq = q2[i], vv = v2[i], pp = p2[i];
-    double2 r;
-    r.x = qq.x - a * vv.x - b * pp.x;
-    r.y = qq.y - a * vv.y - b * pp.y;
-    p2[i] = r;
-  }
-  if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const long long i = N - 1;
-    vprev[i] = q[i] - a * vk[i] - b * vprev[i];
-  }
-}
 
 template <class Tz>
 __global__ void __launch_bounds__(kNT)
@@ -113,21 +92,6 @@ namespace {
 // ------------------------------------------------------------------ double-float vectors
 // Mixed path: vhat, d and x are double-floats (hi + lo float32 pairs, ~46 significant bits);
 // the per-element arithmetic runs on the float32 pipes (see st_df.cuh).
-__global__ void __launch_bounds__(kNT)
-    k_lanczos_df(long long N, const df *__restrict__ q, const df *__restrict__ vk,
-                 df *__restrict__ vprev, const State *S) {
-  if (!S->active) return;
-  const df a = df_neg(S->dfs[DFS_LA]), b = df_neg(S->dfs[DFS_LB]);
-  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
-       i += (long long)gridDim.x * kNT) {
-    const df qq = q[i], vv = vk[i], pp = vprev[i];
-    float s = qq.hi, t = qq.lo;
-    dacc_prod(s, t, a, vv);
-    dacc_prod(s, t, b, pp);
-    vprev[i] = df_from_sum(s, t);
-  }
-}
-
 __global__ void __launch_bounds__(kNT)
     k_update_df(long long N, const float *__restrict__ z, const df *__restrict__ d1,
                 df *__restrict__ d2, df *__restrict__ x, const State *S, int kidx) {
@@ -195,14 +159,6 @@ void prof_end(cudaStream_t st) {
   }
 }
 
-cudaError_t launch_lanczos(long long N, const double *q, const double *vk, double *vkm1_out,
-                           State *S, cudaStream_t st) {
-  prof_begin(KC_LANCZOS, st);
-  k_lanczos<<<kStreamBlocks, kNT, 0, st>>>(N, q, vk, vkm1_out, S);
-  prof_end(st);
-  return cudaGetLastError();
-}
-
 template <class Tz>
 cudaError_t launch_update(long long N, const Tz *z, const double *d1, double *d2_out, double *x,
                           State *S, cudaStream_t st) {
@@ -222,14 +178,6 @@ cudaError_t launch_flip(const Geom &g, const double *src, double *dst, cudaStrea
 cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
   prof_begin(KC_AUX, st);
   k_fill<<<kStreamBlocks, kNT, 0, st>>>(N, p, v);
-  prof_end(st);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_lanczos_df(long long N, const df *q, const df *vk, df *vkm1_out, State *S,
-                              cudaStream_t st) {
-  prof_begin(KC_LANCZOS, st);
-  k_lanczos_df<<<kStreamBlocks, kNT, 0, st>>>(N, q, vk, vkm1_out, S);
   prof_end(st);
   return cudaGetLastError();
 }
