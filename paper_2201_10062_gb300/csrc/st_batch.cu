@@ -267,7 +267,8 @@ int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_d
     S.tol_outer = tol;
     S.maxit_total = maxit;
     S.maxit = maxit;
-    S.target = std::max(0.5 * tol, 1e-6);
+    S.inner_floor = inner_floor();
+    S.target = std::max(0.5 * tol, S.inner_floor);
     BT_TRY(cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, s));
     BT_TRY(cudaMemsetAsync(h->Xdf, 0, g.N * sizeof(df), s));
     BT_TRY(cudaMemsetAsync(u_devs[i], 0, g.N * sizeof(double), s));

@@ -57,6 +57,7 @@ struct State {
   // device-driven refinement (batched solves): after an inner run finishes, the residual
   // kernel decides between done and a restart of the inner run
   double tol_outer;                    // requested ||r||/||b||
+  double inner_floor;                  // lowest target of an inner run (device-side restarts)
   double rho;                          // last true relative residual
   int done, restart, total, outer, maxit_total;
   int pad2;
@@ -264,6 +265,11 @@ struct PrecPlan {
   const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D mixed), or null
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
 };
+
+// Lowest relative target of an inner (float32-preconditioned) MINRES run of the mixed solve:
+// 1e-7, where the float32 preconditioner still lets the estimate fall steadily (ST_INNER_FLOOR
+// overrides it, for measurements).
+double inner_floor();
 
 bool time_tc_supported(int n);
 size_t time_tc_sop_halves(int n);

@@ -138,6 +138,15 @@ __global__ void k_df_to_double(long long N, const df *__restrict__ src, double *
 }
 }  // namespace
 
+double inner_floor() {
+  static const double f = [] {
+    const char *v = std::getenv("ST_INNER_FLOOR");
+    const double x = v ? std::atof(v) : 0.0;
+    return (x > 0.0 && x < 1.0) ? x : 1e-7;
+  }();
+  return f;
+}
+
 thread_local Prof *t_prof = nullptr;
 
 void prof_begin(int cls, cudaStream_t st) {
@@ -776,7 +785,7 @@ int solve_mixed(st_handle *h, const double *fH, double *x, double tol, int maxit
   int status = 0;
   while (total < maxit) {
     ++outer;
-    const double target = std::max(0.5 * tol / rho, 1e-6);
+    const double target = std::max(0.5 * tol / rho, inner_floor());
     h->hS->bnorm2 = bn2;
     r = mixed_start(h, target, maxit - total);
     if (r) return r;

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
             if (S->status == 0) S->status = ST_ERR_NOT_CONVERGED;
           } else {
             const double t = 0.5 * S->tol_outer / rho;
-            S->target = t > 1e-6 ? t : 1e-6;
+            S->target = t > S->inner_floor ? t : S->inner_floor;
             S->maxit = S->maxit_total - S->total;
             S->k = 0;
             S->finish = 0;
