@@ -263,6 +263,8 @@ struct PrecPlan {
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
   const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
   const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D mixed), or null
+  const unsigned short *sop_long;  // streamed S_n chunks for the tensor-core time kernel when
+                                   // 256 < n <= 512 (mixed), or null
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
 };
 
@@ -278,6 +280,12 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st);
 bool dst_tc_supported(int len);
+bool time_tc_long_supported(int n);
+size_t time_tc_long_bytes(int n);
+void time_tc_long_build(int n, unsigned short *out);
+cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &sp,
+                                const unsigned short *A, State *S, int tmode, double *partials,
+                                int gk, cudaStream_t st);
 cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st);
 

@@ -341,6 +341,8 @@ size_t workspace_bytes(const Geom &g, bool mixed) {
   b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
   b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(df) + 256;  // df faces
   if (mixed && time_tc_supported(g.n)) b += time_tc_sop_halves(g.n) * 2;
+  if (mixed && !time_tc_supported(g.n) && time_tc_long_supported(g.n))
+    b += time_tc_long_bytes(g.n) + 256;
   if (mixed && g.dim == 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
   return b;
 }
@@ -448,9 +450,16 @@ int build_tables(st_handle *h) {
   // fp16 S_n image for the tensor-core time kernel (mixed precision, supported n)
   std::vector<unsigned short> sop;
   const char *no_tc = std::getenv("ST_DISABLE_TENSOR_CORES");
-  if (p.precision == ST_MIXED && time_tc_supported(n) && !(no_tc && no_tc[0] == '1')) {
+  const bool use_tc = p.precision == ST_MIXED && !(no_tc && no_tc[0] == '1');
+  bool long_tc = false;
+  if (use_tc && time_tc_supported(n)) {
     sop.resize(time_tc_sop_halves(n));
     time_tc_build_sop(n, sop.data());
+  } else if (use_tc && time_tc_long_supported(n)) {
+    // streamed chunks for 256 < n <= 512, in the same slot of the table allocation
+    sop.resize(time_tc_long_bytes(n) / 2);
+    time_tc_long_build(n, sop.data());
+    long_tc = true;
   }
   const size_t o_sop = (bytes_d + bytes_f + 255) / 256 * 256;
   // double-float copies of the face coefficients
@@ -490,8 +499,11 @@ int build_tables(st_handle *h) {
   h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
   PrecPlan &pp = h->pp;
   pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr) ? 1 : 0;
-  pp.sop = (sop.empty() || pp.pcr) ? nullptr
-                       : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
+  const unsigned short *sop_img =
+      (sop.empty() || pp.pcr) ? nullptr
+                              : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
+  pp.sop = long_tc ? nullptr : sop_img;
+  pp.sop_long = long_tc ? sop_img : nullptr;
   pp.sop_y = sopy.empty() ? nullptr
                           : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopy);
   pp.Lx = Lx;
@@ -974,7 +986,7 @@ int st_autotune(st_handle *h, int reps) {
     h->pp.dst_shift = bs;
   }
   // 3. float32/float64 FFMA time kernel (the tensor-core kernel has a fixed tile): column tile
-  if (!h->pp.sop) {
+  if (!h->pp.sop && !h->pp.sop_long) {
     const int cand[] = {16, 32, 48, 64};
     float best = 1e30f;
     int bj = 0;

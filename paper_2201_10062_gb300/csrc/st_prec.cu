@@ -602,6 +602,9 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
     e = launch_time_tc(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop, S, tmode, partials, gk,
                        st);
+  else if (sizeof(Tc) == sizeof(float) && pp.sop_long != nullptr)
+    e = launch_time_tc_long(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop_long, S, tmode,
+                            partials, gk, st);
   else
     e = launch_time<Tc>(reinterpret_cast<Tc *>(z), g, spec_of<Tc>(pp), S, tmode, 0, partials, gk,
                         sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d, st);

@@ -596,6 +596,343 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
+// ------------------------------------------------------------------ long time axes (n > 256)
+// For 256 < n <= 512 the S_n operand (both parities, two 128-row M tiles each, K padded to 256,
+// hi and lo: 512 KB) does not fit in shared memory.  It is laid out in global memory as 16
+// chunks of 32 KB, chunk q = (P*2 + mt)*4 + kc holding rows mt*128.. of parity P and K range
+// kc*64.., each piece canonical K-major with K = 64, and one thread streams the chunks through a
+// two-slot ring with cp.async.bulk (mbarrier transaction counts), one chunk ahead of the MMAs.
+// The B operand holds both parities for K = 256 (zero beyond h); the four accumulators
+// (parity x M tile, 32 columns each) take 128 tensor-memory columns.
+constexpr int kKP2 = 256;                 // padded K of the long kernel
+constexpr uint32_t kChunk2 = 32768u;      // bytes per streamed A chunk (2 pieces x 128 x 64 fp16)
+constexpr uint32_t kPiece2 = kChunk2 / 2; // one piece of a chunk
+
+struct Tc2Smem {
+  uint32_t ring, bop, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar, tmem, total;
+};
+
+__host__ __device__ inline Tc2Smem tc2_layout(int n) {
+  const int h = n / 2;
+  Tc2Smem L{};
+  uint32_t o = 0;
+  L.ring = o;
+  o += 2u * kChunk2;
+  L.bop = o;
+  o += 2u * 2u * kTN * kKP2 * 2u;  // [parity][piece][32][256] fp16
+  L.ytile = o;
+  o += 2u * h * kYS * 4u;
+  L.colscale = o;
+  o += kTN * 4u;
+  L.colinv1 = o;
+  o += kTN * 4u;
+  L.colinv2 = o;
+  o += kTN * 4u;
+  L.colmax = o;
+  o += kTN * 4u;
+  L.tmu = o;
+  o += kTN * 4u;
+  L.mbar = o;  // full[2], empty[2], done
+  o += 5 * 8;
+  L.tmem = o;
+  o += 8;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// Fold, scale and split for K = 256 (h <= 256 folded rows): thread (column c, group g) handles
+// the t-blocks g and g + 16 of 8 rows each.  Same arithmetic as build_b.
+template <class Src>
+__device__ __forceinline__ void build_b_long(unsigned char *smem, const Tc2Smem &L,
+                                             uint32_t colinv_off, int n, Src src, int tid) {
+  const int h = n >> 1, hb = h >> 3;
+  unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
+  float *colscale = reinterpret_cast<float *>(smem + L.colscale);
+  float *colinv = reinterpret_cast<float *>(smem + colinv_off);
+  const int c = tid & (kTN - 1), g = tid >> 5;
+  if (tid < kTN) colmax[tid] = 0u;
+  float u[2][8], d[2][8];
+  float mx = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = g + 16 * it;
+    if (tb < hb) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int t = tb * 8 + q;
+        const float a = src(t, c), b = src(n - 1 - t, c);
+        u[it][q] = a + b;
+        d[it][q] = a - b;
+        mx = fmaxf(mx, fmaxf(fabsf(u[it][q]), fabsf(d[it][q])));
+      }
+    }
+  }
+  __syncthreads();
+  atomicMax(&colmax[c], __float_as_uint(mx));
+  __syncthreads();
+  if (tid < kTN) {
+    const float m = __uint_as_float(colmax[tid]);
+    float s = 1.0f;
+    if (m > 0.f && isfinite(m)) {
+      int e;
+      frexpf(m, &e);
+      s = ldexpf(1.0f, 14 - e);
+    }
+    colscale[tid] = s;
+    colinv[tid] = 1.0f / (s * kSScale);
+  }
+  __syncthreads();
+  const float s = colscale[c];
+  unsigned char *bop = smem + L.bop;
+  const uint32_t piece = (uint32_t)kTN * kKP2 * 2u;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = g + 16 * it;
+    if (tb < hb) {
+      uint32_t uh[4], ul[4], dh[4], dl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split_h2(u[it][2 * q] * s, u[it][2 * q + 1] * s, uh[q], ul[q]);
+        split_h2(d[it][2 * q] * s, d[it][2 * q + 1] * s, dh[q], dl[q]);
+      }
+      const uint32_t off = canon_off(c, tb * 8, kKP2);
+      *reinterpret_cast<uint4 *>(bop + 0 * piece + off) = make_uint4(uh[0], uh[1], uh[2], uh[3]);
+      *reinterpret_cast<uint4 *>(bop + 1 * piece + off) = make_uint4(ul[0], ul[1], ul[2], ul[3]);
+      *reinterpret_cast<uint4 *>(bop + 2 * piece + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+      *reinterpret_cast<uint4 *>(bop + 3 * piece + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+    }
+  }
+}
+
+// Issued by one thread: one transform (16 streamed A chunks x 4 K steps x 3 products into the
+// four accumulators), then a commit to `done`.  The ring phases persist across calls.  Returns
+// false if a wait ran out (the caller records the timeout).
+__device__ __forceinline__ bool stream_mmas(unsigned char *smem, const Tc2Smem &L,
+                                            const unsigned char *A_g, uint32_t tmem,
+                                            uint32_t *fph, uint32_t *eph) {
+  const uint32_t full0 = smem_u32(smem + L.mbar), empty0 = full0 + 16, done = full0 + 32;
+  const uint32_t ring = smem_u32(smem + L.ring), bbase = smem_u32(smem + L.bop);
+  const uint32_t bpiece = (uint32_t)kTN * kKP2 * 2u;
+  auto fill = [&](int q, int slot) {
+    mbar_expect_tx(full0 + 8u * slot, kChunk2);
+    bulk_g2s(ring + (uint32_t)slot * kChunk2, A_g + (size_t)q * kChunk2, kChunk2,
+             full0 + 8u * slot);
+  };
+  bool ok = true;
+  int pending[2] = {0, 0};  // fills not yet waited for, per slot
+  fill(0, 0);
+  fill(1, 1);
+  pending[0] = pending[1] = 1;
+  for (int q = 0; q < 16; ++q) {
+    const int slot = q & 1;
+    if (!mbar_wait(full0 + 8u * slot, fph[slot])) {
+      ok = false;
+      break;
+    }
+    fph[slot] ^= 1u;
+    --pending[slot];
+    const int P = q >> 3, mt = (q >> 2) & 1, kc = q & 3;
+    const uint32_t d = tmem + (uint32_t)((P * 2 + mt) * kTN);
+    const uint32_t a_hi = ring + (uint32_t)slot * kChunk2, a_lo = a_hi + kPiece2;
+    const uint32_t b_hi = bbase + (2 * P) * bpiece, b_lo = b_hi + bpiece;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const uint32_t aoff = (uint32_t)ks * 256u, boff = (uint32_t)(kc * 4 + ks) * 256u;
+      mma_f16(d, make_desc(a_hi + aoff, 64), make_desc(b_hi + boff, kKP2),
+              (kc > 0 || ks > 0) ? 1u : 0u);
+      mma_f16(d, make_desc(a_hi + aoff, 64), make_desc(b_lo + boff, kKP2), 1u);
+      mma_f16(d, make_desc(a_lo + aoff, 64), make_desc(b_hi + boff, kKP2), 1u);
+    }
+    mma_commit(empty0 + 8u * slot);
+    // chunk q-1 (other slot) is read by MMAs issued before; once they are done, load chunk q+1
+    if (q >= 1 && q + 1 < 16) {
+      const int other = slot ^ 1;
+      if (!mbar_wait(empty0 + 8u * other, eph[other])) {
+        ok = false;
+        break;
+      }
+      eph[other] ^= 1u;
+      fill(q + 1, other);
+      ++pending[other];
+    }
+  }
+  if (ok) {
+    // the commits of the last two chunks (slots 0 and 1) complete one more phase of each empty
+    // barrier: consume them so that the phases stay in step for the next transform
+    for (int sl = 0; sl < 2 && ok; ++sl) {
+      if (!mbar_wait(empty0 + 8u * sl, eph[sl])) ok = false;
+      eph[sl] ^= 1u;
+    }
+  } else {
+    // after a timeout: wait (bounded) for copies still in flight before the block moves on
+    for (int sl = 0; sl < 2; ++sl)
+      if (pending[sl] > 0) mbar_wait(full0 + 8u * sl, fph[sl]);
+  }
+  mma_commit(done);
+  return ok;
+}
+
+__global__ void __launch_bounds__(kNT, 1)
+    k_time_tc_long(float *data, int n, long long m, int mx, Spec<float> sp,
+                   const unsigned char *A_g, State *S, int tmode, double *__restrict__ partials,
+                   int gk) {
+  __shared__ double red[32];
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = n >> 1;
+  const Tc2Smem L = tc2_layout(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+  const float *colinv1 = reinterpret_cast<const float *>(smem + L.colinv1);
+  const float *colinv2 = reinterpret_cast<const float *>(smem + L.colinv2);
+  float *ytile = reinterpret_cast<float *>(smem + L.ytile);
+  float *tmus = reinterpret_cast<float *>(smem + L.tmu);
+  const uint32_t full0 = smem_u32(smem + L.mbar), done = full0 + 32;
+  const long long ntiles = (m + kTN - 1) / kTN;
+  {  // B rows t >= h stay zero for the whole launch
+    uint4 *b = reinterpret_cast<uint4 *>(smem + L.bop);
+    const int cnt = (int)((2u * 2u * kTN * kKP2 * 2u) / 16u);
+    for (int i = tid; i < cnt; i += kNT) b[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t fph[2] = {0u, 0u}, eph[2] = {0u, 0u}, dph = 0u;  // phases (used by thread 0)
+  bool ok = true;
+  float esum = 0.f, ecomp = 0.f;
+  // accumulator view: TMEM lanes 32q.. (rows r = mt*128 + 32q + lane), parity P, columns 16ch..
+  const int qq = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
+  const int c0 = ch * 16;
+  const uint32_t lanes = (uint32_t)(qq * 32) << 16;
+  SymRow sr[2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r = mt * 128 + (qq << 5) + lane;
+    sr[mt] = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
+  }
+  auto ycell = [&](int t, int c) -> float { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
+  auto run_mmas = [&]() {
+    fence_async_smem();
+    __syncthreads();
+    fence_after();
+    bool w = true;
+    if (tid == 0) w = stream_mmas(smem, L, A_g, tmem, fph, eph);
+    const bool d = mbar_wait(done, dph);
+    dph ^= 1u;
+    ok = (__syncthreads_and((w && d) ? 1 : 0) != 0) && ok;
+    fence_after();
+  };
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long j0 = tile * kTN;
+    const int je = (int)min((long long)kTN, m - j0);
+    if (tid < kTN) {
+      float t = 0.f;
+      if (tid < je) {
+        const long long j = j0 + tid;
+        const long long jy = j / mx, jx = j - jy * mx;
+        t = sp.mux[jx] + sp.muy[jy];
+      }
+      tmus[tid] = t;
+    }
+    build_b_long(smem, L, L.colinv1, n,
+                 [&](int t, int c) -> float {
+                   return (c < je) ? data[(long long)t * m + j0 + c] : 0.f;
+                 },
+                 tid);
+    run_mmas();
+    // unscale, spectral scaling, energy; Y into the parity-split tile
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      float v[16];
+      tmem_ld16(tmem + lanes + (uint32_t)((P * 2 + mt) * kTN + c0), v);
+      const int r = mt * 128 + (qq << 5) + lane;
+      if (r < h) {
+        float *yrow = ytile + (P * h + r) * kYS;
+        float rs = 0.f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float y = v[c] * colinv1[c0 + c];
+          const float yi = y * inv_sym(sp, sr[mt], tmus[c0 + c]);
+          if (c0 + c < je) rs = fmaf(y, yi, rs);
+          yrow[c0 + c] = yi;
+        }
+        const float term = rs - ecomp;
+        const float t = esum + term;
+        ecomp = (t - esum) - term;
+        esum = t;
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    build_b_long(smem, L, L.colinv2, n, [&](int t, int c) -> float { return ycell(t, c); }, tid);
+    run_mmas();
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      float v[16];
+      tmem_ld16(tmem + lanes + (uint32_t)((P * 2 + mt) * kTN + c0), v);
+      const int r = mt * 128 + (qq << 5) + lane;
+      if (r < h) {
+        float *yrow = ytile + (P * h + r) * kYS;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv2[c0 + c];
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    for (int idx = tid; idx < n * kTN; idx += kNT) {
+      const int t = idx >> 5, c = idx & (kTN - 1);
+      if (c < je) data[(long long)t * m + j0 + c] = ycell(t, c);
+    }
+    __syncthreads();
+  }
+  if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+  }
+  if (tmode != TM_NONE) {
+    const double e = (double)esum - (double)ecomp;
+    double tot;
+    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                               &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT || tmode == TM_RESTART)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
+}
+
 }  // namespace
 
 // n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
@@ -680,6 +1017,64 @@ cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *so
   prof_begin(KC_DSTY, st);
   k_dst_tc_y<<<grid, kNT, smem_bytes, st>>>(data, g.my, g.mx, g.m, (long long)g.n,
                                             reinterpret_cast<const __half *>(sop), S, gk);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ long time axes: host side
+bool time_tc_long_supported(int n) {
+  return n > 256 && n <= 512 && (n % 32) == 0 && tc2_layout(n).total + 1024u <= 227u * 1024u;
+}
+
+size_t time_tc_long_bytes(int) { return (size_t)16 * kChunk2; }
+
+// Host: the 16 streamed chunks of 8 S_n (rows of parity P, M tile mt, K range kc*64..), hi and
+// lo pieces, each canonical K-major with K = 64.  Rows beyond h or with k > n, and columns
+// t >= h, are zero.
+void time_tc_long_build(int n, unsigned short *out) {
+  const int h = n / 2;
+  const double PI = 3.14159265358979323846;
+  const double sn = std::sqrt(2.0 / (n + 1));
+  const size_t halves = kChunk2 / 2, piece = kPiece2 / 2;
+  for (size_t i = 0; i < 16 * halves; ++i) out[i] = 0;
+  for (int P = 0; P < 2; ++P)
+    for (int mt = 0; mt < 2; ++mt)
+      for (int kc = 0; kc < 4; ++kc) {
+        unsigned short *chunk = out + (size_t)((P * 2 + mt) * 4 + kc) * halves;
+        for (int rr = 0; rr < kM; ++rr) {
+          const int r = mt * kM + rr;
+          const int k = (P == 0) ? 2 * r + 1 : 2 * r + 2;
+          if (r >= h || k > n) continue;
+          for (int kk = 0; kk < 64; ++kk) {
+            const int t = kc * 64 + kk;
+            if (t >= h) continue;
+            const double v = kSScale * sn * std::sin(PI * (double)k * (t + 1) / (n + 1));
+            const __half hi = __float2half_rn((float)v);
+            const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+            const uint32_t off = canon_off(rr, kk, 64) / 2;
+            __half_raw rh = hi, rl = lo;
+            chunk[off] = rh.x;
+            chunk[piece + off] = rl.x;
+          }
+        }
+      }
+}
+
+cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &sp,
+                                const unsigned short *A, State *S, int tmode, double *partials,
+                                int gk, cudaStream_t st) {
+  const uint32_t smem_bytes = tc2_layout(g.n).total;
+  cudaError_t e = cudaFuncSetAttribute(k_time_tc_long,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (g.m + kTN - 1) / kTN;
+  int grid = time_tc_grid();
+  if (ntiles < grid) grid = (int)ntiles;
+  prof_begin(KC_TIME, st);
+  k_time_tc_long<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
+                                                reinterpret_cast<const unsigned char *>(A), S,
+                                                tmode, partials, gk);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -31,7 +31,7 @@ def _rel2(a, b):
 
 # n supported by the tensor-core time path (multiples of 32 up to 256) and my + 1 in
 # {32, ..., 256} for the tensor-core y-DST; spatial sizes with ragged 32-column tiles
-# (m = 63, 15*31, 63*63, 127*127, 31*255); the last case keeps the FFMA time kernel (n = 40)
+# (m = 63, 15*31, 63*63, 127*127, 31*255); n = 40 keeps the FFMA time kernel
 @pytest.mark.parametrize("dim,mx,my,n,scheme,theta", [
     (1, 63, 1, 32, "theta", 1.0),
     (2, 15, 31, 64, "theta", 0.5),
@@ -39,6 +39,10 @@ def _rel2(a, b):
     (2, 127, 127, 256, "theta", 0.5),
     (2, 31, 31, 96, "theta", 0.3),
     (2, 31, 255, 40, "theta", 0.5),
+    # 256 < n <= 512: the kernel that streams S_n through shared memory (K padded to 256)
+    (2, 15, 15, 512, "theta", 0.5),
+    (1, 63, 1, 320, "theta", 1.0),
+    (2, 31, 15, 384, "bdf2", 1.0),
 ])
 def test_tc_time_dst_matches_oracle_and_ffma(pkg, dim, mx, my, n, scheme, theta):
     w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=True, seed=n + mx)
