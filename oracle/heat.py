@@ -26,6 +26,12 @@ Pins (tests/test_oracle_*.py) tie each function to something other than itself:
     main_P_normal); BDF2: rank(T[|g|^2] - P^2) = 2m (Sec. 4, Lemma rankC_P_gen).
   * apply_ptheta: equals the dense H (x) I + H_theta (x) tau K of eq.
     def:matrix_mod_P with matrix square roots from eigh (Sec. 3.1.4).
+  * apply_ptheta_cheb (2D varying a, Chebyshev inner map of step 2): the interval
+    [alpha_k, beta_k] holds the dense generalised spectrum of (A_k, B_k) and its ends are
+    the extreme eigenvalues of the comparison pencils a_min K0, a_max K0; the map of degree
+    d equals I - T_d-polynomial (numpy Chebyshev series) on that spectrum, symmetric
+    positive definite; degree 40 reproduces the sparse LU solve; a constant field is
+    exact at any degree; the whole P_theta^-1 stays within the Chebyshev bound of exact.
   * minres: the ideal preconditioner sqrt(T^T T) converges in at most two
     steps (Proposition absC); each iterate's preconditioned residual equals the
     brute-force least-squares minimum over the explicit Krylov basis; residual
@@ -64,6 +70,9 @@ class Problem:
     theta: float = 1.0
     a_nodal: Optional[np.ndarray] = None
     prec: str = "PH"  # "PH" (eq. def:matrix_P / def:matrix_P_gen) or "Ptheta" (eq. def:matrix_mod_P)
+    # P_theta with a 2D varying a: degree of the Chebyshev inner map of step 2 (Sec. 3.1.4);
+    # None solves every per-frequency system exactly (sparse LU)
+    inner_degree: Optional[int] = None
 
     @property
     def m(self) -> int:
@@ -86,8 +95,9 @@ class Problem:
         return 1.0 / (self.my + 1)
 
     @staticmethod
-    def from_workload(w, prec: str = "PH") -> "Problem":
-        return Problem(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec)
+    def from_workload(w, prec: str = "PH", inner_degree: Optional[int] = None) -> "Problem":
+        return Problem(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec,
+                       inner_degree)
 
 
 # --------------------------------------------------------------------------------------
@@ -389,6 +399,8 @@ def apply_ptheta(prob: Problem, v: np.ndarray, K: Optional[sp.csr_matrix] = None
     restored in the second term, as in the definition eq. def:matrix_mod_P)."""
     if K is None:
         K = stiffness(prob)
+    if prob.dim == 2 and prob.a_nodal is not None and prob.inner_degree is not None:
+        return apply_ptheta_cheb(prob, v, prob.inner_degree, K)
     lam_h, lam_ht = ptheta_time_eigs(prob.n, prob.theta)
     vt = time_dst(prob, v)
     zt = np.empty_like(vt)
@@ -396,6 +408,107 @@ def apply_ptheta(prob: Problem, v: np.ndarray, K: Optional[sp.csr_matrix] = None
     for k in range(prob.n):
         Ak = (lam_h[k] * I + lam_ht[k] * prob.tau * K).tocsc()
         zt[k] = spla.spsolve(Ak, vt[k])
+    return time_dst(prob, zt)
+
+
+# Step 2 of Sec. 3.1.4 leaves the solver of the shifted systems open (the paper names multigrid).
+# For a 2D varying a each system A_k = lam_H,k I + lam_Htheta,k tau K is approximated here by a
+# fixed number of Chebyshev steps preconditioned with B_k = lam_H,k I + lam_Htheta,k tau abar K0,
+# K0 the a = 1 stiffness matrix (diagonalised by the spatial DST) and abar the mean face value of
+# a.  A fixed polynomial in B_k^-1 A_k times B_k^-1 is a fixed symmetric linear map, positive
+# definite when the polynomial's error stays below one on the spectrum, so P_theta stays SPD and
+# MINRES applies unchanged.
+def constant_stiffness_eigs(prob: Problem) -> np.ndarray:
+    """Eigenvalues of K0 (a = 1) in S's order, x fastest: (2 - 2cos(i pi/(mx+1)))/hx^2 plus the
+    same term along y in 2D (the 3-point matrix tridiag(-1, 2, -1)/h^2 per axis)."""
+    ex = (2.0 - 2.0 * np.cos(np.arange(1, prob.mx + 1) * math.pi / (prob.mx + 1))) / prob.hx ** 2
+    if prob.dim == 1:
+        return ex
+    ey = (2.0 - 2.0 * np.cos(np.arange(1, prob.my + 1) * math.pi / (prob.my + 1))) / prob.hy ** 2
+    return (ey[:, None] + ex[None, :]).reshape(-1)
+
+
+def ptheta_cheb_bounds(prob: Problem):
+    """abar and, per time frequency k, the interval [alpha_k, beta_k] holding the eigenvalues of
+    B_k^-1 A_k.
+
+    K's quadratic form is the sum over cell faces of a_f (u_p - u_q)^2 / h_f^2 (u = 0 beyond the
+    boundary) and K0's the same with a_f = 1, so a_min K0 <= K <= a_max K0 with a_min, a_max over
+    the faces.  B_k commutes with K0, and the ratio (lam + c a mu)/(lam + c abar mu) is monotone in
+    mu and equals 1 at mu = 0, so with mu_max = the largest eigenvalue of K0 and c = lam_Htheta,k
+    tau the generalised eigenvalues of (A_k, B_k) lie in
+      [(lam + c a_min mu_max)/(lam + c abar mu_max), (lam + c a_max mu_max)/(lam + c abar mu_max)].
+    """
+    ax, ay = face_values(prob)
+    faces = np.concatenate([ax.reshape(-1), ay.reshape(-1)]) if ay is not None else ax.reshape(-1)
+    amin, amax, abar = float(faces.min()), float(faces.max()), float(faces.mean())
+    lam_h, lam_ht = ptheta_time_eigs(prob.n, prob.theta)
+    mu_max = float(constant_stiffness_eigs(prob).max())
+    c = lam_ht * prob.tau
+    den = lam_h + c * abar * mu_max
+    alpha = (lam_h + c * min(amin, abar) * mu_max) / den
+    beta = (lam_h + c * max(amax, abar) * mu_max) / den
+    return abar, alpha, beta
+
+
+def chebyshev_solve(apply_A: Callable, apply_Binv: Callable, b: np.ndarray, alpha: float,
+                    beta: float, degree: int) -> np.ndarray:
+    """x ~ A^-1 b by `degree` steps of the Chebyshev iteration for B^-1 A with spectrum in
+    [alpha, beta], from x = 0 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1, with
+    the preconditioner B).  The error is x - A^-1 b = -p(B^-1 A) A^-1 b with p the Chebyshev
+    polynomial of degree `degree` on [alpha, beta] scaled to p(0) = 1.  When alpha = beta up to
+    rounding (B = A) the first step is already exact and the later ones are skipped."""
+    centre, half = 0.5 * (beta + alpha), 0.5 * (beta - alpha)
+    x = np.zeros_like(b)
+    r = b.copy()
+    d = apply_Binv(r) / centre
+    if half <= 1e-14 * centre:
+        return d
+    sigma1 = centre / half
+    rho = 1.0 / sigma1
+    for j in range(degree):
+        x = x + d
+        if j == degree - 1:
+            break
+        r = r - apply_A(d)
+        rho_next = 1.0 / (2.0 * sigma1 - rho)
+        d = rho_next * rho * d + (2.0 * rho_next / half) * apply_Binv(r)
+        rho = rho_next
+    return x
+
+
+def ptheta_cheb_blocks(prob: Problem, k: int, K: Optional[sp.csr_matrix] = None):
+    """(A_k as a sparse matrix, the diagonal of B_k in the spatial DST basis) for frequency k."""
+    if K is None:
+        K = stiffness(prob)
+    abar, _, _ = ptheta_cheb_bounds(prob)
+    lam_h, lam_ht = ptheta_time_eigs(prob.n, prob.theta)
+    Ak = (lam_h[k] * sp.identity(prob.m, format="csr") + lam_ht[k] * prob.tau * K).tocsr()
+    bk = lam_h[k] + lam_ht[k] * prob.tau * abar * constant_stiffness_eigs(prob)
+    return Ak, bk
+
+
+def space_dst(prob: Problem, r: np.ndarray) -> np.ndarray:
+    """U_m r for one space vector (S_my (x) S_mx, x fastest)."""
+    R = dst(np.asarray(r, dtype=np.float64).reshape(prob.my, prob.mx), axis=1)
+    if prob.dim == 2:
+        R = dst(R, axis=0)
+    return R.reshape(-1)
+
+
+def apply_ptheta_cheb(prob: Problem, v: np.ndarray, degree: int,
+                      K: Optional[sp.csr_matrix] = None) -> np.ndarray:
+    """z = P_theta^-1 v (Sec. 3.1.4) with step 2 done by `degree` Chebyshev steps per frequency
+    (see ptheta_cheb_bounds / chebyshev_solve)."""
+    if K is None:
+        K = stiffness(prob)
+    _, alpha, beta = ptheta_cheb_bounds(prob)
+    vt = time_dst(prob, v)
+    zt = np.empty_like(vt)
+    for k in range(prob.n):
+        Ak, bk = ptheta_cheb_blocks(prob, k, K)
+        zt[k] = chebyshev_solve(lambda u: Ak @ u, lambda r: space_dst(prob, space_dst(prob, r) / bk),
+                                vt[k], alpha[k], beta[k], degree)
     return time_dst(prob, zt)
 
 

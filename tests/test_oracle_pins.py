@@ -250,6 +250,128 @@ def test_ptheta_matches_dense(varcoef):
     assert np.allclose(H.apply_ptheta(p, v).reshape(-1), ref, atol=1e-11)
 
 
+# ------------------------------------------------ P_theta, 2D varying a: Chebyshev inner map
+def _cheb_case(mx=7, my=5, n=4, theta=0.5, seed=21, const=None):
+    w = W.small_case(2, mx, my, n, scheme="theta", theta=theta, varcoef=True, seed=seed)
+    a = w.a_nodal if const is None else np.full_like(w.a_nodal, const)
+    return H.Problem(2, mx, my, n, w.T, "theta", theta, a, "Ptheta")
+
+
+def _dense_space_dst(p):
+    return np.kron(H.dst_matrix(p.my), H.dst_matrix(p.mx))
+
+
+def _cheb_map_dense(p, k, degree):
+    """The per-frequency inner map as a dense matrix, column by column."""
+    Ak, bk = H.ptheta_cheb_blocks(p, k)
+    _, al, be = H.ptheta_cheb_bounds(p)
+    cols = [H.chebyshev_solve(lambda u: Ak @ u, lambda r: H.space_dst(p, H.space_dst(p, r) / bk),
+                              e, al[k], be[k], degree) for e in np.eye(p.m)]
+    return np.array(cols).T, Ak.toarray(), bk
+
+
+def test_cheb_interval_holds_generalised_spectrum():
+    """a_min K0 <= K <= a_max K0 gives the interval of the pencil (A_k, B_k): every generalised
+    eigenvalue (dense, scipy.linalg.eigh) lies in [alpha_k, beta_k]."""
+    import scipy.linalg as sla
+    p = _cheb_case()
+    _, al, be = H.ptheta_cheb_bounds(p)
+    S = _dense_space_dst(p)
+    for k in range(p.n):
+        _, Ak, bk = _cheb_map_dense(p, k, 1)
+        lam = sla.eigh(Ak, S @ np.diag(bk) @ S, eigvals_only=True)
+        assert lam.min() >= al[k] * (1 - 1e-12) and lam.max() <= be[k] * (1 + 1e-12)
+        assert lam.max() / lam.min() > 1.2  # the field is not constant: a real interval
+
+
+def test_cheb_interval_is_attained_by_comparison_operators():
+    """B_k is lam_H,k I + lam_Htheta,k tau abar K0 with abar the mean face value and K0 the a = 1
+    stiffness matrix (built densely here by the oracle's own K with a = 1).  alpha_k and beta_k are
+    the extreme generalised eigenvalues of the comparison pencils (lam I + c a_min K0, B_k) and
+    (lam I + c a_max K0, B_k), c = lam_Htheta,k tau, which bound the pencil (A_k, B_k)."""
+    import scipy.linalg as sla
+    p = _cheb_case()
+    K0 = H.stiffness(H.Problem(2, p.mx, p.my, p.n, p.T, "theta", p.theta)).toarray()
+    ax, ay = H.face_values(p)
+    faces = np.concatenate([ax.reshape(-1), ay.reshape(-1)])
+    lam_h, lam_ht = H.ptheta_time_eigs(p.n, p.theta)
+    abar, al, be = H.ptheta_cheb_bounds(p)
+    assert abar == pytest.approx(faces.mean(), rel=1e-14)
+    S = _dense_space_dst(p)
+    I = np.eye(p.m)
+    for k in range(p.n):
+        c = lam_ht[k] * p.tau
+        _, _, bk = _cheb_map_dense(p, k, 1)
+        B = S @ np.diag(bk) @ S
+        assert np.allclose(B, lam_h[k] * I + c * faces.mean() * K0, rtol=0, atol=1e-10 * np.abs(B).max())
+        lo = sla.eigh(lam_h[k] * I + c * faces.min() * K0, B, eigvals_only=True).min()
+        hi = sla.eigh(lam_h[k] * I + c * faces.max() * K0, B, eigvals_only=True).max()
+        assert al[k] == pytest.approx(lo, rel=1e-12) and be[k] == pytest.approx(hi, rel=1e-12)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5])
+def test_cheb_map_is_the_chebyshev_polynomial(degree):
+    """The inner map M_k of degree d satisfies M_k A_k = I - p_d(B_k^-1 A_k), with p_d the
+    Chebyshev polynomial T_d of the first kind mapped from [alpha_k, beta_k] onto [-1, 1] and scaled
+    to p_d(0) = 1 (evaluated by numpy's Chebyshev series, independent of the recurrence).  M_k is
+    symmetric and positive definite."""
+    import numpy.polynomial.chebyshev as C
+    import scipy.linalg as sla
+    p = _cheb_case()
+    _, al, be = H.ptheta_cheb_bounds(p)
+    S = _dense_space_dst(p)
+    coef = [0.0] * degree + [1.0]
+    for k in (0, p.n - 1):
+        M, Ak, bk = _cheb_map_dense(p, k, degree)
+        assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+        assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+        lam = sla.eigh(Ak, S @ np.diag(bk) @ S, eigvals_only=True)
+        a, b = al[k], be[k]
+        pd = C.chebval((b + a - 2 * lam) / (b - a), coef) / C.chebval((b + a) / (b - a), coef)
+        got = np.sort(np.linalg.eigvals(M @ Ak).real)
+        assert np.allclose(got, np.sort(1.0 - pd), atol=1e-11)
+
+
+def test_cheb_high_degree_is_the_exact_solve():
+    """With degree 40 the Chebyshev error (about 0.25^40 here) is below rounding: P_theta^-1 v
+    equals the exact per-frequency sparse LU solve."""
+    p = _cheb_case(mx=15, my=7, n=5)
+    v = np.random.default_rng(4).standard_normal((p.n, p.m))
+    exact = H.apply_ptheta(p, v)
+    p.inner_degree = 40
+    assert np.linalg.norm(H.apply_ptheta(p, v) - exact) <= 1e-12 * np.linalg.norm(exact)
+
+
+def test_cheb_constant_field_is_exact_at_any_degree():
+    """A constant a makes B_k = A_k (abar = a): the first step is exact, and the map equals the
+    exact solve for every degree."""
+    p = _cheb_case(const=1.3)
+    v = np.random.default_rng(5).standard_normal((p.n, p.m))
+    exact = H.apply_ptheta(p, v)
+    for d in (1, 3):
+        p.inner_degree = d
+        assert np.linalg.norm(H.apply_ptheta(p, v) - exact) <= 1e-12 * np.linalg.norm(exact)
+        p.inner_degree = None
+
+
+def test_cheb_ptheta_spd_and_close_to_exact():
+    """The whole P_theta^-1 with the inner map (degree 3) is symmetric positive definite, and its
+    product with the exact P_theta has eigenvalues within the Chebyshev bound 1/T_3((b+a)/(b-a))
+    of one, with the widest interval over the frequencies."""
+    p = _cheb_case(mx=3, my=3, n=4)
+    _, al, be = H.ptheta_cheb_bounds(p)
+    p.inner_degree = 3
+    E = np.eye(p.N)
+    Mc = np.array([H.apply_ptheta(p, e.reshape(p.n, p.m)).reshape(-1) for e in E]).T
+    assert np.abs(Mc - Mc.T).max() <= 1e-12 * np.abs(Mc).max()
+    assert np.linalg.eigvalsh(0.5 * (Mc + Mc.T)).min() > 0
+    ev = np.linalg.eigvals(Mc @ H.dense_Ptheta(p)).real
+    t = ((be + al) / (be - al)).min()
+    eps = 1.0 / math.cosh(3 * math.acosh(t))
+    assert np.abs(ev - 1).max() <= eps * (1 + 1e-9)
+    assert np.abs(ev - 1).max() > 1e-3 * eps  # the map is not exact
+
+
 def test_preconditioned_spectrum_clusters():
     """Eigenvalues of P^{-1} Y T cluster at +-1 with a number of outliers that does not depend on n
     (Theorem absP_main). The blocks A0, A1 are held fixed (fixed tau) while n grows."""
