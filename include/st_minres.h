@@ -51,7 +51,15 @@ extern "C" {
                          /* 3.1.1, after eq. matrix_Km_va)                                    */
 #define ST_PREC_PTHETA 1 /* P_theta = H (x) M + H_theta (x) tau K (eq. def:matrix_mod_P).     */
                          /* Constant a: spatial DST; 1D varying a: per-frequency tridiagonal  */
-                         /* solves by parallel cyclic reduction.  2D varying a: ST_ERR_ARG.    */
+                         /* solves by parallel cyclic reduction; 2D varying a: per-frequency  */
+                         /* fixed-degree Chebyshev iteration (st_problem.inner_degree steps)  */
+                         /* preconditioned by the sine solve with a = mean face value.  The   */
+                         /* paper leaves this solver open (Sec. 3.1.4, step 2).  The result   */
+                         /* is a fixed SPD map.  theta-method only.                           */
+
+/* default number of Chebyshev steps of the 2D varying-a P_theta (st_problem.inner_degree = 0) */
+#define ST_PTHETA_DEFAULT_DEGREE 2
+#define ST_PTHETA_MAX_DEGREE 16
 
 /* arithmetic */
 #define ST_FP64 0  /* every step in float64                                                   */
@@ -71,6 +79,10 @@ typedef struct st_problem {
   int prec;               /* ST_PREC_PH or ST_PREC_PTHETA                                    */
   int precision;          /* ST_FP64 or ST_MIXED                                             */
   void *stream;           /* cudaStream_t; NULL = the legacy default stream                  */
+  int inner_degree;       /* ST_PREC_PTHETA with 2D a_nodal: Chebyshev steps per apply in     */
+                          /* [1, ST_PTHETA_MAX_DEGREE]; 0 = ST_PTHETA_DEFAULT_DEGREE; must be  */
+                          /* 0 otherwise.  The map is symmetric positive definite at any     */
+                          /* degree (its error polynomial stays below one on the spectrum).    */
 } st_problem;
 
 typedef struct st_stats {

@@ -420,11 +420,12 @@ def apply_ptheta(prob: Problem, v: np.ndarray, K: Optional[sp.csr_matrix] = None
 # MINRES applies unchanged.
 def constant_stiffness_eigs(prob: Problem) -> np.ndarray:
     """Eigenvalues of K0 (a = 1) in S's order, x fastest: (2 - 2cos(i pi/(mx+1)))/hx^2 plus the
-    same term along y in 2D (the 3-point matrix tridiag(-1, 2, -1)/h^2 per axis)."""
-    ex = (2.0 - 2.0 * np.cos(np.arange(1, prob.mx + 1) * math.pi / (prob.mx + 1))) / prob.hx ** 2
+    same term along y in 2D (the 3-point matrix tridiag(-1, 2, -1)/h^2 per axis), evaluated as
+    4 sin^2(i pi/(2(mx+1))), which is the same number without the cancellation at small i."""
+    ex = 4.0 * np.sin(np.arange(1, prob.mx + 1) * math.pi / (2 * (prob.mx + 1))) ** 2 / prob.hx ** 2
     if prob.dim == 1:
         return ex
-    ey = (2.0 - 2.0 * np.cos(np.arange(1, prob.my + 1) * math.pi / (prob.my + 1))) / prob.hy ** 2
+    ey = 4.0 * np.sin(np.arange(1, prob.my + 1) * math.pi / (2 * (prob.my + 1))) ** 2 / prob.hy ** 2
     return (ey[:, None] + ex[None, :]).reshape(-1)
 
 

@@ -21,6 +21,7 @@ ST_OK, ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_NOT_CONVERGED, ST_ERR_BREAKDOWN, ST_ERR_T
 ST_THETA, ST_BDF2 = 0, 1
 ST_PREC_PH, ST_PREC_PTHETA = 0, 1
 ST_FP64, ST_MIXED = 0, 1
+ST_PTHETA_DEFAULT_DEGREE, ST_PTHETA_MAX_DEGREE = 2, 16
 
 # Every symbol declared in include/st_minres.h.
 EXPORTS = (
@@ -39,7 +40,7 @@ class StProblem(ctypes.Structure):
         ("dim", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("n", ctypes.c_int),
         ("T", ctypes.c_double), ("scheme", ctypes.c_int), ("theta", ctypes.c_double),
         ("a_nodal", ctypes.POINTER(ctypes.c_double)), ("prec", ctypes.c_int),
-        ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("inner_degree", ctypes.c_int),
     ]
 
 
@@ -157,6 +158,7 @@ class ProblemSpec:
     a_nodal: Optional[np.ndarray] = None
     prec: str = "PH"  # "PH" | "Ptheta"
     precision: str = "fp64"  # "fp64" | "mixed"
+    inner_degree: int = 0  # Ptheta with a 2D a_nodal: Chebyshev steps (0 = library default)
 
     @property
     def m(self):
@@ -177,7 +179,7 @@ class ProblemSpec:
             ST_THETA if self.scheme == "theta" else ST_BDF2, float(self.theta),
             a, ST_PREC_PH if self.prec == "PH" else ST_PREC_PTHETA,
             ST_FP64 if self.precision == "fp64" else ST_MIXED,
-            ctypes.c_void_p(stream_ptr) if stream_ptr else None,
+            ctypes.c_void_p(stream_ptr) if stream_ptr else None, int(self.inner_degree),
         )
         return p, keep
 

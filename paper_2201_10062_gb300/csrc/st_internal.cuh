@@ -266,6 +266,16 @@ struct PrecPlan {
   const unsigned short *sop_long;  // streamed S_n chunks for the tensor-core time kernel when
                                    // 256 < n <= 512 (mixed), or null
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
+  const unsigned short *sop_t1;  // fp16 S_n image for unscaled single time transforms on the
+                                 // tensor cores (mixed P_theta with varying a), or null
+  // P_theta with varying a in 2D: Chebyshev steps per apply (0: not this path), the per-step,
+  // per-frequency scalars [cheb][n] (a: carry-over of the previous direction, s: factor of
+  // B_k^-1 r), and five N-vectors of float64 scratch (used as the transform type: residual,
+  // transformed residual, iterate, two directions)
+  int cheb;
+  const double *cheb_a_d, *cheb_s_d;
+  const float *cheb_a_f, *cheb_s_f;
+  void *cheb_work;
 };
 
 // Lowest relative target of an inner (float32-preconditioned) MINRES run of the mixed solve:
@@ -288,6 +298,9 @@ cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &s
                                 int gk, cudaStream_t st);
 cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st);
+bool dst_tc_len_supported(int len);
+cudaError_t launch_time_tc_single(const float *in, float *out, const Geom &g,
+                                  const unsigned short *sop, State *S, int gk, cudaStream_t st);
 
 // energy mode of the time kernel's last block
 enum { TM_NONE = 0, TM_INIT = 1, TM_ITER = 2, TM_RESTART = 3 };
@@ -428,6 +441,7 @@ struct st_handle {
   st::State *S;          // device scalars
   double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
   double *gfx, *gfy;     // face-gradient scratch for st_grad_a
+  void *cheb;            // P_theta, 2D varying a: Chebyshev scalars and scratch vectors
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)

@@ -261,7 +261,11 @@ int check_problem(const st_problem *p) {
   if (p->prec != ST_PREC_PH && p->prec != ST_PREC_PTHETA) return ST_ERR_ARG;
   if (p->precision != ST_FP64 && p->precision != ST_MIXED) return ST_ERR_ARG;
   if (p->prec == ST_PREC_PTHETA && p->scheme != ST_THETA) return ST_ERR_ARG;
-  if (p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr && p->dim != 1) return ST_ERR_ARG;
+  {
+    const bool cheb = p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr && p->dim == 2;
+    if (p->inner_degree < 0 || p->inner_degree > ST_PTHETA_MAX_DEGREE) return ST_ERR_ARG;
+    if (!cheb && p->inner_degree != 0) return ST_ERR_ARG;
+  }
   if (p->a_nodal) {
     const long long cnt = (p->dim == 1) ? (p->mx + 2) : (long long)(p->mx + 2) * (p->my + 2);
     for (long long i = 0; i < cnt; ++i)
@@ -326,9 +330,20 @@ size_t table_floats(const Geom &g) {
   return spec + tw;
 }
 
-size_t workspace_bytes(const Geom &g, bool mixed) {
+// Chebyshev steps of the 2D varying-a P_theta, 0 for every other preconditioner
+int cheb_degree(const st_problem *p) {
+  if (p->prec != ST_PREC_PTHETA || p->a_nodal == nullptr || p->dim != 2) return 0;
+  return p->inner_degree > 0 ? p->inner_degree : ST_PTHETA_DEFAULT_DEGREE;
+}
+
+size_t cheb_coef_bytes(const Geom &g, int deg) {
+  return ((size_t)deg * g.n * 2 * (sizeof(double) + sizeof(float)) + 255) / 256 * 256;
+}
+
+size_t workspace_bytes(const Geom &g, bool mixed, int cheb) {
   const size_t N = (size_t)g.N;
   size_t b = 0;
+  if (cheb) b += cheb_coef_bytes(g, cheb) + 5 * N * sizeof(double);
   b += 2 * N * sizeof(double);                             // V
   b += 2 * N * (mixed ? sizeof(float) : sizeof(double));   // Z
   b += 2 * N * sizeof(double);                             // D
@@ -408,6 +423,33 @@ int build_tables(st_handle *h) {
   for (int i = 0; i < mx; ++i) mux[i] = dbar - 2.0 * ex * std::cos((i + 1) * PI / (mx + 1));
   for (int j = 0; j < my; ++j)
     muy[j] = (g.dim == 2) ? -2.0 * ey * std::cos((j + 1) * PI / (my + 1)) : 0.0;
+  // P_theta with a varying 2D coefficient: the Chebyshev inner map is preconditioned by the
+  // a = abar operator, so the spatial tables hold tau abar times the eigenvalues of K0 (a = 1),
+  // 4 sin^2(i pi / (2(mx+1))) / hx^2 per axis, instead of the averaged K
+  const int cheb = cheb_degree(&p);
+  double f_min = 0.0, f_max = 0.0, f_bar = 0.0, mu0_max = 0.0;
+  if (cheb) {
+    CSum fs;
+    f_min = INFINITY;
+    f_max = 0.0;
+    auto face = [&](double a) {
+      fs.add(a);
+      f_min = std::min(f_min, a);
+      f_max = std::max(f_max, a);
+    };
+    for (int j = 0; j < my; ++j)
+      for (int i = 0; i <= mx; ++i) face(0.5 * (anode(j + 1, i) + anode(j + 1, i + 1)));
+    for (int j = 0; j <= my; ++j)
+      for (int i = 0; i < mx; ++i) face(0.5 * (anode(j, i + 1) + anode(j + 1, i + 1)));
+    f_bar = fs.get() / (double)(nfx + nfy);
+    auto mu0 = [&](int i, int len, double h2) {
+      const double sv = std::sin((i + 1) * PI / (2.0 * (len + 1)));
+      return 4.0 * sv * sv / h2;
+    };
+    for (int i = 0; i < mx; ++i) mux[i] = tau * f_bar * mu0(i, mx, hx * hx);
+    for (int j = 0; j < my; ++j) muy[j] = tau * f_bar * mu0(j, my, hy * hy);
+    mu0_max = mu0(mx - 1, mx, hx * hx) + mu0(my - 1, my, hy * hy);
+  }
   const double th = g.theta;
   for (int k = 1; k <= n; ++k) {
     const double x = k * PI / (n + 1);
@@ -420,6 +462,37 @@ int build_tables(st_handle *h) {
   }
   const double sn = std::sqrt(2.0 / (n + 1));
   for (int r = 0; r < 2 * (n + 1); ++r) sintab[r] = sn * std::sin(r * PI / (n + 1));
+  // Chebyshev scalars per step j and frequency k.  a_min K0 <= K <= a_max K0 over the faces, and
+  // (lam + c a mu)/(lam + c abar mu) is monotone in mu and 1 at mu = 0, so the spectrum of
+  // B_k^-1 A_k lies in [alpha, beta] = (lam + c {a_min, a_max} mu0_max)/(lam + c abar mu0_max),
+  // c = lam_Htheta,k tau.  With centre and half-width of that interval (Saad, Alg. 12.1):
+  // s_0 = 1/centre, rho_0 = half/centre; rho_j = 1/(2 centre/half - rho_{j-1}),
+  // a_j = rho_j rho_{j-1}, s_j = 2 rho_j/half.  A zero-width interval (B_k = A_k) is solved by the
+  // first step: the later scalars are zero.
+  std::vector<double> cheb_a((size_t)cheb * n), cheb_s((size_t)cheb * n);
+  for (int k = 0; k < n && cheb; ++k) {
+    const double c = lht[k] * tau;
+    const double den = lh[k] + c * f_bar * mu0_max;
+    const double alpha = (lh[k] + c * std::min(f_min, f_bar) * mu0_max) / den;
+    const double beta = (lh[k] + c * std::max(f_max, f_bar) * mu0_max) / den;
+    const double centre = 0.5 * (beta + alpha), half = 0.5 * (beta - alpha);
+    cheb_a[k] = 0.0;
+    cheb_s[k] = 1.0 / centre;
+    const bool exact = !(half > 1e-14 * centre);
+    const double sigma1 = exact ? 0.0 : centre / half;
+    double rho = exact ? 0.0 : 1.0 / sigma1;
+    for (int j = 1; j < cheb; ++j) {
+      double aj = 0.0, sj = 0.0;
+      if (!exact) {
+        const double rn = 1.0 / (2.0 * sigma1 - rho);
+        aj = rn * rho;
+        sj = 2.0 * rn / half;
+        rho = rn;
+      }
+      cheb_a[(size_t)j * n + k] = aj;
+      cheb_s[(size_t)j * n + k] = sj;
+    }
+  }
   const int Lx = 2 * (mx + 1), Ly = 2 * (my + 1);
   std::vector<double> twx(Lx), twy(Ly);
   for (int j = 0; j < Lx / 2; ++j) {
@@ -498,10 +571,38 @@ int build_tables(st_handle *h) {
   h->g.omth_d = df_of_double(1.0 - h->g.theta);
   h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
   PrecPlan &pp = h->pp;
-  pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr) ? 1 : 0;
+  pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr && g.dim == 1) ? 1 : 0;
+  pp.cheb = cheb;
+  if (cheb) {
+    const size_t cb = cheb_coef_bytes(g, cheb);
+    ST_TRY(cudaMalloc(&h->cheb, cb + 5 * (size_t)g.N * sizeof(double)));
+    const size_t cnt = (size_t)cheb * n;
+    std::vector<float> af(cnt), sf(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+      af[i] = (float)cheb_a[i];
+      sf[i] = (float)cheb_s[i];
+    }
+    char *cbase = (char *)h->cheb;
+    ST_TRY(cudaMemcpy(cbase, cheb_a.data(), cnt * sizeof(double), cudaMemcpyHostToDevice));
+    ST_TRY(cudaMemcpy(cbase + cnt * sizeof(double), cheb_s.data(), cnt * sizeof(double),
+                      cudaMemcpyHostToDevice));
+    ST_TRY(cudaMemcpy(cbase + 2 * cnt * sizeof(double), af.data(), cnt * sizeof(float),
+                      cudaMemcpyHostToDevice));
+    ST_TRY(cudaMemcpy(cbase + 2 * cnt * sizeof(double) + cnt * sizeof(float), sf.data(),
+                      cnt * sizeof(float), cudaMemcpyHostToDevice));
+    pp.cheb_a_d = (const double *)cbase;
+    pp.cheb_s_d = pp.cheb_a_d + cnt;
+    pp.cheb_a_f = (const float *)(cbase + 2 * cnt * sizeof(double));
+    pp.cheb_s_f = pp.cheb_a_f + cnt;
+    pp.cheb_work = cbase + cb;
+  }
   const unsigned short *sop_img =
-      (sop.empty() || pp.pcr) ? nullptr
+      (sop.empty() || pp.pcr || pp.cheb) ? nullptr
                               : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop);
+  // the P_theta paths with varying a transform time alone (no scaling) on the tensor cores
+  pp.sop_t1 = (!sop.empty() && !long_tc && (pp.pcr || pp.cheb) && dst_tc_len_supported(n))
+                  ? reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sop)
+                  : nullptr;
   pp.sop = long_tc ? nullptr : sop_img;
   pp.sop_long = long_tc ? sop_img : nullptr;
   pp.sop_y = sopy.empty() ? nullptr
@@ -535,6 +636,7 @@ void free_handle(st_handle *h) {
   cudaFree(h->hbuf_out);
   cudaFree(h->gfx);
   cudaFree(h->gfy);
+  cudaFree(h->cheb);
   if (h->hS) cudaFreeHost(h->hS);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_givens[i]) cudaEventDestroy(h->ev_givens[i]);
@@ -908,7 +1010,8 @@ int st_autotune(st_handle *h, int reps) {
   ST_TRY(cudaSetDevice(h->device));
   const bool fp32 = h->mixed;
   const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.n, (int)fp32,
-                                   (h->pp.sop ? 1 : 0) + (h->pp.pcr ? 2 : 0));
+                                   (h->pp.sop ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
+                                       (h->pp.cheb ? 4 : 0));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1036,7 +1139,7 @@ int st_workspace_bytes(const st_problem *prob, size_t *bytes) {
   int r = check_problem(prob);
   if (r) return r;
   Geom g = geom_of(prob);
-  *bytes = workspace_bytes(g, prob->precision == ST_MIXED);
+  *bytes = workspace_bytes(g, prob->precision == ST_MIXED, cheb_degree(prob));
   return ST_OK;
 }
 

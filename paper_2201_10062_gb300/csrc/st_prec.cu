@@ -262,7 +262,7 @@ __device__ __forceinline__ T inv_symbol(const Spec<T> &sp, int k, T tmu) {
 
 template <class Tc, int KT, int JT>
 __global__ void __launch_bounds__(kNT)
-    k_time(Tc *data, int n, long long m, int mx, int J, Spec<Tc> sp, State *S,
+    k_time(const Tc *data, Tc *out, int n, long long m, int mx, int J, Spec<Tc> sp, State *S,
            int tmode, int tkind, double *__restrict__ partials, int gk) {
   __shared__ double red[32];
   if (gate_closed(S, gk)) return;
@@ -310,12 +310,12 @@ __global__ void __launch_bounds__(kNT)
     time_dst_tile<Tc, KT, JT>(Y, X, sintab, n, J);
     for (int idx = tid; idx < n * J; idx += kNT) {
       const int t = idx / J, c = idx - t * J;
-      if (c < Je) data[(long long)t * m + j0 + c] = X[idx];
+      if (c < Je) out[(long long)t * m + j0 + c] = X[idx];
     }
   } else {
     for (int idx = tid; idx < n * J; idx += kNT) {
       const int t = idx / J, c = idx - t * J;
-      if (c < Je) data[(long long)t * m + j0 + c] = Y[idx];
+      if (c < Je) out[(long long)t * m + j0 + c] = Y[idx];
     }
   }
   if (tmode != TM_NONE) {
@@ -399,6 +399,122 @@ __global__ void __launch_bounds__(kNT)
     if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
                                &tot) &&
         tid == 0) {
+      if (tmode == TM_INIT || tmode == TM_RESTART)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- P_theta, 2D a(x, y)
+// Step 2 of the P_theta apply (Sec. 3.1.4) when K is not sine-diagonalisable in 2D.  The paper
+// leaves the solver of the shifted systems A_k = lam_H,k I + lam_Htheta,k tau K open; here each
+// one gets a fixed number of preconditioned Chebyshev steps (Saad, Iterative Methods for Sparse
+// Linear Systems, Alg. 12.1) with B_k = lam_H,k I + lam_Htheta,k tau abar K0 (K0 the a = 1
+// stiffness matrix, abar the mean face value), which the spatial DST diagonalises.  All n
+// frequencies advance together.  Step j:
+//   w = s_j,k B_k^-1 r_j           four spatial DST passes, the diagonal fused into the third
+//   d_j = a_j,k d_{j-1} + w        (d_{-1} = 0)
+//   x_{j+1} = x_j + d_j,  r_{j+1} = r_j - A_k d_j    (k_cheb_resid; the last step: k_cheb_final)
+// The scalars come from the Chebyshev interval of B_k^-1 A_k, set up on the host.
+
+// The B_k^-1 diagonal times the step scalar, applied as the third transform loads its input.
+template <class Tc>
+struct SrcChebScale {
+  const Tc *w;
+  const Tc *s;  // [n] step scalar per frequency
+  const Tc *lh, *lht, *mux, *muy;
+  unsigned m, mx;
+  __device__ __forceinline__ void prepare(const State *) {}
+  __device__ __forceinline__ Tc operator()(long long i) const {
+    const unsigned e = (unsigned)i;  // N < 2^31 for every accepted size
+    const unsigned k = e / m, r = e - k * m;
+    const unsigned jy = r / mx, ix = r - jy * mx;
+    return w[i] * s[k] / (lh[k] + lht[k] * (mux[ix] + muy[jy]));
+  }
+};
+
+// Face coefficient tau a / h^2 in the transform type: float64 tables for float64, the leading
+// float of the double-float copy for float32 (no float64 conversion per element).
+template <class Tc>
+__device__ __forceinline__ Tc face_c(const double *c, const df *cd, long long i);
+template <>
+__device__ __forceinline__ double face_c<double>(const double *c, const df *, long long i) {
+  return c[i];
+}
+template <>
+__device__ __forceinline__ float face_c<float>(const double *, const df *cd, long long i) {
+  return cd[i].hi;
+}
+
+// d_j = a_k d_{j-1} + w into dnext (its own buffer: the stencil reads neighbours of d_{j-1}),
+// x = x + d_j (x = d_j when first), r = rsrc - A_k d_j with tau K the 5-point stencil of the face
+// coefficients cx, cy (tau a / h^2).  r may alias rsrc.
+template <class Tc>
+__global__ void __launch_bounds__(kNT)
+    k_cheb_resid(Geom g, const Tc *__restrict__ dprev, const Tc *__restrict__ w,
+                 Tc *__restrict__ dnext, const Tc *rsrc, Tc *r, Tc *__restrict__ x,
+                 const Tc *__restrict__ acoef, const Tc *__restrict__ lh,
+                 const Tc *__restrict__ lht, int first, const State *S, int gk) {
+  if (gate_closed(S, gk)) return;
+  const int mx = g.mx, my = g.my;
+  const long long m = g.m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned ue = (unsigned)e;
+    const unsigned k = ue / (unsigned)m, rr = ue - k * (unsigned)m;
+    const int jy = (int)(rr / (unsigned)mx), ix = (int)(rr - (unsigned)jy * mx);
+    const Tc ak = first ? Tc(0) : acoef[k];
+    auto dv = [&](long long q) -> Tc { return first ? w[q] : ak * dprev[q] + w[q]; };
+    const Tc dc = dv(e);
+    const long long fx = (long long)jy * (mx + 1) + ix, fy = (long long)jy * mx + ix;
+    const Tc cw = face_c<Tc>(g.cx, g.cxd, fx), ce = face_c<Tc>(g.cx, g.cxd, fx + 1);
+    const Tc cs = face_c<Tc>(g.cy, g.cyd, fy), cn = face_c<Tc>(g.cy, g.cyd, fy + mx);
+    Tc kd = (cw + ce + cs + cn) * dc;
+    if (ix > 0) kd -= cw * dv(e - 1);
+    if (ix < mx - 1) kd -= ce * dv(e + 1);
+    if (jy > 0) kd -= cs * dv(e - mx);
+    if (jy < my - 1) kd -= cn * dv(e + mx);
+    r[e] = rsrc[e] - (lh[k] * dc + lht[k] * kd);
+    x[e] = first ? dc : x[e] + dc;
+    dnext[e] = dc;
+  }
+}
+
+// Last step: d = a_k d_{j-1} + w (w alone when first), o = x + d (d alone when first); z holds
+// the time-transformed v, and <v, P^-1 v> = sum z * o (the time DST is orthogonal) completes in
+// the last block, which also runs the MINRES scalar step.  The per-thread sum is compensated in
+// the transform type (float64 arithmetic per element would bind a float32 pass to the slow
+// float64 pipe) and combined across threads in float64.  o is a separate array: rewriting z in
+// place inside this accumulating loop measured five times slower (213 against 43 us per
+// 255^2 x 128 float pass).
+template <class Tc>
+__global__ void __launch_bounds__(kNT)
+    k_cheb_final(long long N, long long m, const Tc *__restrict__ dprev,
+                 const Tc *__restrict__ w, const Tc *__restrict__ x, const Tc *__restrict__ z,
+                 Tc *__restrict__ o, const Tc *__restrict__ acoef, int first, State *S, int tmode,
+                 double *__restrict__ partials, int gk) {
+  __shared__ double red[32];
+  if (gate_closed(S, gk)) return;
+  Tc esum = Tc(0), ecomp = Tc(0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned k = (unsigned)e / (unsigned)m;
+    const Tc d = first ? w[e] : acoef[k] * dprev[e] + w[e];
+    const Tc xv = first ? d : x[e] + d;
+    const Tc term = z[e] * xv - ecomp;
+    const Tc t = esum + term;
+    ecomp = (t - esum) - term;
+    esum = t;
+    o[e] = xv;
+  }
+  if (tmode != TM_NONE) {
+    const double en = (double)esum - (double)ecomp;
+    double tot;
+    if (last_block_reduce<kNT>(en, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                               &tot) &&
+        threadIdx.x == 0) {
       if (tmode == TM_INIT || tmode == TM_RESTART)
         minres_init_scalars_dev(S, tot);
       else
@@ -501,9 +617,11 @@ int time_J(int n) {
   return J;
 }
 
+// out: null for in place, else an array that does not overlap data
 template <class Tc>
 cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, int tmode,
-                        int tkind, double *partials, int gk, int Jover, cudaStream_t st) {
+                        int tkind, double *partials, int gk, int Jover, cudaStream_t st,
+                        Tc *out = nullptr) {
   const int J = Jover > 0 ? Jover : time_J<Tc>(g.n);
   const size_t sm = time_smem<Tc>(g.n, J);
   const long long blocks = (g.m + J - 1) / J;
@@ -512,8 +630,8 @@ cudaError_t launch_time(Tc *data, const Geom &g, const Spec<Tc> &sp, State *S, i
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   prof_begin(KC_TIME, st);
-  kern<<<(unsigned)blocks, kNT, sm, st>>>(data, g.n, g.m, g.mx, J, sp, S, tmode, tkind, partials,
-                                          gk);
+  kern<<<(unsigned)blocks, kNT, sm, st>>>(data, out ? out : data, g.n, g.m, g.mx, J, sp, S, tmode,
+                                          tkind, partials, gk);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -556,6 +674,104 @@ const Spec<float> &spec_of<float>(const PrecPlan &pp) {
   return pp.spec_f;
 }
 
+template <class Tc>
+static const Tc *cheb_a_of(const PrecPlan &pp);
+template <>
+const double *cheb_a_of<double>(const PrecPlan &pp) {
+  return pp.cheb_a_d;
+}
+template <>
+const float *cheb_a_of<float>(const PrecPlan &pp) {
+  return pp.cheb_a_f;
+}
+template <class Tc>
+static const Tc *cheb_s_of(const PrecPlan &pp);
+template <>
+const double *cheb_s_of<double>(const PrecPlan &pp) {
+  return pp.cheb_s_d;
+}
+template <>
+const float *cheb_s_of<float>(const PrecPlan &pp) {
+  return pp.cheb_s_f;
+}
+
+constexpr int kChebBlocks = 152 * 8;
+
+// The time DST alone (the P_theta paths with varying a): tensor cores in float32 when the plan has
+// the S_n image, else the FFMA/DFMA kernel.
+// in -> out (the same array, or one that does not overlap).
+template <class Tc>
+cudaError_t time_single(Tc *in, Tc *out, const Geom &g, const PrecPlan &pp, State *S,
+                        double *partials, int gk, int Jo, cudaStream_t st) {
+  if (sizeof(Tc) == sizeof(float) && pp.sop_t1 != nullptr)
+    return launch_time_tc_single(reinterpret_cast<const float *>(in),
+                                 reinterpret_cast<float *>(out), g, pp.sop_t1, S, gk, st);
+  return launch_time<Tc>(in, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st, out);
+}
+
+// P_theta with a varying 2D coefficient: time DST, pp.cheb Chebyshev steps per frequency, time
+// DST (see k_cheb_resid).  zc receives the source, then the transformed v, then the result (the
+// last step leaves its iterate in R, from which the inverse time DST writes zc).
+template <class Tc, class Src>
+cudaError_t cheb_stages(const Geom &g, const PrecPlan &pp, Src src, Tc *zc, State *S, int tmode,
+                        double *partials, cudaStream_t st, cudaEvent_t after_time) {
+  using Arr = SrcArray<Tc, Tc>;
+  const int gk = gate_kind_of(tmode);
+  const Spec<Tc> &sp = spec_of<Tc>(pp);
+  const long long N = g.N;
+  Tc *R = reinterpret_cast<Tc *>(pp.cheb_work);
+  Tc *W = R + N, *X = R + 2 * N;
+  Tc *Dd[2] = {R + 3 * N, R + 4 * N};
+  const Tc *acoef = cheb_a_of<Tc>(pp), *scoef = cheb_s_of<Tc>(pp);
+  const int Jo = sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d;
+  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
+  const Tc *twx = tw_of<Tc>(pp, true), *twy = tw_of<Tc>(pp, false);
+  cudaError_t e;
+  auto y_pass = [&](Tc *a) -> cudaError_t {
+    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
+      return launch_dst_tc_y(reinterpret_cast<float *>(a), g, pp.sop_y, S, gk, st);
+    return launch_dst<Tc, Arr, Tc, false>(Arr{a}, a, g.my, pp.Ly, ny, g.mx, g.m, twy, S, gk,
+                                          pp.dst_shift, st);
+  };
+  prof_begin(KC_AUX, st);
+  k_copy_to<Tc, Src><<<kChebBlocks, kNT, 0, st>>>(N, src, zc, S, gk);
+  prof_end(st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = time_single<Tc>(zc, zc, g, pp, S, partials, gk, Jo, st);
+  if (e != cudaSuccess) return e;
+  int cur = 0;
+  for (int j = 0; j < pp.cheb; ++j) {
+    // the two axes commute: x, y, then x with the scaling fused into its loads, then y; the
+    // y passes take the tensor cores in float32 when the plan has the S_my image
+    e = launch_dst<Tc, Arr, Tc, true>(Arr{j == 0 ? zc : R}, W, g.mx, pp.Lx, nx, g.mx, g.m, twx, S,
+                                      gk, pp.dst_shift, st);
+    if (e != cudaSuccess) return e;
+    if ((e = y_pass(W)) != cudaSuccess) return e;
+    const SrcChebScale<Tc> sc{W, scoef + (size_t)j * g.n, sp.lh, sp.lht, sp.mux, sp.muy,
+                              (unsigned)g.m, (unsigned)g.mx};
+    e = launch_dst<Tc, SrcChebScale<Tc>, Tc, true>(sc, W, g.mx, pp.Lx, nx, g.mx, g.m, twx, S, gk,
+                                                   pp.dst_shift, st);
+    if (e != cudaSuccess) return e;
+    if ((e = y_pass(W)) != cudaSuccess) return e;
+    const Tc *aj = acoef + (size_t)j * g.n;
+    if (j + 1 < pp.cheb) {
+      prof_begin(KC_TIME, st);
+      k_cheb_resid<Tc><<<kChebBlocks, kNT, 0, st>>>(g, Dd[cur], W, Dd[cur ^ 1], j == 0 ? zc : R, R,
+                                                    X, aj, sp.lh, sp.lht, j == 0 ? 1 : 0, S, gk);
+      prof_end(st);
+      cur ^= 1;
+    } else {
+      prof_begin(KC_TIME, st);
+      k_cheb_final<Tc><<<kChebBlocks, kNT, 0, st>>>(N, g.m, Dd[cur], W, X, zc, R, aj,
+                                                    j == 0 ? 1 : 0, S, tmode, partials, gk);
+      prof_end(st);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
+  return time_single<Tc>(R, zc, g, pp, S, partials, gk, Jo, st);
+}
+
 // The stages of one preconditioner pass; `src` feeds the first one.
 // after_time (optional) is recorded once the time kernel (which performs the MINRES scalar step)
 // has been enqueued.
@@ -566,6 +782,9 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
   using Inner = SrcArray<Tc, Tout>;
   const int gk = gate_kind_of(tmode);
   cudaError_t e;
+  if (pp.cheb)
+    return cheb_stages<Tc>(g, pp, src, reinterpret_cast<Tc *>(z), S, tmode, partials, st,
+                           after_time);
   if (pp.pcr) {
     // P_theta with a varying 1D coefficient: time DST, tridiagonal solves, time DST
     Tc *zc = reinterpret_cast<Tc *>(z);
@@ -574,7 +793,7 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int Jo = sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d;
-    e = launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
+    e = time_single<Tc>(zc, zc, g, pp, S, partials, gk, Jo, st);
     if (e != cudaSuccess) return e;
     const size_t sm = (size_t)8 * g.mx * sizeof(Tc);
     auto kern = k_pcr_ptheta<Tc>;
@@ -585,7 +804,7 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
     prof_end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
-    return launch_time<Tc>(zc, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st);
+    return time_single<Tc>(zc, zc, g, pp, S, partials, gk, Jo, st);
   }
   const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
   e = launch_dst<Tc, Src, Tout, true>(src, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,

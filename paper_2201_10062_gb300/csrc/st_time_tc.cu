@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // level.  Same folded two-parity product as the time kernel, with S_len: one transform, no
 // scaling.  The next tile's input is staged by cp.async while the current one is transformed.
 __global__ void __launch_bounds__(kNT, 1)
-    k_dst_tc_y(float *data, int len, int mx, long long m, long long nplanes,
+    k_dst_tc_y(const float *data, float *out, int len, int mx, long long m, long long nplanes,
                const __half *sop_g, State *S, int gk) {
   if (gate_closed(S, gk)) return;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kNT, 1)
     // coalesced write-back: output row e holds coefficient k = e + 1 (parity e & 1)
     for (int idx = tid; idx < len * kTN; idx += kNT) {
       const int e = idx >> 5, c = idx & (kTN - 1);
-      if (c < je) data[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+      if (c < je) out[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
     }
   }
   cp_async_wait_all();
@@ -1005,20 +1005,43 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
   return cudaGetLastError();
 }
 
-cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
-                            int gk, cudaStream_t st) {
-  const uint32_t smem_bytes = dst_layout(g.my).total;
+// A multiple of 32 up to 256 (time axes: h = len/2 folded rows, a multiple of the K step) is
+// also accepted by the single-transform kernel, with the same layout limit
+bool dst_tc_len_supported(int len) {
+  if (dst_tc_supported(len)) return true;
+  return len >= 32 && len <= 256 && (len % 32) == 0 &&
+         dst_layout(len).total + 1024u <= 227u * 1024u;
+}
+
+// One DST-I of length len along lines `stride` apart, nplanes planes `plane` apart, 32 adjacent
+// lines per tile (k_dst_tc_y), from `in` to `out` (the same array, or one that does not overlap).
+cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride, long long plane,
+                                long long nplanes, const unsigned short *sop, State *S, int gk,
+                                int kc, cudaStream_t st) {
+  const uint32_t smem_bytes = dst_layout(len).total;
   cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
-  const long long ntiles = (long long)g.n * ((g.mx + kTN - 1) / kTN);
+  const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
   int grid = time_tc_grid();
   if (ntiles < grid) grid = (int)ntiles;
-  prof_begin(KC_DSTY, st);
-  k_dst_tc_y<<<grid, kNT, smem_bytes, st>>>(data, g.my, g.mx, g.m, (long long)g.n,
+  prof_begin(kc, st);
+  k_dst_tc_y<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
                                             reinterpret_cast<const __half *>(sop), S, gk);
   prof_end(st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st) {
+  return launch_dst_tc_lines(data, data, g.my, g.mx, g.m, (long long)g.n, sop, S, gk, KC_DSTY,
+                             st);
+}
+
+// The time DST alone (no scaling): lines of n values m apart, one plane of all m columns.
+cudaError_t launch_time_tc_single(const float *in, float *out, const Geom &g,
+                                  const unsigned short *sop, State *S, int gk, cudaStream_t st) {
+  return launch_dst_tc_lines(in, out, g.n, (int)g.m, g.N, 1, sop, S, gk, KC_TIME, st);
 }
 
 // ------------------------------------------------------------------ long time axes: host side

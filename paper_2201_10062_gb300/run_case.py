@@ -4,7 +4,9 @@
       --repeat 3
 
 Workloads (seeded, from ``workloads.synthetic``): ``cn2d`` (a = 1, Crank-Nicolson, manufactured
-rhs + N(0, 1e-3) noise), ``bdf2var`` (random a field, BDF2), ``sine1d`` (1D, backward Euler).
+rhs + N(0, 1e-3) noise), ``bdf2var`` (random a field, BDF2), ``thetavar`` (random a field,
+theta-method with --theta; with --prec Ptheta the Chebyshev inner map of --degree steps),
+``sine1d`` (1D, backward Euler).
 Prints one JSON line per solve with the iteration count, residuals and the time.
 """
 from __future__ import annotations
@@ -22,11 +24,13 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="cn2d", choices=["cn2d", "bdf2var", "sine1d"])
+    ap.add_argument("--workload", default="cn2d", choices=["cn2d", "bdf2var", "thetavar", "sine1d"])
     ap.add_argument("--mx", type=int, default=255)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--prec", default="PH", choices=["PH", "Ptheta"])
+    ap.add_argument("--theta", type=float, default=1.0, help="thetavar: theta of the time scheme")
+    ap.add_argument("--degree", type=int, default=0, help="Ptheta, 2D varying a: Chebyshev steps")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=400)
     ap.add_argument("--repeat", type=int, default=1)
@@ -44,10 +48,12 @@ def main(argv=None):
         w = W.config_2d_sine_cn(mx=args.mx, n=args.n)
     elif args.workload == "bdf2var":
         w = W.config_2d_varcoef_bdf2(mx=args.mx, n=args.n)
+    elif args.workload == "thetavar":
+        w = W.config_2d_varcoef_theta(args.mx, args.n, args.theta, seed=5)
     else:
         w = W.config_1d_sine(mx=args.mx, n=args.n)
     spec = P.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, args.prec,
-                         args.precision)
+                         args.precision, args.degree)
     s = P.Solver(spec)
     if args.autotune:
         s.st_autotune()
@@ -64,6 +70,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         print(json.dumps({"workload": w.name, "unknowns": w.N, "precision": args.precision,
+                          "prec": args.prec, "degree": args.degree,
                           "repeat": r, "seconds": dt, "unknowns_per_s": w.N / dt, **st}),
               flush=True)
     s.close()

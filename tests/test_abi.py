@@ -56,7 +56,10 @@ def _spec(**kw):
 @pytest.mark.parametrize("bad", [
     dict(mx=14), dict(my=16), dict(dim=3), dict(n=0), dict(n=2000), dict(T=0.0), dict(theta=1.5),
     dict(dim=1, my=3), dict(mx=2047), dict(prec="Ptheta", scheme="bdf2"),
-    dict(prec="Ptheta", a_nodal=np.ones((17, 17))),
+    dict(prec="Ptheta", a_nodal=np.ones((17, 17)), inner_degree=17),
+    dict(prec="Ptheta", a_nodal=np.ones((17, 17)), inner_degree=-1),
+    dict(inner_degree=2), dict(prec="Ptheta", inner_degree=2),
+    dict(dim=1, my=1, prec="Ptheta", a_nodal=np.ones(17), inner_degree=2),
 ])
 def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
     from paper_2201_10062_gb300 import ST_ERR_ARG
@@ -88,6 +91,18 @@ def test_workspace_bytes(lib):
     assert 9 * 8 * N <= b64 <= 9 * 8 * N + (64 << 20)
     # float32 z vectors, plus a double-float x accumulator and the tensor-core S_n image
     assert b32 <= b64 + (1 << 20)
+
+
+def test_workspace_bytes_chebyshev_ptheta(lib):
+    """P_theta with a 2D varying a adds five float64 scratch vectors and the step scalars."""
+    from paper_2201_10062_gb300 import st_workspace_bytes
+
+    a = np.ones((257, 257))
+    N = 255 * 255 * 64
+    base = st_workspace_bytes(_spec(mx=255, my=255, n=64, a_nodal=a))
+    for deg in (0, 1, 16):
+        b = st_workspace_bytes(_spec(mx=255, my=255, n=64, a_nodal=a, prec="Ptheta", inner_degree=deg))
+        assert 5 * 8 * N <= b - base <= 5 * 8 * N + (1 << 20)
 
 
 def test_null_arguments(lib):

@@ -274,6 +274,95 @@ def test_ptheta_solve(pkg, precision):
     s.close()
 
 
+# P_theta with a varying 2D coefficient: per-frequency Chebyshev inner map (degree 0 = the
+# library default); ragged sizes, n = 1, degree 1 (no residual pass)
+CHEB_CASES = [
+    (15, 15, 8, 0.5, 3),
+    (31, 15, 12, 1.0, 1),
+    (63, 31, 5, 0.3, 5),
+    (7, 7, 1, 0.5, 2),
+    (127, 127, 16, 0.5, 0),
+]
+
+
+def _cheb_tol32(p, degree):
+    """float32 tolerance of the Chebyshev map: each step forms r - A_k d, whose rounding relative
+    to the result grows with the condition of A_k, at most (lam_H + c a_max mu0_max) /
+    (lam_H + c a_min mu0_min), c = lam_Htheta tau; the steps add their errors."""
+    ax, ay = H.face_values(p)
+    fmin = min(ax.min(), ay.min())
+    fmax = max(ax.max(), ay.max())
+    mu = H.constant_stiffness_eigs(p)
+    lh, lt = H.ptheta_time_eigs(p.n, p.theta)
+    cond = max((lh + lt * p.tau * fmax * mu.max()) / (lh + lt * p.tau * fmin * mu.min()))
+    return max(2e-5, 4 * 2.0 ** -24 * cond * degree)
+
+
+@pytest.mark.parametrize("case", CHEB_CASES, ids=lambda c: f"{c[0]}x{c[1]}-n{c[2]}-th{c[3]}-d{c[4]}")
+def test_ptheta_cheb_apply(pkg, case):
+    mx, my, n, theta, deg = case
+    w = W.small_case(2, mx, my, n, theta=theta, varcoef=True, seed=mx + 5 * n)
+    d_used = deg if deg else pkg.ST_PTHETA_DEFAULT_DEGREE
+    p = H.Problem.from_workload(w, prec="Ptheta", inner_degree=d_used)
+    spec = _spec(pkg, w, prec="Ptheta")
+    spec.inner_degree = deg
+    s = pkg.Solver(spec)
+    v = np.random.default_rng(9).standard_normal((n, p.m))
+    ref = H.apply_ptheta(p, v)
+    z = _h(s.st_apply_prec(_d(v))).reshape(n, p.m)
+    assert _rel_max(z, ref) <= 1e-11
+    z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(n, p.m)
+    assert _rel2(z32, ref) <= _cheb_tol32(p, d_used)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ptheta_cheb_solve(pkg, precision):
+    """MINRES with the Chebyshev P_theta (2D varying a, degree 3): equal-iteration parity and
+    iteration count within one of the oracle (float64), error against the converged oracle
+    solution (mixed)."""
+    w = W.small_case(2, 31, 31, 16, theta=0.5, varcoef=True, seed=43)
+    p = H.Problem.from_workload(w, prec="Ptheta", inner_degree=3)
+    fH = H.rhs(p, w.f, w.u0)
+    spec = _spec(pkg, w, prec="Ptheta", precision=precision)
+    spec.inner_degree = 3
+    s = pkg.Solver(spec)
+    if precision == "fp64":
+        u, st = s.st_solve(_d(fH), tol=0.0, maxit=9, allow_not_converged=True)
+        x_or, info = H.solve(p, fH, tol=0.0, maxit=9, rule="est")
+        assert st["iterations"] == info["iterations"] == 9
+        assert _rel2(_h(u).reshape(p.n, p.m), x_or) <= 1e-10
+        u, st = s.st_solve(_d(fH), tol=1e-8, maxit=200)
+        x_or, info = H.solve(p, fH, tol=1e-8, maxit=200)
+        assert abs(st["iterations"] - info["iterations"]) <= 1
+        assert _rel2(_h(u).reshape(p.n, p.m), x_or) <= 1e-6
+    else:
+        x_ref, info = H.solve(p, fH, tol=1e-13, maxit=400)
+        u, st = s.st_solve(_d(fH), tol=1e-10, maxit=400)
+        assert st["true_rel_res"] <= 1e-10
+        assert _rel2(_h(u).reshape(p.n, p.m), x_ref) <= 1e-8
+    s.close()
+
+
+def test_ptheta_cheb_full_size(pkg):
+    """2D 255^2, n = 256, theta = 1, seeded 8x8-mode coefficient field (the adjoint problem's
+    shape) with the Chebyshev P_theta: full-vector apply parity (float64), and a mixed-precision
+    solve that reaches 1e-8, checked with the oracle's operator."""
+    w = W.config_2d_varcoef_theta(255, 256, 1.0, seed=5)
+    p = H.Problem.from_workload(w, prec="Ptheta", inner_degree=pkg.ST_PTHETA_DEFAULT_DEGREE)
+    s = pkg.Solver(_spec(pkg, w, prec="Ptheta"))
+    v = np.random.default_rng(10).standard_normal((p.n, p.m))
+    assert _rel_max(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m), H.apply_ptheta(p, v)) <= 1e-11
+    s.close()
+    s = pkg.Solver(_spec(pkg, w, prec="Ptheta", precision="mixed"))
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0))
+    u, st = s.st_solve(fH, tol=1e-8, maxit=400)
+    fH_or = H.rhs(p, w.f, w.u0)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, _h(u).reshape(p.n, p.m))
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-8 * (1 + 1e-6)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_size_2d_varcoef_bdf2(pkg, precision):
     """2D 511^2, n = 128, BDF2, seeded 8x8-mode coefficient field: the solve reaches 1e-8 (checked

@@ -63,3 +63,37 @@ def test_tc_time_dst_matches_oracle_and_ffma(pkg, dim, mx, my, n, scheme, theta)
     assert _rel2(z_tc, z_ff) <= 2e-5
     s_tc.close()
     s_ff.close()
+
+
+# The P_theta paths with a varying coefficient transform time alone (no scaling); for n a
+# multiple of 32 up to 256 that transform runs on the tensor cores.  1D: PCR blocks; 2D: the
+# Chebyshev inner map (degree 0 = the library default).
+@pytest.mark.parametrize("dim,mx,my,n,theta,deg", [
+    (1, 127, 1, 64, 1.0, 0),
+    (2, 31, 15, 32, 0.5, 2),
+    (2, 15, 15, 256, 0.5, 2),
+    (2, 63, 63, 96, 1.0, 3),
+])
+def test_tc_single_time_transform_ptheta(pkg, dim, mx, my, n, theta, deg):
+    w = W.small_case(dim, mx, my, n, scheme="theta", theta=theta, varcoef=True, seed=n + mx)
+    d_used = (deg if deg else pkg.ST_PTHETA_DEFAULT_DEGREE) if dim == 2 else None
+    p = H.Problem.from_workload(w, prec="Ptheta", inner_degree=d_used)
+    v = np.random.default_rng(8).standard_normal((n, p.m))
+    ref = H.apply_ptheta(p, v)
+    spec = pkg.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, "Ptheta",
+                           "mixed", deg)
+    s_tc = pkg.Solver(spec)
+    z_tc = s_tc.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    os.environ["ST_DISABLE_TENSOR_CORES"] = "1"
+    try:
+        s_ff = pkg.Solver(spec)
+    finally:
+        del os.environ["ST_DISABLE_TENSOR_CORES"]
+    z_ff = s_ff.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    # float32 errors of the per-frequency solves dominate and are the same on both paths; the
+    # tensor-core transform adds float32-level rounding of its own
+    e_ff = _rel2(z_ff.reshape(n, p.m), ref)
+    assert _rel2(z_tc.reshape(n, p.m), ref) <= max(2e-5, 2 * e_ff)
+    assert _rel2(z_tc, z_ff) <= max(2e-5, 2 * e_ff)
+    s_tc.close()
+    s_ff.close()
