@@ -32,6 +32,11 @@ Pins (tests/test_oracle_*.py) tie each function to something other than itself:
     d equals I - T_d-polynomial (numpy Chebyshev series) on that spectrum, symmetric
     positive definite; degree 40 reproduces the sparse LU solve; a constant field is
     exact at any degree; the whole P_theta^-1 stays within the Chebyshev bound of exact.
+  * 3D (Sec. 5, Example 3): the 7-point K equals the Kronecker sum of 1D second
+    differences for constant a and the face energy form for varying a; the 3D
+    transform diagonalises it in the stated order; Y T symmetric, marching, the
+    block matrix of P_H^2 and the Chebyshev interval in 3D; the iteration counts of
+    Tables 6-7 within one.
   * minres: the ideal preconditioner sqrt(T^T T) converges in at most two
     steps (Proposition absC); each iterate's preconditioned residual equals the
     brute-force least-squares minimum over the explicit Krylov basis; residual
@@ -70,13 +75,14 @@ class Problem:
     theta: float = 1.0
     a_nodal: Optional[np.ndarray] = None
     prec: str = "PH"  # "PH" (eq. def:matrix_P / def:matrix_P_gen) or "Ptheta" (eq. def:matrix_mod_P)
-    # P_theta with a 2D varying a: degree of the Chebyshev inner map of step 2 (Sec. 3.1.4);
+    # P_theta with a 2D or 3D varying a: degree of the Chebyshev inner map of step 2 (Sec. 3.1.4);
     # None solves every per-frequency system exactly (sparse LU)
     inner_degree: Optional[int] = None
+    mz: int = 1  # interior points along z (3D, Sec. 5 Example 3); 1 in 1D and 2D
 
     @property
     def m(self) -> int:
-        return self.mx * self.my
+        return self.mx * self.my * self.mz
 
     @property
     def N(self) -> int:
@@ -94,10 +100,14 @@ class Problem:
     def hy(self) -> float:
         return 1.0 / (self.my + 1)
 
+    @property
+    def hz(self) -> float:
+        return 1.0 / (self.mz + 1)
+
     @staticmethod
     def from_workload(w, prec: str = "PH", inner_degree: Optional[int] = None) -> "Problem":
         return Problem(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec,
-                       inner_degree)
+                       inner_degree, getattr(w, "mz", 1))
 
 
 # --------------------------------------------------------------------------------------
@@ -106,7 +116,8 @@ class Problem:
 def nodal_a(prob: Problem) -> np.ndarray:
     if prob.a_nodal is not None:
         return np.asarray(prob.a_nodal, dtype=np.float64)
-    shape = (prob.mx + 2,) if prob.dim == 1 else (prob.my + 2, prob.mx + 2)
+    shape = ((prob.mx + 2,) if prob.dim == 1 else (prob.my + 2, prob.mx + 2) if prob.dim == 2
+             else (prob.mz + 2, prob.my + 2, prob.mx + 2))
     return np.ones(shape)
 
 
@@ -117,9 +128,16 @@ def face_values(prob: Problem):
     onto them. Returns (ax, ay): ax[j, i] is the face between x-nodes i and i+1
     (node index 0 and mx+1 are boundary nodes) on interior row j, shape
     (my, mx+1); ay[j, i] the face between y-nodes j and j+1 on interior column
-    i, shape (my+1, mx). In 1D ay is None and ax has shape (1, mx+1).
+    i, shape (my+1, mx). In 1D ay is None and ax has shape (1, mx+1).  In 3D (the same reading
+    along a third axis) the result is (ax, ay, az) with shapes (mz, my, mx+1), (mz, my+1, mx) and
+    (mz+1, my, mx), each face between two nodes of its axis on interior lines of the others.
     """
     a = nodal_a(prob)
+    if prob.dim == 3:
+        ax = 0.5 * (a[1:-1, 1:-1, :-1] + a[1:-1, 1:-1, 1:])
+        ay = 0.5 * (a[1:-1, :-1, 1:-1] + a[1:-1, 1:, 1:-1])
+        az = 0.5 * (a[:-1, 1:-1, 1:-1] + a[1:, 1:-1, 1:-1])
+        return ax, ay, az
     if prob.dim == 1:
         ax = 0.5 * (a[:-1] + a[1:])
         return ax[None, :], None
@@ -134,7 +152,10 @@ def stiffness(prob: Problem) -> sp.csr_matrix:
     1D: the tridiagonal matrix of eq. matrix_Km_va,
     (1/h^2) [ -a_{i-1/2}, a_{i-1/2} + a_{i+1/2}, -a_{i+1/2} ].
     2D: the same three-point form along x and along y, summed (5-point).
+    3D: the same along x, y and z (7-point), assembled with array indexing.
     """
+    if prob.dim == 3:
+        return _stiffness_3d(prob)
     mx, my = prob.mx, prob.my
     ax, ay = face_values(prob)
     m = mx * my
@@ -161,6 +182,25 @@ def stiffness(prob: Problem) -> sp.csr_matrix:
                     rows.append(p); cols.append(idx(i, j + 1)); vals.append(-nn)
             rows.append(p); cols.append(p); vals.append(diag)
     return sp.csr_matrix((vals, (rows, cols)), shape=(m, m))
+
+
+def _stiffness_3d(prob: Problem) -> sp.csr_matrix:
+    """7-point K: node p couples to its neighbour q across face f with -a_f/h^2 and its diagonal
+    is the sum of a_f/h^2 over its six faces (faces on the boundary included)."""
+    mx, my, mz = prob.mx, prob.my, prob.mz
+    ax, ay, az = face_values(prob)
+    wx, wy, wz = ax / prob.hx ** 2, ay / prob.hy ** 2, az / prob.hz ** 2
+    idx = np.arange(prob.m).reshape(mz, my, mx)
+    diag = (wx[:, :, :-1] + wx[:, :, 1:]) + (wy[:, :-1, :] + wy[:, 1:, :]) + (wz[:-1] + wz[1:])
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [diag.ravel()]
+    for c, p, q in ((wx[:, :, 1:-1], idx[:, :, :-1], idx[:, :, 1:]),
+                    (wy[:, 1:-1, :], idx[:, :-1, :], idx[:, 1:, :]),
+                    (wz[1:-1], idx[:-1], idx[1:])):
+        rows += [p.ravel(), q.ravel()]
+        cols += [q.ravel(), p.ravel()]
+        vals += [-c.ravel(), -c.ravel()]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(prob.m, prob.m))
 
 
 def time_blocks(prob: Problem, K: Optional[sp.csr_matrix] = None):
@@ -282,10 +322,13 @@ def dst(v: np.ndarray, axis: int) -> np.ndarray:
 
 
 def spatial_dst(prob: Problem, V: np.ndarray) -> np.ndarray:
-    """(I_n (x) U_m) with U_m = S_my (x) S_mx (x fastest); S is its own inverse."""
-    W = np.asarray(V, dtype=np.float64).reshape(prob.n, prob.my, prob.mx)
-    W = dst(W, axis=2)
-    if prob.dim == 2:
+    """(I_n (x) U_m) with U_m = S_my (x) S_mx (x fastest), S_mz (x) S_my (x) S_mx in 3D; S is its
+    own inverse."""
+    W = np.asarray(V, dtype=np.float64).reshape(prob.n, prob.mz, prob.my, prob.mx)
+    W = dst(W, axis=3)
+    if prob.dim >= 2:
+        W = dst(W, axis=2)
+    if prob.dim == 3:
         W = dst(W, axis=1)
     return W.reshape(prob.n, prob.m)
 
@@ -307,7 +350,7 @@ def averaged_stiffness_eigs(prob: Problem) -> np.ndarray:
     y-couplings separately (only couplings that exist), giving
     Kbar = d I - e_x (shift_x + shift_x^T) - e_y (shift_y + shift_y^T), whose
     eigenvalues are d - 2 e_x cos(i pi/(mx+1)) - 2 e_y cos(j pi/(my+1)).
-    For constant a this is exactly K.
+    For constant a this is exactly K.  3D: the z-couplings are averaged apart as well.
     """
     K = stiffness(prob).tocoo()
     mx = prob.mx
@@ -315,15 +358,22 @@ def averaged_stiffness_eigs(prob: Problem) -> np.ndarray:
     d = v[r == c].mean()
     xmask = np.abs(r - c) == 1
     ex = -v[xmask].mean() if np.any(xmask) else 0.0
-    ey = 0.0
-    if prob.dim == 2:
+    ey = ez = 0.0
+    if prob.dim >= 2:
         ymask = np.abs(r - c) == mx
         ey = -v[ymask].mean() if np.any(ymask) else 0.0
+    if prob.dim == 3:
+        zmask = np.abs(r - c) == mx * prob.my
+        ez = -v[zmask].mean() if np.any(zmask) else 0.0
     cx = np.cos(np.arange(1, mx + 1) * math.pi / (mx + 1))
     if prob.dim == 1:
         return d - 2.0 * ex * cx
     cy = np.cos(np.arange(1, prob.my + 1) * math.pi / (prob.my + 1))
-    return (d - 2.0 * ex * cx[None, :] - 2.0 * ey * cy[:, None]).reshape(-1)
+    if prob.dim == 2:
+        return (d - 2.0 * ex * cx[None, :] - 2.0 * ey * cy[:, None]).reshape(-1)
+    cz = np.cos(np.arange(1, prob.mz + 1) * math.pi / (prob.mz + 1))
+    return (d - 2.0 * ex * cx[None, None, :] - 2.0 * ey * cy[None, :, None]
+            - 2.0 * ez * cz[:, None, None]).reshape(-1)
 
 
 def time_cos(n: int) -> np.ndarray:
@@ -399,7 +449,7 @@ def apply_ptheta(prob: Problem, v: np.ndarray, K: Optional[sp.csr_matrix] = None
     restored in the second term, as in the definition eq. def:matrix_mod_P)."""
     if K is None:
         K = stiffness(prob)
-    if prob.dim == 2 and prob.a_nodal is not None and prob.inner_degree is not None:
+    if prob.dim >= 2 and prob.a_nodal is not None and prob.inner_degree is not None:
         return apply_ptheta_cheb(prob, v, prob.inner_degree, K)
     lam_h, lam_ht = ptheta_time_eigs(prob.n, prob.theta)
     vt = time_dst(prob, v)
@@ -426,7 +476,10 @@ def constant_stiffness_eigs(prob: Problem) -> np.ndarray:
     if prob.dim == 1:
         return ex
     ey = 4.0 * np.sin(np.arange(1, prob.my + 1) * math.pi / (2 * (prob.my + 1))) ** 2 / prob.hy ** 2
-    return (ey[:, None] + ex[None, :]).reshape(-1)
+    if prob.dim == 2:
+        return (ey[:, None] + ex[None, :]).reshape(-1)
+    ez = 4.0 * np.sin(np.arange(1, prob.mz + 1) * math.pi / (2 * (prob.mz + 1))) ** 2 / prob.hz ** 2
+    return (ez[:, None, None] + ey[None, :, None] + ex[None, None, :]).reshape(-1)
 
 
 def ptheta_cheb_bounds(prob: Problem):
@@ -440,8 +493,7 @@ def ptheta_cheb_bounds(prob: Problem):
     tau the generalised eigenvalues of (A_k, B_k) lie in
       [(lam + c a_min mu_max)/(lam + c abar mu_max), (lam + c a_max mu_max)/(lam + c abar mu_max)].
     """
-    ax, ay = face_values(prob)
-    faces = np.concatenate([ax.reshape(-1), ay.reshape(-1)]) if ay is not None else ax.reshape(-1)
+    faces = np.concatenate([f.reshape(-1) for f in face_values(prob) if f is not None])
     amin, amax, abar = float(faces.min()), float(faces.max()), float(faces.mean())
     lam_h, lam_ht = ptheta_time_eigs(prob.n, prob.theta)
     mu_max = float(constant_stiffness_eigs(prob).max())
@@ -490,9 +542,11 @@ def ptheta_cheb_blocks(prob: Problem, k: int, K: Optional[sp.csr_matrix] = None)
 
 
 def space_dst(prob: Problem, r: np.ndarray) -> np.ndarray:
-    """U_m r for one space vector (S_my (x) S_mx, x fastest)."""
-    R = dst(np.asarray(r, dtype=np.float64).reshape(prob.my, prob.mx), axis=1)
-    if prob.dim == 2:
+    """U_m r for one space vector (S_my (x) S_mx, x fastest; S_mz (x) S_my (x) S_mx in 3D)."""
+    R = dst(np.asarray(r, dtype=np.float64).reshape(prob.mz, prob.my, prob.mx), axis=2)
+    if prob.dim >= 2:
+        R = dst(R, axis=1)
+    if prob.dim == 3:
         R = dst(R, axis=0)
     return R.reshape(-1)
 
@@ -802,6 +856,8 @@ def adjoint_gradients(prob: Problem, u: np.ndarray, lam: np.ndarray, u0: np.ndar
         gf[1:] += tau * L
         gu0 = 2.0 * L[0] - (0.5 * L[1] if n > 1 else 0.0)
         W = U
+    if prob.dim == 3:
+        raise NotImplementedError("the a-gradient is written for 1D and 2D grids")
     mx, my = prob.mx, prob.my
     Lg = L.reshape(n, my, mx)
     Wg = W.reshape(n, my, mx)

@@ -14,9 +14,9 @@ from workloads import synthetic as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _tiny(dim, scheme, theta=0.5, varcoef=True, mx=4, my=3, n=6, seed=11):
+def _tiny(dim, scheme, theta=0.5, varcoef=True, mx=4, my=3, n=6, seed=11, mz=3):
     my = 1 if dim == 1 else my
-    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=varcoef, seed=seed)
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=varcoef, seed=seed, mz=mz)
     return w, H.Problem.from_workload(w)
 
 
@@ -46,10 +46,10 @@ def test_dst_routine_is_sine_matrix(n, axis):
 
 
 # ----------------------------------------------------------------------------- space operator
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 def test_stiffness_energy_form(dim):
     """v^T K v = sum over faces a_f (v_p - v_q)^2 / h^2 with zero boundary values (eq. matrix_Km_va)."""
-    w, p = _tiny(dim, "theta", mx=6, my=5)
+    w, p = _tiny(dim, "theta", mx=6, my=5, mz=4)
     K = H.stiffness(p).toarray()
     assert np.allclose(K, K.T)
     rng = np.random.default_rng(1)
@@ -61,6 +61,23 @@ def test_stiffness_energy_form(dim):
         for i in range(p.mx + 1):
             af = 0.5 * (a[i] + a[i + 1])
             e += af * (vp[i + 1] - vp[i]) ** 2 / p.hx ** 2
+    elif dim == 3:
+        V = np.zeros((p.mz + 2, p.my + 2, p.mx + 2))
+        V[1:-1, 1:-1, 1:-1] = v.reshape(p.mz, p.my, p.mx)
+        for k in range(p.mz + 2):
+            for j in range(p.my + 2):
+                for i in range(p.mx + 2):
+                    # the face towards +x, +y, +z of node (k, j, i) when both ends lie on a line
+                    # of interior nodes of the other two axes
+                    if i <= p.mx and 1 <= j <= p.my and 1 <= k <= p.mz:
+                        af = 0.5 * (a[k, j, i] + a[k, j, i + 1])
+                        e += af * (V[k, j, i + 1] - V[k, j, i]) ** 2 / p.hx ** 2
+                    if j <= p.my and 1 <= i <= p.mx and 1 <= k <= p.mz:
+                        af = 0.5 * (a[k, j, i] + a[k, j + 1, i])
+                        e += af * (V[k, j + 1, i] - V[k, j, i]) ** 2 / p.hy ** 2
+                    if k <= p.mz and 1 <= i <= p.mx and 1 <= j <= p.my:
+                        af = 0.5 * (a[k, j, i] + a[k + 1, j, i])
+                        e += af * (V[k + 1, j, i] - V[k, j, i]) ** 2 / p.hz ** 2
     else:
         V = np.zeros((p.my + 2, p.mx + 2))
         V[1:-1, 1:-1] = v.reshape(p.my, p.mx)
@@ -89,8 +106,30 @@ def test_stiffness_constant_eigenvectors():
     assert np.allclose(np.sort(mu), np.sort(np.linalg.eigvalsh(K.toarray())), rtol=1e-12)
 
 
+def test_stiffness_3d_constant_is_kronecker_sum():
+    """3D, constant a: K = a (T_z/hz^2 (x) I (x) I + I (x) T_y/hy^2 (x) I + I (x) I (x) T_x/hx^2)
+    with T = tridiag(-1, 2, -1), built here by Kronecker products; its eigenvalues are the sums
+    of the three 1D ones, which the a = 1 and the averaged spectra reproduce."""
+    mx, my, mz, c = 5, 4, 3, 1.7
+    p = H.Problem(3, mx, my, 2, a_nodal=np.full((mz + 2, my + 2, mx + 2), c), mz=mz)
+    T = lambda k: 2 * np.eye(k) - np.eye(k, k=1) - np.eye(k, k=-1)  # noqa: E731
+    I = np.eye
+    ref = c * (np.kron(np.kron(T(mz), I(my)), I(mx)) / p.hz ** 2
+               + np.kron(np.kron(I(mz), T(my)), I(mx)) / p.hy ** 2
+               + np.kron(np.kron(I(mz), I(my)), T(mx)) / p.hx ** 2)
+    assert np.allclose(H.stiffness(p).toarray(), ref, rtol=1e-13, atol=1e-9)
+    ev = np.sort(np.linalg.eigvalsh(ref))
+    assert np.allclose(np.sort(H.averaged_stiffness_eigs(p)), ev, rtol=1e-12)
+    assert np.allclose(np.sort(c * H.constant_stiffness_eigs(p)), ev, rtol=1e-12)
+    # the 3D transform diagonalises it in the stated order (x fastest)
+    S = np.kron(np.kron(H.dst_matrix(mz), H.dst_matrix(my)), H.dst_matrix(mx))
+    assert np.allclose(S @ ref @ S, np.diag(c * H.constant_stiffness_eigs(p)), atol=1e-8)
+    v = np.random.default_rng(2).standard_normal((2, p.m))
+    assert np.allclose(H.spatial_dst(p, v), v @ S, atol=1e-12)
+
+
 # ----------------------------------------------------------------------------- all-at-once system
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("scheme", ["theta", "bdf2"])
 def test_flipped_operator_symmetric(dim, scheme):
     """Y T is symmetric (eq. main_system / main_system_gem_sym) and T^T = Y T Y."""
@@ -108,7 +147,7 @@ def test_flipped_operator_symmetric(dim, scheme):
     assert np.allclose(H.apply_T_transpose(p, v).reshape(-1), T.T @ v, atol=1e-12)
 
 
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("scheme,theta", [("theta", 1.0), ("theta", 0.5), ("theta", 0.3), ("bdf2", 1.0)])
 def test_all_at_once_equals_time_marching(dim, scheme, theta):
     """Solving T u = f_H at once equals stepping the scheme sequentially (Sec. 1)."""
@@ -160,6 +199,17 @@ def test_table5_backward_euler_errors():
         assert float(f"{err:.2e}") == ref, (n, err, ref)
 
 
+def test_table_iteration_counts_3d():
+    """Example 3 (3D) iteration counts of Tables 6-7 (P_H, P_theta), within one."""
+    g = json.load(open(os.path.join(GOLDEN, "table_iterations_3d.json")))
+    for c in g["cases"]:
+        w = W.paper_example3(c["m_plus_1"] - 1, c["n"], c["theta"])
+        p = H.Problem.from_workload(w, prec=c["prec"])
+        fH = H.rhs(p, w.f, w.u0)
+        x, info = H.solve(p, fH, tol=1e-6, maxit=100)
+        assert abs(info["iterations"] - c["iter"]) <= g["tolerance_iterations"], (c, info["iterations"])
+
+
 def test_table_iteration_counts():
     """Iteration counts of Tables 1-3 (P_H, P_theta) within +-2 (stopping-rule details differ)."""
     g = json.load(open(os.path.join(GOLDEN, "table_iterations.json")))
@@ -187,14 +237,22 @@ def _averaged_dense_K(p):
     for i in range(m - 1):
         if (i % mx) != mx - 1:
             Kb[i, i + 1] = Kb[i + 1, i] = ex
-    if p.dim == 2:
-        ey = np.mean(np.diag(K, mx))
-        for i in range(m - mx):
+    if p.dim >= 2:
+        # y-couplings exist between rows of one z-plane only
+        pl = mx * p.my
+        cols = [i for i in range(m - mx) if (i % pl) < pl - mx]
+        ey = np.mean([K[i, i + mx] for i in cols])
+        for i in cols:
             Kb[i, i + mx] = Kb[i + mx, i] = ey
+    if p.dim == 3:
+        pl = mx * p.my
+        ez = np.mean(np.diag(K, pl))
+        for i in range(m - pl):
+            Kb[i, i + pl] = Kb[i + pl, i] = ez
     return Kb
 
 
-@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("scheme", ["theta", "bdf2"])
 @pytest.mark.parametrize("varcoef", [False, True])
 def test_prec_squared_is_block_matrix(dim, scheme, varcoef):
@@ -337,6 +395,24 @@ def test_cheb_high_degree_is_the_exact_solve():
     equals the exact per-frequency sparse LU solve."""
     p = _cheb_case(mx=15, my=7, n=5)
     v = np.random.default_rng(4).standard_normal((p.n, p.m))
+    exact = H.apply_ptheta(p, v)
+    p.inner_degree = 40
+    assert np.linalg.norm(H.apply_ptheta(p, v) - exact) <= 1e-12 * np.linalg.norm(exact)
+
+
+def test_cheb_3d_interval_and_limit():
+    """3D (faces along z as well): the interval holds the dense generalised spectrum of
+    (A_k, B_k), and degree 40 reproduces the exact per-frequency solve."""
+    import scipy.linalg as sla
+    w = W.small_case(3, 5, 4, 3, scheme="theta", theta=0.5, varcoef=True, seed=23, mz=3)
+    p = H.Problem.from_workload(w, prec="Ptheta")
+    _, al, be = H.ptheta_cheb_bounds(p)
+    S = np.kron(np.kron(H.dst_matrix(p.mz), H.dst_matrix(p.my)), H.dst_matrix(p.mx))
+    for k in range(p.n):
+        Ak, bk = H.ptheta_cheb_blocks(p, k)
+        lam = sla.eigh(Ak.toarray(), S @ np.diag(bk) @ S, eigvals_only=True)
+        assert lam.min() >= al[k] * (1 - 1e-12) and lam.max() <= be[k] * (1 + 1e-12)
+    v = np.random.default_rng(6).standard_normal((p.n, p.m))
     exact = H.apply_ptheta(p, v)
     p.inner_degree = 40
     assert np.linalg.norm(H.apply_ptheta(p, v) - exact) <= 1e-12 * np.linalg.norm(exact)

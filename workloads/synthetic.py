@@ -57,10 +57,11 @@ class Workload:
     u_exact: Optional[np.ndarray] = None  # (n, m) exact solution at t_1..t_n
     noise: Optional[np.ndarray] = None  # (n, m) added to the all-at-once rhs
     extra: dict = field(default_factory=dict)
+    mz: int = 1  # interior points along z (3D); 1 in 1D and 2D
 
     @property
     def m(self) -> int:
-        return self.mx * self.my
+        return self.mx * self.my * self.mz
 
     @property
     def N(self) -> int:
@@ -306,15 +307,68 @@ def paper_example2(mx: int, n: int, theta: float, T: float = 1.0) -> Workload:
 
 
 def small_case(dim: int, mx: int, my: int, n: int, scheme: str = "theta", theta: float = 1.0,
-               varcoef: bool = False, seed: int = 7, T: float = 1.0) -> Workload:
-    """Small random instance for parity tests: seeded f, u0 (and a if varcoef)."""
+               varcoef: bool = False, seed: int = 7, T: float = 1.0, mz: int = 1) -> Workload:
+    """Small random instance for parity tests: seeded f, u0 (and a if varcoef).  dim = 3 takes
+    mz interior points along z."""
     rng = np.random.default_rng(seed)
-    m = mx * my
+    mz = mz if dim == 3 else 1
+    m = mx * my * mz
     f = rng.standard_normal((n + 1, m))
     u0 = rng.standard_normal(m)
     u_prev = rng.standard_normal(m) if scheme == "bdf2" else None
     a = None
     if varcoef:
-        a = random_field(mx, my, seed + 1) if dim == 2 else random_field_1d(mx, seed + 1)
-    return Workload(f"small_{dim}d_{mx}x{my}x{n}_{scheme}", dim, mx, my, n, T, scheme, theta, a, f,
-                    u0, u_prev)
+        if dim == 3:
+            a = random_field_3d(mx, my, mz, seed + 1)
+        else:
+            a = random_field(mx, my, seed + 1) if dim == 2 else random_field_1d(mx, seed + 1)
+    name = f"small_{dim}d_{mx}x{my}" + (f"x{mz}" if dim == 3 else "") + f"x{n}_{scheme}"
+    return Workload(name, dim, mx, my, n, T, scheme, theta, a, f, u0, u_prev, mz=mz)
+
+
+def random_field_3d(mx: int, my: int, mz: int, seed: int, modes: int = 4,
+                    amp: float = 0.5) -> np.ndarray:
+    """Nodal a on the (mz+2, my+2, mx+2) grid (boundary nodes included): 1 + amp F / max|F| with
+    F = sum_{p,q,r <= modes} c_pqr sin(p pi x) sin(q pi y) sin(r pi z), c_pqr ~ U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1.0, 1.0, (modes, modes, modes))
+    x = np.linspace(0.0, 1.0, mx + 2)
+    y = np.linspace(0.0, 1.0, my + 2)
+    z = np.linspace(0.0, 1.0, mz + 2)
+    k = np.arange(1, modes + 1)
+    sx = np.sin(math.pi * k[:, None] * x[None, :])  # (modes, mx+2)
+    sy = np.sin(math.pi * k[:, None] * y[None, :])
+    sz = np.sin(math.pi * k[:, None] * z[None, :])
+    F = np.einsum("pqr,rk,qj,pi->kji", c, sz, sy, sx)
+    fmax = np.abs(F).max()
+    return np.ascontiguousarray(1.0 + amp * F / fmax if fmax > 0 else np.ones_like(F))
+
+
+def interior_grid_3d(mx: int, my: int, mz: int):
+    """Interior node coordinates as 3D arrays [k, j, i] (x fastest)."""
+    x = np.arange(1, mx + 1) / (mx + 1)
+    y = np.arange(1, my + 1) / (my + 1)
+    z = np.arange(1, mz + 1) / (mz + 1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def paper_example3(mx: int, n: int, theta: float, a_const: float = 1e-3, T: float = 1.0) -> Workload:
+    """Example 3 shape: the unit cube, a = 1e-3, u0 = x(x-1)y(y-1)z(z-1), f = 0 (Sec. 5,
+    Example 3)."""
+    X, Y, Z = interior_grid_3d(mx, mx, mx)
+    u0 = (X * (X - 1) * Y * (Y - 1) * Z * (Z - 1)).reshape(-1)
+    a_nodal = np.full((mx + 2, mx + 2, mx + 2), a_const)
+    f = np.zeros((n + 1, mx ** 3))
+    return Workload("paper_ex3", 3, mx, mx, n, T, "theta", theta, a_nodal, f, u0, mz=mx)
+
+
+def config_3d_sine(mx: int = 63, n: int = 64, T: float = 1.0, theta: float = 0.5) -> Workload:
+    """3D, a = 1, u = sin(pi x) sin(pi y) sin(pi z) e^t, f = (1 + 3 pi^2) u."""
+    X, Y, Z = interior_grid_3d(mx, mx, mx)
+    base = (np.sin(math.pi * X) * np.sin(math.pi * Y) * np.sin(math.pi * Z)).reshape(-1)
+    t = _times(n, T)
+    f = (1.0 + 3.0 * math.pi ** 2) * np.exp(t)[:, None] * base[None, :]
+    u_exact = np.exp(t[1:])[:, None] * base[None, :]
+    return Workload(f"3d_sine_{mx}_{n}", 3, mx, mx, n, T, "theta", theta, None, f, base.copy(),
+                    None, u_exact, mz=mx)
