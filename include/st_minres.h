@@ -6,14 +6,16 @@
  * for all-at-once systems from constant and variable-coefficient evolutionary PDEs"
  * (arXiv 2201.10062).  The heat equation u_t = div(a grad u) + f on (0,1)^dim x (0,T], u = 0 on
  * the boundary (Sec. 1, eq. heat), is discretised with finite differences in space (M = I, K the
- * 3-/5-point stiffness matrix of eq. matrix_Km_va) and the theta-method (Sec. 1, eq. theta) or
+ * 3-/5-/7-point stiffness matrix of eq. matrix_Km_va in 1D/2D/3D; 3D as in Sec. 5, Example 3)
+ * and the theta-method (Sec. 1, eq. theta) or
  * BDF2 (Sec. 4, eq. matrix_gen) in time.  The all-at-once system T u = f_H is flipped to the
  * symmetric Y T u = Y f_H (eq. main_system) and solved by MINRES with the SPD preconditioner P_H
  * (eq. def:matrix_P), P-hat (eq. def:matrix_P_gen) or P_theta (eq. def:matrix_mod_P).
  *
  * Conventions shared by every entry point
- *   - Grid: interior nodes only; x_i = (i+1)/(mx+1), y_j = (j+1)/(my+1); dim 1 has my = 1.
- *   - A space vector has m = mx*my entries, index j*mx + i (x fastest).
+ *   - Grid: interior nodes only; x_i = (i+1)/(mx+1), y_j = (j+1)/(my+1), z_l = (l+1)/(mz+1);
+ *     dim 1 has my = 1; dim 1 and 2 have mz = 1 (0 is accepted as 1).
+ *   - A space vector has m = mx*my*mz entries, index (l*my + j)*mx + i (x fastest).
  *   - A space-time vector has N = n*m entries, index k*m + j*mx + i, k = 0..n-1 for the time
  *     levels t_1..t_n (the stacked u = [u^(1); ...; u^(n)] of Sec. 1).
  *   - Pointers named *_dev are caller-owned device memory (float64, contiguous) on the device
@@ -51,7 +53,7 @@ extern "C" {
                          /* 3.1.1, after eq. matrix_Km_va)                                    */
 #define ST_PREC_PTHETA 1 /* P_theta = H (x) M + H_theta (x) tau K (eq. def:matrix_mod_P).     */
                          /* Constant a: spatial DST; 1D varying a: per-frequency tridiagonal  */
-                         /* solves by parallel cyclic reduction; 2D varying a: per-frequency  */
+                         /* solves by parallel cyclic reduction; 2D/3D varying a: per-freq.   */
                          /* fixed-degree Chebyshev iteration (st_problem.inner_degree steps)  */
                          /* preconditioned by the sine solve with a = mean face value.  The   */
                          /* paper leaves this solver open (Sec. 3.1.4, step 2).  The result   */
@@ -67,7 +69,7 @@ extern "C" {
                    /* refinement; stencil, Lanczos vectors, Givens rotations in float64       */
 
 typedef struct st_problem {
-  int dim;                /* 1 or 2                                                          */
+  int dim;                /* 1, 2 or 3                                                       */
   int mx, my;             /* interior points per axis, mx+1 and my+1 powers of two in         */
                           /* [4, 1024] (the spatial DST is a radix-2 FFT); my = 1 if dim = 1  */
   int n;                  /* time steps, 1 <= n <= 1024                                      */
@@ -75,14 +77,17 @@ typedef struct st_problem {
   int scheme;             /* ST_THETA or ST_BDF2                                             */
   double theta;           /* in [0,1] for ST_THETA, ignored for ST_BDF2                       */
   const double *a_nodal;  /* host, nodal a on the (my+2) x (mx+2) grid incl. boundary nodes  */
-                          /* ((mx+2) in 1D), a > 0; NULL means a = 1.  Copied by st_setup.    */
+                          /* ((mx+2) in 1D, (mz+2) x (my+2) x (mx+2) in 3D), a > 0; NULL     */
+                          /* means a = 1.  Copied by st_setup.                                */
   int prec;               /* ST_PREC_PH or ST_PREC_PTHETA                                    */
   int precision;          /* ST_FP64 or ST_MIXED                                             */
   void *stream;           /* cudaStream_t; NULL = the legacy default stream                  */
-  int inner_degree;       /* ST_PREC_PTHETA with 2D a_nodal: Chebyshev steps per apply in     */
+  int inner_degree;       /* ST_PREC_PTHETA with 2D/3D a_nodal: Chebyshev steps per apply in  */
                           /* [1, ST_PTHETA_MAX_DEGREE]; 0 = ST_PTHETA_DEFAULT_DEGREE; must be  */
                           /* 0 otherwise.  The map is symmetric positive definite at any     */
                           /* degree (its error polynomial stays below one on the spectrum).    */
+  int mz;                 /* dim 3: interior points along z, mz+1 a power of two in [4, 1024]; */
+                          /* otherwise 0 or 1.  n*mx*my*mz must stay below 2^31.              */
 } st_problem;
 
 typedef struct st_stats {
@@ -159,14 +164,14 @@ int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double 
  * dL/da = -tau sum_k lam_k^T (dK/da) (theta u_k + (1-theta) u_{k-1}) with u_0 = u0 (BDF2: u_k);
  * each face value is the mean of its two nodal values, so half of each face term goes to each
  * node.  lam_dev, u_dev: N; u0_dev: m; grad_dev: the nodal grid ((my+2)(mx+2), or mx+2 in 1D),
- * overwritten. */
+ * overwritten.  1D and 2D only: ST_ERR_ARG for a 3D handle. */
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev);
 
 /* Autotuner: times the candidate launch shapes of this handle's kernels on its own buffers
  * (CUDA events, `reps` launches each, 1..100) -- blocks per stencil launch, sequences per
  * spatial-DST block, column tile of the FFMA time kernel -- keeps the fastest, and caches the
- * choice per (dim, mx, my, n, precision, kernel path) for the process.  Synchronous; clobbers
+ * choice per (dim, mx, my, mz, n, precision, kernel path) for the process.  Synchronous; clobbers
  * the handle's workspace (call it between solves).  st_setup_batch runs it for every instance. */
 int st_autotune(st_handle *h, int reps);
 

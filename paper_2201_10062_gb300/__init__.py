@@ -41,6 +41,7 @@ class StProblem(ctypes.Structure):
         ("T", ctypes.c_double), ("scheme", ctypes.c_int), ("theta", ctypes.c_double),
         ("a_nodal", ctypes.POINTER(ctypes.c_double)), ("prec", ctypes.c_int),
         ("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("inner_degree", ctypes.c_int),
+        ("mz", ctypes.c_int),
     ]
 
 
@@ -158,11 +159,12 @@ class ProblemSpec:
     a_nodal: Optional[np.ndarray] = None
     prec: str = "PH"  # "PH" | "Ptheta"
     precision: str = "fp64"  # "fp64" | "mixed"
-    inner_degree: int = 0  # Ptheta with a 2D a_nodal: Chebyshev steps (0 = library default)
+    inner_degree: int = 0  # Ptheta with a 2D/3D a_nodal: Chebyshev steps (0 = library default)
+    mz: int = 1  # dim 3: interior points along z
 
     @property
     def m(self):
-        return self.mx * self.my
+        return self.mx * self.my * (self.mz if self.dim == 3 else 1)
 
     @property
     def N(self):
@@ -180,6 +182,7 @@ class ProblemSpec:
             a, ST_PREC_PH if self.prec == "PH" else ST_PREC_PTHETA,
             ST_FP64 if self.precision == "fp64" else ST_MIXED,
             ctypes.c_void_p(stream_ptr) if stream_ptr else None, int(self.inner_degree),
+            int(self.mz if self.dim == 3 else 1),
         )
         return p, keep
 

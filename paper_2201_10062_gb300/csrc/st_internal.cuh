@@ -9,25 +9,70 @@
 
 namespace st {
 
-// Geometry and coefficients of one problem, passed by value to kernels.
+// Geometry and coefficients of one problem, passed by value to kernels.  A space vector is
+// u[z][y][x] (x fastest); "rows" are the my*mz lines of x, row r = jz*my + jy.
 struct Geom {
   int dim, mx, my, n;
-  long long m, N;
+  long long m, N;       // m = mx*my*mz, N = n*m
   int scheme;           // ST_THETA / ST_BDF2
   double tau, theta;
-  const double *cx;     // [my][mx+1]  tau * a(x-face) / hx^2, faces i = 0..mx between nodes i-1, i
-  const double *cy;     // [my+1][mx]  tau * a(y-face) / hy^2 (NULL in 1D)
+  const double *cx;     // [mz*my][mx+1]  tau * a(x-face) / hx^2, faces i = 0..mx between nodes i-1, i
+  const double *cy;     // [mz][my+1][mx] tau * a(y-face) / hy^2 (NULL in 1D)
   const df *cxd, *cyd;  // the same coefficients as double-float pairs (mixed-precision stencil)
   df th_d, omth_d;      // theta and 1 - theta as double-float pairs
   int th_exact;         // theta in {0, 1/2, 1}: products with theta, 1 - theta are exact scalings
   int st_target;        // stencil launch: target number of blocks (0: default), set by autotune
+  int mz;               // interior points along z: 1 unless 3D
+  const double *cz;     // [mz+1][my][mx] tau * a(z-face) / hz^2 (NULL unless 3D)
+  const df *czd;
 };
+
+// The six face coefficients (tau a / h^2) around interior node (i, jy, jz): west/east along x,
+// south/north along y, down/up along z; zero along axes the grid does not have.
+template <class T>
+struct Faces6 {
+  T w, e, s, n, d, u;
+};
+
+__host__ __device__ inline Faces6<double> faces_at(const Geom &g, int i, int jy, int jz) {
+  const long long row = (long long)jz * g.my + jy;
+  Faces6<double> f{g.cx[row * (g.mx + 1) + i], g.cx[row * (g.mx + 1) + i + 1], 0.0, 0.0, 0.0, 0.0};
+  if (g.dim >= 2) {
+    const long long ys = ((long long)jz * (g.my + 1) + jy) * g.mx + i;
+    f.s = g.cy[ys];
+    f.n = g.cy[ys + g.mx];
+  }
+  if (g.dim == 3) {
+    const long long zs = row * g.mx + i;
+    f.d = g.cz[zs];
+    f.u = g.cz[zs + (long long)g.mx * g.my];
+  }
+  return f;
+}
+
+__host__ __device__ inline Faces6<df> faces_df_at(const Geom &g, int i, int jy, int jz) {
+  const long long row = (long long)jz * g.my + jy;
+  const df zero{0.f, 0.f};
+  Faces6<df> f{g.cxd[row * (g.mx + 1) + i], g.cxd[row * (g.mx + 1) + i + 1], zero, zero, zero,
+               zero};
+  if (g.dim >= 2) {
+    const long long ys = ((long long)jz * (g.my + 1) + jy) * g.mx + i;
+    f.s = g.cyd[ys];
+    f.n = g.cyd[ys + g.mx];
+  }
+  if (g.dim == 3) {
+    const long long zs = row * g.mx + i;
+    f.d = g.czd[zs];
+    f.u = g.czd[zs + (long long)g.mx * g.my];
+  }
+  return f;
+}
 
 // Spectral tables used by the preconditioner kernels.
 template <class T>
 struct Spec {
   const T *mux;    // [mx]  x-part of the (averaged) stiffness eigenvalue, times tau
-  const T *muy;    // [my]  y-part, times tau (zeros in 1D)
+  const T *muy;    // [mz*my] y- plus z-part, times tau, indexed by the row jz*my + jy (zeros in 1D)
   const T *hk;     // [n]   1 - cos(x_k), x_k = k pi/(n+1), k = 1..n (from 2 sin^2(x_k/2))
   const T *ck;     // [n]   cos(x_k)
   const T *sk;     // [n]   sin(x_k)
@@ -251,9 +296,9 @@ cudaError_t launch_grad_a(const Geom &g, const double *lam, const double *u, con
 
 // preconditioner pipeline: z = P^-1 v (v may be double, z double or float)
 struct PrecPlan {
-  int Lx, Ly;                 // FFT lengths 2(mx+1), 2(my+1)
-  const double *twx_d, *twy_d;  // e^{-2 pi i j/L}, j < L/2, interleaved (re, im)
-  const float *twx_f, *twy_f;
+  int Lx, Ly, Lz;             // FFT lengths 2(mx+1), 2(my+1), 2(mz+1)
+  const double *twx_d, *twy_d, *twz_d;  // e^{-2 pi i j/L}, j < L/2, interleaved (re, im)
+  const float *twx_f, *twy_f, *twz_f;
   Spec<double> spec_d;
   Spec<float> spec_f;
   int time_J_d, time_J_f;     // spatial columns per FFMA time-kernel block (0: default)
@@ -262,7 +307,8 @@ struct PrecPlan {
   const double *pcr_diag;     // P_theta 1D varying a: tau*K diagonal [mx]
   const double *pcr_off;      // tau*K off-diagonal [mx] (entry i couples i and i+1)
   const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
-  const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D mixed), or null
+  const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D/3D mixed), or null
+  const unsigned short *sop_z;  // fp16 S_mz image for the tensor-core z-DST (3D mixed), or null
   const unsigned short *sop_long;  // streamed S_n chunks for the tensor-core time kernel when
                                    // 256 < n <= 512 (mixed), or null
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
@@ -297,6 +343,8 @@ cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &s
                                 const unsigned short *A, State *S, int tmode, double *partials,
                                 int gk, cudaStream_t st);
 cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st);
+cudaError_t launch_dst_tc_z(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st);
 bool dst_tc_len_supported(int len);
 cudaError_t launch_time_tc_single(const float *in, float *out, const Geom &g,

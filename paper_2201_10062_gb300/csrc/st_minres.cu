@@ -250,11 +250,18 @@ bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_problem(const st_problem *p) {
   if (!p) return ST_ERR_ARG;
-  if (p->dim != 1 && p->dim != 2) return ST_ERR_ARG;
+  if (p->dim < 1 || p->dim > 3) return ST_ERR_ARG;
   if (p->mx < 3 || p->mx > 1023 || !pow2(p->mx + 1)) return ST_ERR_ARG;
   if (p->dim == 1 && p->my != 1) return ST_ERR_ARG;
-  if (p->dim == 2 && (p->my < 3 || p->my > 1023 || !pow2(p->my + 1))) return ST_ERR_ARG;
+  if (p->dim >= 2 && (p->my < 3 || p->my > 1023 || !pow2(p->my + 1))) return ST_ERR_ARG;
+  if (p->dim == 3 && (p->mz < 3 || p->mz > 1023 || !pow2(p->mz + 1))) return ST_ERR_ARG;
+  if (p->dim < 3 && p->mz != 0 && p->mz != 1) return ST_ERR_ARG;
   if (p->n < 1 || p->n > 1024) return ST_ERR_ARG;
+  {
+    // element indices of a space-time vector stay below 2^31 (32-bit index arithmetic)
+    const long long mz = (p->dim == 3) ? p->mz : 1;
+    if ((long long)p->n * p->mx * p->my * mz > 2147483647LL) return ST_ERR_ARG;
+  }
   if (!(p->T > 0.0) || !std::isfinite(p->T)) return ST_ERR_ARG;
   if (p->scheme != ST_THETA && p->scheme != ST_BDF2) return ST_ERR_ARG;
   if (p->scheme == ST_THETA && !(p->theta >= 0.0 && p->theta <= 1.0)) return ST_ERR_ARG;
@@ -262,12 +269,14 @@ int check_problem(const st_problem *p) {
   if (p->precision != ST_FP64 && p->precision != ST_MIXED) return ST_ERR_ARG;
   if (p->prec == ST_PREC_PTHETA && p->scheme != ST_THETA) return ST_ERR_ARG;
   {
-    const bool cheb = p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr && p->dim == 2;
+    const bool cheb = p->prec == ST_PREC_PTHETA && p->a_nodal != nullptr && p->dim >= 2;
     if (p->inner_degree < 0 || p->inner_degree > ST_PTHETA_MAX_DEGREE) return ST_ERR_ARG;
     if (!cheb && p->inner_degree != 0) return ST_ERR_ARG;
   }
   if (p->a_nodal) {
-    const long long cnt = (p->dim == 1) ? (p->mx + 2) : (long long)(p->mx + 2) * (p->my + 2);
+    const long long cnt = (p->dim == 1)   ? (p->mx + 2)
+                          : (p->dim == 2) ? (long long)(p->mx + 2) * (p->my + 2)
+                                          : (long long)(p->mx + 2) * (p->my + 2) * (p->mz + 2);
     for (long long i = 0; i < cnt; ++i)
       if (!(p->a_nodal[i] > 0.0) || !std::isfinite(p->a_nodal[i])) return ST_ERR_ARG;
   }
@@ -309,8 +318,9 @@ Geom geom_of(const st_problem *p) {
   g.dim = p->dim;
   g.mx = p->mx;
   g.my = (p->dim == 1) ? 1 : p->my;
+  g.mz = (p->dim == 3) ? p->mz : 1;
   g.n = p->n;
-  g.m = (long long)g.mx * g.my;
+  g.m = (long long)g.mx * g.my * g.mz;
   g.N = g.m * g.n;
   g.scheme = p->scheme;
   g.tau = p->T / p->n;
@@ -318,21 +328,28 @@ Geom geom_of(const st_problem *p) {
   return g;
 }
 
+// face coefficients along x, y and z (the last two zero-length where the axis is absent)
+size_t faces_x(const Geom &g) { return (size_t)g.mz * g.my * (g.mx + 1); }
+size_t faces_y(const Geom &g) { return g.dim >= 2 ? (size_t)g.mz * (g.my + 1) * g.mx : 0; }
+size_t faces_z(const Geom &g) { return g.dim == 3 ? (size_t)(g.mz + 1) * g.my * g.mx : 0; }
+
 size_t table_doubles(const Geom &g) {
-  const size_t faces = (size_t)g.my * (g.mx + 1) + (g.dim == 2 ? (size_t)(g.my + 1) * g.mx : 0);
-  const size_t spec = (size_t)g.mx + g.my + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
-  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2;  // L/2 complex per axis
+  const size_t faces = faces_x(g) + faces_y(g) + faces_z(g);
+  const size_t spec = (size_t)g.mx + (size_t)g.my * g.mz + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
+  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2 +
+                    (g.dim == 3 ? (size_t)(g.mz + 1) * 2 : 0);  // L/2 complex per axis
   return faces + spec + tw;
 }
 size_t table_floats(const Geom &g) {
-  const size_t spec = (size_t)g.mx + g.my + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
-  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2;
+  const size_t spec = (size_t)g.mx + (size_t)g.my * g.mz + 5 * (size_t)g.n + 2 * (size_t)(g.n + 1);
+  const size_t tw = (size_t)(g.mx + 1) * 2 + (size_t)(g.my + 1) * 2 +
+                    (g.dim == 3 ? (size_t)(g.mz + 1) * 2 : 0);
   return spec + tw;
 }
 
 // Chebyshev steps of the 2D varying-a P_theta, 0 for every other preconditioner
 int cheb_degree(const st_problem *p) {
-  if (p->prec != ST_PREC_PTHETA || p->a_nodal == nullptr || p->dim != 2) return 0;
+  if (p->prec != ST_PREC_PTHETA || p->a_nodal == nullptr || p->dim < 2) return 0;
   return p->inner_degree > 0 ? p->inner_degree : ST_PTHETA_DEFAULT_DEGREE;
 }
 
@@ -354,11 +371,13 @@ size_t workspace_bytes(const Geom &g, bool mixed, int cheb) {
   b += sizeof(State);
   b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(double);  // grad faces
   b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
-  b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(df) + 256;  // df faces
+  b += (faces_x(g) + faces_y(g) + faces_z(g)) * sizeof(df) + 256;  // df faces
   if (mixed && time_tc_supported(g.n)) b += time_tc_sop_halves(g.n) * 2;
   if (mixed && !time_tc_supported(g.n) && time_tc_long_supported(g.n))
     b += time_tc_long_bytes(g.n) + 256;
-  if (mixed && g.dim == 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
+  if (mixed && g.dim >= 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
+  if (mixed && g.dim == 3 && dst_tc_supported(g.mz)) b += time_tc_sop_halves(g.mz) * 2 + 256;
+  b += 256;  // alignment of the z image
   return b;
 }
 
@@ -366,25 +385,39 @@ size_t workspace_bytes(const Geom &g, bool mixed, int cheb) {
 int build_tables(st_handle *h) {
   const Geom &g = h->g;
   const st_problem &p = h->prob;
-  const int mx = g.mx, my = g.my, n = g.n;
+  const int mx = g.mx, my = g.my, mz = g.mz, n = g.n;
   const double tau = g.tau;
-  const double hx = 1.0 / (mx + 1), hy = (g.dim == 2) ? 1.0 / (my + 1) : 1.0;
+  const double hx = 1.0 / (mx + 1), hy = (g.dim >= 2) ? 1.0 / (my + 1) : 1.0;
+  const double hz = (g.dim == 3) ? 1.0 / (mz + 1) : 1.0;
   const double *A = p.a_nodal;
-  auto anode = [&](int J, int I) -> double {
+  // nodal a at node (K, J, I) of the grid with boundary nodes (K ignored below 3D, J in 1D)
+  auto anode = [&](int K, int J, int I) -> double {
     if (!A) return 1.0;
-    return (g.dim == 1) ? A[I] : A[(long long)J * (mx + 2) + I];
+    if (g.dim == 1) return A[I];
+    if (g.dim == 2) return A[(long long)J * (mx + 2) + I];
+    return A[((long long)K * (my + 2) + J) * (mx + 2) + I];
   };
-  const size_t nfx = (size_t)my * (mx + 1), nfy = (g.dim == 2) ? (size_t)(my + 1) * mx : 0;
-  std::vector<double> cx(nfx), cy(nfy);
-  for (int j = 0; j < my; ++j)
-    for (int i = 0; i <= mx; ++i)
-      cx[(size_t)j * (mx + 1) + i] = tau * 0.5 * (anode(j + 1, i) + anode(j + 1, i + 1)) / (hx * hx);
-  for (size_t j = 0; j < (g.dim == 2 ? (size_t)my + 1 : 0); ++j)
-    for (int i = 0; i < mx; ++i)
-      cy[j * mx + i] = tau * 0.5 * (anode((int)j, i + 1) + anode((int)j + 1, i + 1)) / (hy * hy);
-  // diagonal-averaged stiffness matrix (times tau): mean diagonal, mean x- and y-couplings.
-  // The small eigenvalues d - 2 e_x cos - 2 e_y cos cancel strongly, so the sums are compensated
-  // (Neumaier) to keep their own rounding at the level of one ulp.
+  std::vector<double> cx(faces_x(g)), cy(faces_y(g)), cz(faces_z(g));
+  for (int jz = 0; jz < mz; ++jz)
+    for (int j = 0; j < my; ++j)
+      for (int i = 0; i <= mx; ++i)
+        cx[((size_t)jz * my + j) * (mx + 1) + i] =
+            tau * 0.5 * (anode(jz + 1, j + 1, i) + anode(jz + 1, j + 1, i + 1)) / (hx * hx);
+  if (g.dim >= 2)
+    for (int jz = 0; jz < mz; ++jz)
+      for (int j = 0; j <= my; ++j)
+        for (int i = 0; i < mx; ++i)
+          cy[((size_t)jz * (my + 1) + j) * mx + i] =
+              tau * 0.5 * (anode(jz + 1, j, i + 1) + anode(jz + 1, j + 1, i + 1)) / (hy * hy);
+  if (g.dim == 3)
+    for (int k = 0; k <= mz; ++k)
+      for (int j = 0; j < my; ++j)
+        for (int i = 0; i < mx; ++i)
+          cz[((size_t)k * my + j) * mx + i] =
+              tau * 0.5 * (anode(k, j + 1, i + 1) + anode(k + 1, j + 1, i + 1)) / (hz * hz);
+  // diagonal-averaged stiffness matrix (times tau): mean diagonal, mean x-, y- and z-couplings.
+  // The small eigenvalues d - 2 e_x cos - 2 e_y cos - 2 e_z cos cancel strongly, so the sums are
+  // compensated (Neumaier) to keep their own rounding at the level of one ulp.
   struct CSum {
     double s = 0.0, c = 0.0;
     void add(double x) {
@@ -395,35 +428,56 @@ int build_tables(st_handle *h) {
     double get() const { return s + c; }
   };
   CSum dsum;
-  for (int j = 0; j < my; ++j)
-    for (int i = 0; i < mx; ++i) {
-      dsum.add(cx[(size_t)j * (mx + 1) + i]);
-      dsum.add(cx[(size_t)j * (mx + 1) + i + 1]);
-      if (g.dim == 2) {
-        dsum.add(cy[(size_t)j * mx + i]);
-        dsum.add(cy[(size_t)(j + 1) * mx + i]);
+  for (int jz = 0; jz < mz; ++jz)
+    for (int j = 0; j < my; ++j)
+      for (int i = 0; i < mx; ++i) {
+        const size_t row = (size_t)jz * my + j;
+        dsum.add(cx[row * (mx + 1) + i]);
+        dsum.add(cx[row * (mx + 1) + i + 1]);
+        if (g.dim >= 2) {
+          const size_t ys = ((size_t)jz * (my + 1) + j) * mx + i;
+          dsum.add(cy[ys]);
+          dsum.add(cy[ys + mx]);
+        }
+        if (g.dim == 3) {
+          dsum.add(cz[row * mx + i]);
+          dsum.add(cz[row * mx + i + (size_t)mx * my]);
+        }
       }
-    }
   const double dbar = dsum.get() / (double)g.m;
-  double ex = 0.0, ey = 0.0;
+  double ex = 0.0, ey = 0.0, ez = 0.0;
   if (mx > 1) {
     CSum sx;
-    for (int j = 0; j < my; ++j)
-      for (int i = 1; i < mx; ++i) sx.add(cx[(size_t)j * (mx + 1) + i]);
-    ex = sx.get() / ((double)my * (mx - 1));
+    for (int r = 0; r < my * mz; ++r)
+      for (int i = 1; i < mx; ++i) sx.add(cx[(size_t)r * (mx + 1) + i]);
+    ex = sx.get() / ((double)my * mz * (mx - 1));
   }
-  if (g.dim == 2 && my > 1) {
+  if (g.dim >= 2 && my > 1) {
     CSum sy;
-    for (int j = 1; j < my; ++j)
-      for (int i = 0; i < mx; ++i) sy.add(cy[(size_t)j * mx + i]);
-    ey = sy.get() / ((double)(my - 1) * mx);
+    for (int jz = 0; jz < mz; ++jz)
+      for (int j = 1; j < my; ++j)
+        for (int i = 0; i < mx; ++i) sy.add(cy[((size_t)jz * (my + 1) + j) * mx + i]);
+    ey = sy.get() / ((double)mz * (my - 1) * mx);
+  }
+  if (g.dim == 3 && mz > 1) {
+    CSum sz;
+    for (int k = 1; k < mz; ++k)
+      for (int j = 0; j < my; ++j)
+        for (int i = 0; i < mx; ++i) sz.add(cz[((size_t)k * my + j) * mx + i]);
+    ez = sz.get() / ((double)(mz - 1) * my * mx);
   }
   const double PI = 3.14159265358979323846;
-  std::vector<double> mux(mx), muy(my), hk(n), ck(n), sk(n), lh(n), lht(n), sintab(2 * (n + 1));
+  // muy holds the y- and z-parts together, indexed by the row jz*my + jy
+  std::vector<double> mux(mx), muy((size_t)my * mz), hk(n), ck(n), sk(n), lh(n), lht(n),
+      sintab(2 * (n + 1));
   for (int i = 0; i < mx; ++i) mux[i] = dbar - 2.0 * ex * std::cos((i + 1) * PI / (mx + 1));
-  for (int j = 0; j < my; ++j)
-    muy[j] = (g.dim == 2) ? -2.0 * ey * std::cos((j + 1) * PI / (my + 1)) : 0.0;
-  // P_theta with a varying 2D coefficient: the Chebyshev inner map is preconditioned by the
+  for (int jz = 0; jz < mz; ++jz)
+    for (int j = 0; j < my; ++j) {
+      double v = (g.dim >= 2) ? -2.0 * ey * std::cos((j + 1) * PI / (my + 1)) : 0.0;
+      if (g.dim == 3) v += -2.0 * ez * std::cos((jz + 1) * PI / (mz + 1));
+      muy[(size_t)jz * my + j] = v;
+    }
+  // P_theta with a varying 2D/3D coefficient: the Chebyshev inner map is preconditioned by the
   // a = abar operator, so the spatial tables hold tau abar times the eigenvalues of K0 (a = 1),
   // 4 sin^2(i pi / (2(mx+1))) / hx^2 per axis, instead of the averaged K
   const int cheb = cheb_degree(&p);
@@ -437,18 +491,33 @@ int build_tables(st_handle *h) {
       f_min = std::min(f_min, a);
       f_max = std::max(f_max, a);
     };
-    for (int j = 0; j < my; ++j)
-      for (int i = 0; i <= mx; ++i) face(0.5 * (anode(j + 1, i) + anode(j + 1, i + 1)));
-    for (int j = 0; j <= my; ++j)
-      for (int i = 0; i < mx; ++i) face(0.5 * (anode(j, i + 1) + anode(j + 1, i + 1)));
-    f_bar = fs.get() / (double)(nfx + nfy);
+    for (int jz = 0; jz < mz; ++jz)
+      for (int j = 0; j < my; ++j)
+        for (int i = 0; i <= mx; ++i)
+          face(0.5 * (anode(jz + 1, j + 1, i) + anode(jz + 1, j + 1, i + 1)));
+    for (int jz = 0; jz < mz; ++jz)
+      for (int j = 0; j <= my; ++j)
+        for (int i = 0; i < mx; ++i)
+          face(0.5 * (anode(jz + 1, j, i + 1) + anode(jz + 1, j + 1, i + 1)));
+    if (g.dim == 3)
+      for (int k = 0; k <= mz; ++k)
+        for (int j = 0; j < my; ++j)
+          for (int i = 0; i < mx; ++i)
+            face(0.5 * (anode(k, j + 1, i + 1) + anode(k + 1, j + 1, i + 1)));
+    f_bar = fs.get() / (double)(faces_x(g) + faces_y(g) + faces_z(g));
     auto mu0 = [&](int i, int len, double h2) {
       const double sv = std::sin((i + 1) * PI / (2.0 * (len + 1)));
       return 4.0 * sv * sv / h2;
     };
     for (int i = 0; i < mx; ++i) mux[i] = tau * f_bar * mu0(i, mx, hx * hx);
-    for (int j = 0; j < my; ++j) muy[j] = tau * f_bar * mu0(j, my, hy * hy);
+    for (int jz = 0; jz < mz; ++jz)
+      for (int j = 0; j < my; ++j) {
+        double mu = mu0(j, my, hy * hy);
+        if (g.dim == 3) mu += mu0(jz, mz, hz * hz);
+        muy[(size_t)jz * my + j] = tau * f_bar * mu;
+      }
     mu0_max = mu0(mx - 1, mx, hx * hx) + mu0(my - 1, my, hy * hy);
+    if (g.dim == 3) mu0_max += mu0(mz - 1, mz, hz * hz);
   }
   const double th = g.theta;
   for (int k = 1; k <= n; ++k) {
@@ -493,8 +562,8 @@ int build_tables(st_handle *h) {
       cheb_s[(size_t)j * n + k] = sj;
     }
   }
-  const int Lx = 2 * (mx + 1), Ly = 2 * (my + 1);
-  std::vector<double> twx(Lx), twy(Ly);
+  const int Lx = 2 * (mx + 1), Ly = 2 * (my + 1), Lz = 2 * (mz + 1);
+  std::vector<double> twx(Lx), twy(Ly), twz(g.dim == 3 ? Lz : 0);
   for (int j = 0; j < Lx / 2; ++j) {
     twx[2 * j] = std::cos(2.0 * PI * j / Lx);
     twx[2 * j + 1] = -std::sin(2.0 * PI * j / Lx);
@@ -503,7 +572,12 @@ int build_tables(st_handle *h) {
     twy[2 * j] = std::cos(2.0 * PI * j / Ly);
     twy[2 * j + 1] = -std::sin(2.0 * PI * j / Ly);
   }
-  // layout: doubles [cx cy mux muy hk ck sk lh lht sintab twx twy] then floats [mux ... twy]
+  for (size_t j = 0; j < twz.size() / 2; ++j) {
+    twz[2 * j] = std::cos(2.0 * PI * (double)j / Lz);
+    twz[2 * j + 1] = -std::sin(2.0 * PI * (double)j / Lz);
+  }
+  // layout: doubles [cx cy cz mux muy hk ck sk lh lht sintab twx twy twz] then floats
+  // [mux ... twz]
   std::vector<double> hd;
   hd.reserve(table_doubles(g));
   auto app = [&](const std::vector<double> &v) {
@@ -511,10 +585,10 @@ int build_tables(st_handle *h) {
     hd.insert(hd.end(), v.begin(), v.end());
     return off;
   };
-  const size_t o_cx = app(cx), o_cy = app(cy);
+  const size_t o_cx = app(cx), o_cy = app(cy), o_cz = app(cz);
   const size_t o_mux = app(mux), o_muy = app(muy), o_hk = app(hk), o_ck = app(ck), o_sk = app(sk),
                o_lh = app(lh), o_lht = app(lht), o_sin = app(sintab), o_twx = app(twx),
-               o_twy = app(twy);
+               o_twy = app(twy), o_twz = app(twz);
   const size_t nd = hd.size();
   std::vector<float> hf(nd - o_mux);
   for (size_t i = o_mux; i < nd; ++i) hf[i - o_mux] = (float)hd[i];
@@ -536,19 +610,26 @@ int build_tables(st_handle *h) {
   }
   const size_t o_sop = (bytes_d + bytes_f + 255) / 256 * 256;
   // double-float copies of the face coefficients
-  std::vector<df> cdf(cx.size() + cy.size());
+  std::vector<df> cdf(cx.size() + cy.size() + cz.size());
   for (size_t i = 0; i < cx.size(); ++i) cdf[i] = df_of_double(cx[i]);
   for (size_t i = 0; i < cy.size(); ++i) cdf[cx.size() + i] = df_of_double(cy[i]);
+  for (size_t i = 0; i < cz.size(); ++i) cdf[cx.size() + cy.size() + i] = df_of_double(cz[i]);
   const size_t o_cdf = (o_sop + sop.size() * sizeof(unsigned short) + 255) / 256 * 256;
-  // fp16 S_my image for the tensor-core y-DST (2D, mixed precision, supported my)
-  std::vector<unsigned short> sopy;
-  if (p.precision == ST_MIXED && g.dim == 2 && dst_tc_supported(g.my) &&
+  // fp16 S_my / S_mz images for the tensor-core y- and z-DSTs (mixed precision, supported lengths)
+  std::vector<unsigned short> sopy, sopz;
+  if (p.precision == ST_MIXED && g.dim >= 2 && dst_tc_supported(g.my) &&
       !(no_tc && no_tc[0] == '1')) {
     sopy.resize(time_tc_sop_halves(g.my));
     time_tc_build_sop(g.my, sopy.data());
   }
+  if (p.precision == ST_MIXED && g.dim == 3 && dst_tc_supported(g.mz) &&
+      !(no_tc && no_tc[0] == '1')) {
+    sopz.resize(time_tc_sop_halves(g.mz));
+    time_tc_build_sop(g.mz, sopz.data());
+  }
   const size_t o_sopy = (o_cdf + cdf.size() * sizeof(df) + 255) / 256 * 256;
-  const size_t bytes = o_sopy + sopy.size() * sizeof(unsigned short);
+  const size_t o_sopz = (o_sopy + sopy.size() * sizeof(unsigned short) + 255) / 256 * 256;
+  const size_t bytes = o_sopz + sopz.size() * sizeof(unsigned short);
   ST_TRY(cudaMalloc(&h->tables, bytes));
   ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice));
@@ -560,13 +641,18 @@ int build_tables(st_handle *h) {
   if (!sopy.empty())
     ST_TRY(cudaMemcpy((char *)h->tables + o_sopy, sopy.data(),
                       sopy.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+  if (!sopz.empty())
+    ST_TRY(cudaMemcpy((char *)h->tables + o_sopz, sopz.data(),
+                      sopz.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
   const double *D = (const double *)h->tables;
   const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
   h->g.cx = D + o_cx;
-  h->g.cy = (g.dim == 2) ? D + o_cy : nullptr;
+  h->g.cy = (g.dim >= 2) ? D + o_cy : nullptr;
+  h->g.cz = (g.dim == 3) ? D + o_cz : nullptr;
   const df *CD = reinterpret_cast<const df *>((const char *)h->tables + o_cdf);
   h->g.cxd = CD;
-  h->g.cyd = (g.dim == 2) ? CD + cx.size() : nullptr;
+  h->g.cyd = (g.dim >= 2) ? CD + cx.size() : nullptr;
+  h->g.czd = (g.dim == 3) ? CD + cx.size() + cy.size() : nullptr;
   h->g.th_d = df_of_double(h->g.theta);
   h->g.omth_d = df_of_double(1.0 - h->g.theta);
   h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
@@ -607,12 +693,17 @@ int build_tables(st_handle *h) {
   pp.sop_long = long_tc ? sop_img : nullptr;
   pp.sop_y = sopy.empty() ? nullptr
                           : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopy);
+  pp.sop_z = sopz.empty() ? nullptr
+                          : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopz);
   pp.Lx = Lx;
   pp.Ly = Ly;
+  pp.Lz = Lz;
   pp.twx_d = D + o_twx;
   pp.twy_d = D + o_twy;
+  pp.twz_d = D + o_twz;
   pp.twx_f = F + o_twx;
   pp.twy_f = F + o_twy;
+  pp.twz_f = F + o_twz;
   pp.spec_d = Spec<double>{D + o_mux, D + o_muy, D + o_hk, D + o_ck, D + o_sk, D + o_lh, D + o_lht,
                            D + o_sin, p.prec, p.scheme, th};
   pp.spec_f = Spec<float>{F + o_mux, F + o_muy, F + o_hk, F + o_ck, F + o_sk, F + o_lh, F + o_lht,
@@ -1002,14 +1093,14 @@ struct Knobs {
   int st_target, dst_shift, jd, jf;
 };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, Knobs> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int>, Knobs> g_tune_cache;
 }  // namespace
 
 int st_autotune(st_handle *h, int reps) {
   if (!h || reps < 1 || reps > 100) return ST_ERR_ARG;
   ST_TRY(cudaSetDevice(h->device));
   const bool fp32 = h->mixed;
-  const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.n, (int)fp32,
+  const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.mz, h->g.n, (int)fp32,
                                    (h->pp.sop ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
                                        (h->pp.cheb ? 4 : 0));
   {
@@ -1316,6 +1407,7 @@ int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double 
 int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const double *u0_dev,
               double *grad_dev) {
   if (!h || !lam_dev || !u_dev || !u0_dev || !grad_dev) return ST_ERR_ARG;
+  if (h->g.dim == 3) return ST_ERR_ARG;  // the face gradient is written for 1D and 2D grids
   ProfScope prof_scope(h);
   ST_TRY(cudaSetDevice(h->device));
   ST_TRY(launch_grad_a(h->g, lam_dev, u_dev, u0_dev, h->gfx, h->gfy, grad_dev, h->stream));

@@ -449,8 +449,8 @@ __device__ __forceinline__ float face_c<float>(const double *, const df *cd, lon
 }
 
 // d_j = a_k d_{j-1} + w into dnext (its own buffer: the stencil reads neighbours of d_{j-1}),
-// x = x + d_j (x = d_j when first), r = rsrc - A_k d_j with tau K the 5-point stencil of the face
-// coefficients cx, cy (tau a / h^2).  r may alias rsrc.
+// x = x + d_j (x = d_j when first), r = rsrc - A_k d_j with tau K the 5-point (2D) or 7-point
+// (3D) stencil of the face coefficients cx, cy, cz (tau a / h^2).  r may alias rsrc.
 template <class Tc>
 __global__ void __launch_bounds__(kNT)
     k_cheb_resid(Geom g, const Tc *__restrict__ dprev, const Tc *__restrict__ w,
@@ -458,24 +458,33 @@ __global__ void __launch_bounds__(kNT)
                  const Tc *__restrict__ acoef, const Tc *__restrict__ lh,
                  const Tc *__restrict__ lht, int first, const State *S, int gk) {
   if (gate_closed(S, gk)) return;
-  const int mx = g.mx, my = g.my;
-  const long long m = g.m;
+  const int mx = g.mx, my = g.my, mz = g.mz;
+  const long long m = g.m, pl = (long long)mx * my;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.N;
        e += (long long)gridDim.x * blockDim.x) {
     const unsigned ue = (unsigned)e;
     const unsigned k = ue / (unsigned)m, rr = ue - k * (unsigned)m;
-    const int jy = (int)(rr / (unsigned)mx), ix = (int)(rr - (unsigned)jy * mx);
+    const int row = (int)(rr / (unsigned)mx), ix = (int)(rr - (unsigned)row * mx);
+    const int jz = row / my, jy = row - jz * my;
     const Tc ak = first ? Tc(0) : acoef[k];
     auto dv = [&](long long q) -> Tc { return first ? w[q] : ak * dprev[q] + w[q]; };
     const Tc dc = dv(e);
-    const long long fx = (long long)jy * (mx + 1) + ix, fy = (long long)jy * mx + ix;
+    const long long fx = (long long)row * (mx + 1) + ix;
+    const long long fy = ((long long)jz * (my + 1) + jy) * mx + ix;
     const Tc cw = face_c<Tc>(g.cx, g.cxd, fx), ce = face_c<Tc>(g.cx, g.cxd, fx + 1);
     const Tc cs = face_c<Tc>(g.cy, g.cyd, fy), cn = face_c<Tc>(g.cy, g.cyd, fy + mx);
-    Tc kd = (cw + ce + cs + cn) * dc;
+    Tc cd = Tc(0), cu = Tc(0);
+    if (g.dim == 3) {
+      cd = face_c<Tc>(g.cz, g.czd, (long long)row * mx + ix);
+      cu = face_c<Tc>(g.cz, g.czd, (long long)row * mx + ix + pl);
+    }
+    Tc kd = (cw + ce + cs + cn + cd + cu) * dc;
     if (ix > 0) kd -= cw * dv(e - 1);
     if (ix < mx - 1) kd -= ce * dv(e + 1);
     if (jy > 0) kd -= cs * dv(e - mx);
     if (jy < my - 1) kd -= cn * dv(e + mx);
+    if (jz > 0) kd -= cd * dv(e - pl);
+    if (jz < mz - 1) kd -= cu * dv(e + pl);
     r[e] = rsrc[e] - (lh[k] * dc + lht[k] * kd);
     x[e] = first ? dc : x[e] + dc;
     dnext[e] = dc;
@@ -697,6 +706,40 @@ const float *cheb_s_of<float>(const PrecPlan &pp) {
 
 constexpr int kChebBlocks = 152 * 8;
 
+// Spatial DST-I along y (lines mx apart, planes of mx*my, n*mz of them) or z (lines mx*my apart,
+// planes of m, n of them), from src into out: the tensor cores in float32 when the plan has the
+// S_len image, else the shared-memory FFT.  Tensor-core passes work in place (src must be out).
+template <class Tc, class Src>
+cudaError_t dst_y_pass(Src src, Tc *out, const Geom &g, const PrecPlan &pp, State *S, int gk,
+                       cudaStream_t st) {
+  if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
+    return launch_dst_tc_y(reinterpret_cast<float *>(out), g, pp.sop_y, S, gk, st);
+  const long long ny = (long long)g.n * g.mz * g.mx;
+  return launch_dst<Tc, Src, Tc, false>(src, out, g.my, pp.Ly, ny, g.mx, (long long)g.mx * g.my,
+                                        tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
+}
+
+template <class Tc>
+static const Tc *twz_of(const PrecPlan &pp);
+template <>
+const double *twz_of<double>(const PrecPlan &pp) {
+  return pp.twz_d;
+}
+template <>
+const float *twz_of<float>(const PrecPlan &pp) {
+  return pp.twz_f;
+}
+
+template <class Tc, class Src>
+cudaError_t dst_z_pass(Src src, Tc *out, const Geom &g, const PrecPlan &pp, State *S, int gk,
+                       cudaStream_t st) {
+  if (sizeof(Tc) == sizeof(float) && pp.sop_z != nullptr)
+    return launch_dst_tc_z(reinterpret_cast<float *>(out), g, pp.sop_z, S, gk, st);
+  const long long nz = (long long)g.n * g.mx * g.my;
+  return launch_dst<Tc, Src, Tc, false>(src, out, g.mz, pp.Lz, nz, g.mx * g.my, g.m,
+                                        twz_of<Tc>(pp), S, gk, pp.dst_shift, st);
+}
+
 // The time DST alone (the P_theta paths with varying a): tensor cores in float32 when the plan has
 // the S_n image, else the FFMA/DFMA kernel.
 // in -> out (the same array, or one that does not overlap).
@@ -724,14 +767,14 @@ cudaError_t cheb_stages(const Geom &g, const PrecPlan &pp, Src src, Tc *zc, Stat
   Tc *Dd[2] = {R + 3 * N, R + 4 * N};
   const Tc *acoef = cheb_a_of<Tc>(pp), *scoef = cheb_s_of<Tc>(pp);
   const int Jo = sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d;
-  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
-  const Tc *twx = tw_of<Tc>(pp, true), *twy = tw_of<Tc>(pp, false);
+  const long long nx = (long long)g.n * g.my * g.mz;
+  const Tc *twx = tw_of<Tc>(pp, true);
   cudaError_t e;
-  auto y_pass = [&](Tc *a) -> cudaError_t {
-    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
-      return launch_dst_tc_y(reinterpret_cast<float *>(a), g, pp.sop_y, S, gk, st);
-    return launch_dst<Tc, Arr, Tc, false>(Arr{a}, a, g.my, pp.Ly, ny, g.mx, g.m, twy, S, gk,
-                                          pp.dst_shift, st);
+  // the y (and z) passes of one half of the spatial transform, in place
+  auto yz_pass = [&](Tc *a) -> cudaError_t {
+    cudaError_t r = dst_y_pass<Tc>(Arr{a}, a, g, pp, S, gk, st);
+    if (r == cudaSuccess && g.dim == 3) r = dst_z_pass<Tc>(Arr{a}, a, g, pp, S, gk, st);
+    return r;
   };
   prof_begin(KC_AUX, st);
   k_copy_to<Tc, Src><<<kChebBlocks, kNT, 0, st>>>(N, src, zc, S, gk);
@@ -741,18 +784,18 @@ cudaError_t cheb_stages(const Geom &g, const PrecPlan &pp, Src src, Tc *zc, Stat
   if (e != cudaSuccess) return e;
   int cur = 0;
   for (int j = 0; j < pp.cheb; ++j) {
-    // the two axes commute: x, y, then x with the scaling fused into its loads, then y; the
-    // y passes take the tensor cores in float32 when the plan has the S_my image
+    // the axes commute: x, y (z), then x with the scaling fused into its loads, then y (z); the
+    // y and z passes take the tensor cores in float32 when the plan has the S_my / S_mz image
     e = launch_dst<Tc, Arr, Tc, true>(Arr{j == 0 ? zc : R}, W, g.mx, pp.Lx, nx, g.mx, g.m, twx, S,
                                       gk, pp.dst_shift, st);
     if (e != cudaSuccess) return e;
-    if ((e = y_pass(W)) != cudaSuccess) return e;
+    if ((e = yz_pass(W)) != cudaSuccess) return e;
     const SrcChebScale<Tc> sc{W, scoef + (size_t)j * g.n, sp.lh, sp.lht, sp.mux, sp.muy,
                               (unsigned)g.m, (unsigned)g.mx};
     e = launch_dst<Tc, SrcChebScale<Tc>, Tc, true>(sc, W, g.mx, pp.Lx, nx, g.mx, g.m, twx, S, gk,
                                                    pp.dst_shift, st);
     if (e != cudaSuccess) return e;
-    if ((e = y_pass(W)) != cudaSuccess) return e;
+    if ((e = yz_pass(W)) != cudaSuccess) return e;
     const Tc *aj = acoef + (size_t)j * g.n;
     if (j + 1 < pp.cheb) {
       prof_begin(KC_TIME, st);
@@ -806,18 +849,13 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
     if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
     return time_single<Tc>(zc, zc, g, pp, S, partials, gk, Jo, st);
   }
-  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
+  const long long nx = (long long)g.n * g.my * g.mz;
+  Tc *zt = reinterpret_cast<Tc *>(z);
   e = launch_dst<Tc, Src, Tout, true>(src, z, g.mx, pp.Lx, nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
                                       gk, pp.dst_shift, st);
   if (e != cudaSuccess) return e;
-  if (g.dim == 2) {
-    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
-      e = launch_dst_tc_y(reinterpret_cast<float *>(z), g, pp.sop_y, S, gk, st);
-    else
-      e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
-                                             tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
-    if (e != cudaSuccess) return e;
-  }
+  if (g.dim >= 2 && (e = dst_y_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
+  if (g.dim == 3 && (e = dst_z_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
   if (sizeof(Tc) == sizeof(float) && pp.sop != nullptr)
     e = launch_time_tc(reinterpret_cast<float *>(z), g, pp.spec_f, pp.sop, S, tmode, partials, gk,
                        st);
@@ -829,14 +867,8 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
                         sizeof(Tc) == sizeof(float) ? pp.time_J_f : pp.time_J_d, st);
   if (e != cudaSuccess) return e;
   if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
-  if (g.dim == 2) {
-    if (sizeof(Tc) == sizeof(float) && pp.sop_y != nullptr)
-      e = launch_dst_tc_y(reinterpret_cast<float *>(z), g, pp.sop_y, S, gk, st);
-    else
-      e = launch_dst<Tc, Inner, Tout, false>(Inner{z}, z, g.my, pp.Ly, ny, g.mx, g.m,
-                                             tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
-    if (e != cudaSuccess) return e;
-  }
+  if (g.dim == 3 && (e = dst_z_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
+  if (g.dim >= 2 && (e = dst_y_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
   return launch_dst<Tc, Inner, Tout, true>(Inner{z}, z, g.mx, pp.Lx, nx, g.mx, g.m,
                                            tw_of<Tc>(pp, true), S, gk, pp.dst_shift, st);
 }
@@ -864,24 +896,33 @@ cudaError_t launch_prec_lanczos(const Geom &g, const PrecPlan &pp, const Tin *q,
 // ungated, with the knobs currently in pp.
 cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
                           cudaStream_t st) {
-  const long long nx = (long long)g.n * g.my, ny = (long long)g.n * g.mx;
+  const long long nx = (long long)g.n * g.my * g.mz, ny = (long long)g.n * g.mz * g.mx;
+  const long long nz = (long long)g.n * g.mx * g.my;
   cudaError_t e;
   if (fp32) {
     float *z = (float *)data;
     using A = SrcArray<float, float>;
     e = launch_dst<float, A, float, true>(A{z}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_f, nullptr,
                                           GK_NONE, pp.dst_shift, st);
-    if (e == cudaSuccess && g.dim == 2)
-      e = launch_dst<float, A, float, false>(A{z}, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_f,
-                                             nullptr, GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim >= 2)
+      e = launch_dst<float, A, float, false>(A{z}, z, g.my, pp.Ly, ny, g.mx,
+                                             (long long)g.mx * g.my, pp.twy_f, nullptr, GK_NONE,
+                                             pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim == 3)
+      e = launch_dst<float, A, float, false>(A{z}, z, g.mz, pp.Lz, nz, g.mx * g.my, g.m,
+                                             pp.twz_f, nullptr, GK_NONE, pp.dst_shift, st);
   } else {
     double *z = (double *)data;
     using A = SrcArray<double, double>;
     e = launch_dst<double, A, double, true>(A{z}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_d,
                                             nullptr, GK_NONE, pp.dst_shift, st);
-    if (e == cudaSuccess && g.dim == 2)
-      e = launch_dst<double, A, double, false>(A{z}, z, g.my, pp.Ly, ny, g.mx, g.m, pp.twy_d,
-                                               nullptr, GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim >= 2)
+      e = launch_dst<double, A, double, false>(A{z}, z, g.my, pp.Ly, ny, g.mx,
+                                               (long long)g.mx * g.my, pp.twy_d, nullptr,
+                                               GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim == 3)
+      e = launch_dst<double, A, double, false>(A{z}, z, g.mz, pp.Lz, nz, g.mx * g.my, g.m,
+                                               pp.twz_d, nullptr, GK_NONE, pp.dst_shift, st);
   }
   return e;
 }

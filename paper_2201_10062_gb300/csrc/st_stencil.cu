@@ -28,8 +28,9 @@ Tile tile_for(const Geom &g) {
     t.gx = (g.mx + kBX1 - 1) / kBX1;
     t.gy = 1;
   } else {
+    // 2D blocks over x and the rows (y, and z in 3D)
     t.gx = (g.mx + kBX2 - 1) / kBX2;
-    t.gy = (g.my + kBY2 - 1) / kBY2;
+    t.gy = (g.my * g.mz + kBY2 - 1) / kBY2;
   }
   // chunks cover the first ceil(n/2) planes (each thread also does their mirror images)
   const int half = (g.n + 1) / 2;
@@ -49,17 +50,22 @@ __device__ __forceinline__ double ld(const Tz *p) {
   return (double)__ldg(p);
 }
 
-// tau*K applied at node p of plane base (zero Dirichlet values outside the grid).
+// tau*K applied at node p = (i, jy, jz) of plane base (zero Dirichlet values outside the grid);
+// f holds the node's face coefficients (zero along absent axes, so 1D and 2D add exact zeros).
 template <class Tz>
-__device__ __forceinline__ double tauK(const Tz *__restrict__ base, long long p, int i, int j,
-                                       int mx, int my, int dim, double cw, double ce, double cs,
-                                       double cn, double c) {
-  double r = (cw + ce + cs + cn) * c;
-  if (i > 0) r -= cw * ld(base + p - 1);
-  if (i < mx - 1) r -= ce * ld(base + p + 1);
-  if (dim == 2) {
-    if (j > 0) r -= cs * ld(base + p - mx);
-    if (j < my - 1) r -= cn * ld(base + p + mx);
+__device__ __forceinline__ double tauK(const Tz *__restrict__ base, long long p, int i, int jy,
+                                       int jz, const Geom &g, const Faces6<double> &f, double c) {
+  double r = (f.w + f.e + f.s + f.n + f.d + f.u) * c;
+  if (i > 0) r -= f.w * ld(base + p - 1);
+  if (i < g.mx - 1) r -= f.e * ld(base + p + 1);
+  if (g.dim >= 2) {
+    if (jy > 0) r -= f.s * ld(base + p - g.mx);
+    if (jy < g.my - 1) r -= f.n * ld(base + p + g.mx);
+  }
+  if (g.dim == 3) {
+    const long long pl = (long long)g.mx * g.my;
+    if (jz > 0) r -= f.d * ld(base + p - pl);
+    if (jz < g.mz - 1) r -= f.u * ld(base + p + pl);
   }
   return r;
 }
@@ -88,28 +94,23 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
   }
   if (MODE == SM_RESID_OUTER && !(S->finish && !S->done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;  // row jz*my + jy
+  const int mx = g.mx, n = g.n;
   const long long m = g.m;
-  const bool valid = (i < mx) && (j < my);
+  const bool valid = (i < mx) && (j < g.my * g.mz);
   const int half = (n + 1) >> 1;
   const int k0 = blockIdx.z * kc;
   const int k1 = min(half, k0 + kc);
   const double s = (MODE == SM_MINRES) ? S->inv_beta : 1.0;
   double acc = 0.0;
   if (valid) {
+    const int jz = j / g.my, jy = j - jz * g.my;
     const long long p = (long long)j * mx + i;
-    const double cw = g.cx[(long long)j * (mx + 1) + i];
-    const double ce = g.cx[(long long)j * (mx + 1) + i + 1];
-    double cs = 0.0, cn = 0.0;
-    if (dim == 2) {
-      cs = g.cy[(long long)j * mx + i];
-      cn = g.cy[(long long)(j + 1) * mx + i];
-    }
+    const Faces6<double> fc = faces_at(g, i, jy, jz);
     const double th = g.theta, omth = 1.0 - g.theta;
     auto center = [&](int k) -> double { return ld(z + (long long)k * m + p); };
     auto stiff = [&](int k, double c) -> double {
-      return tauK(z + (long long)k * m, p, i, j, mx, my, dim, cw, ce, cs, cn, c);
+      return tauK(z + (long long)k * m, p, i, jy, jz, g, fc, c);
     };
     // side A (ascending) carries plane kA-1 (and kA-2); side B (descending) carries plane kB and
     // the planes below it
@@ -267,19 +268,10 @@ __device__ __forceinline__ void face_term(acc_df &A, df c, float a, float b) {
   A.add(p, e);
 }
 
-__device__ __forceinline__ df tauK_df(const float *__restrict__ b, long long p, int i, int j, int mx,
-                                      int my, int dim, df cw, df ce, df cs, df cn, float c) {
-  acc_df A{0.f, 0.f};
-  face_term(A, cw, c, i > 0 ? __ldg(b + p - 1) : 0.f);
-  face_term(A, ce, c, i < mx - 1 ? __ldg(b + p + 1) : 0.f);
-  if (dim == 2) {
-    face_term(A, cs, c, j > 0 ? __ldg(b + p - mx) : 0.f);
-    face_term(A, cn, c, j < my - 1 ? __ldg(b + p + mx) : 0.f);
-  }
-  return A.get();
-}
-
-__global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__restrict__ z,
+// D3: the 3D grid (7-point stencil; planes mx*my apart), at three resident blocks per SM so that
+// its two extra planes stay in registers.  The 1D/2D instantiation carries no z terms.
+template <bool D3>
+__global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const float *__restrict__ z,
                                                     df *__restrict__ out, State *S,
                                                     double *__restrict__ partials, int kc) {
   __shared__ double red[32];
@@ -292,30 +284,23 @@ __global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__re
   // first iteration after a device-side restart: the restart pass is complete
   if (lead && S->restart) S->restart = 0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;  // row jz*my + jy
   const int mx = g.mx, my = g.my, dim = g.dim, n = g.n;
-  const long long m = g.m;
-  const bool valid = (i < mx) && (j < my);
+  const long long m = g.m, pl = (long long)mx * my;
+  const bool valid = (i < mx) && (j < my * g.mz);
   const int half = (n + 1) >> 1;
   const int k0 = blockIdx.z * kc;
   const int k1 = min(half, k0 + kc);
   const df s = S->dfs[DFS_IB];
   acc_df D{0.f, 0.f};
   if (valid) {
+    const int jz = D3 ? j / my : 0, jy = j - jz * my;
     const long long p = (long long)j * mx + i;
-    const df cw = g.cxd[(long long)j * (mx + 1) + i];
-    const df ce = g.cxd[(long long)j * (mx + 1) + i + 1];
-    df cs{0.f, 0.f}, cn{0.f, 0.f};
-    if (dim == 2) {
-      cs = g.cyd[(long long)j * mx + i];
-      cn = g.cyd[(long long)(j + 1) * mx + i];
-    }
+    const Faces6<df> fc = faces_df_at(g, i, jy, jz);
+    const df cw = fc.w, ce = fc.e, cs = fc.s, cn = fc.n, cd = fc.d, cu = fc.u;
     const df th = g.th_d, omth = g.omth_d;
     const bool theta = (g.scheme == ST_THETA);
     auto center = [&](int k) -> float { return __ldg(z + (long long)k * m + p); };
-    auto stiff = [&](int k, float c) -> df {
-      return tauK_df(z + (long long)k * m, p, i, j, mx, my, dim, cw, ce, cs, cn, c);
-    };
     auto combine = [&](float c, float c1, float c2, df Kc, df K1) -> df {
       acc_df A{0.f, 0.f};
       if (theta) {
@@ -341,6 +326,39 @@ __global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__re
       }
       return A.get();
     };
+    // The loads of iteration kA + 1 (stencil points of both walks) are issued before the
+    // arithmetic of iteration kA, so their latency overlaps it.
+    struct P5 {
+      float c, w, e, s, n, d, u;
+    };
+    auto load5 = [&](int k) -> P5 {
+      const float *b = z + (long long)k * m + p;
+      P5 r;
+      r.c = __ldg(b);
+      r.w = i > 0 ? __ldg(b - 1) : 0.f;
+      r.e = i < mx - 1 ? __ldg(b + 1) : 0.f;
+      r.s = (dim >= 2 && jy > 0) ? __ldg(b - mx) : 0.f;
+      r.n = (dim >= 2 && jy < my - 1) ? __ldg(b + mx) : 0.f;
+      r.d = (D3 && jz > 0) ? __ldg(b - pl) : 0.f;
+      r.u = (D3 && jz < g.mz - 1) ? __ldg(b + pl) : 0.f;
+      return r;
+    };
+    // tau K at a plane: the face terms in a fixed order
+    auto stiff5 = [&](const P5 &q, float c) -> df {
+      acc_df A{0.f, 0.f};
+      face_term(A, cw, c, q.w);
+      face_term(A, ce, c, q.e);
+      if (dim >= 2) {
+        face_term(A, cs, c, q.s);
+        face_term(A, cn, c, q.n);
+      }
+      if (D3) {
+        face_term(A, cd, c, q.d);
+        face_term(A, cu, c, q.u);
+      }
+      return A.get();
+    };
+    auto stiff = [&](int k, float c) -> df { return stiff5(load5(k), c); };
     const df zero{0.f, 0.f};
     float a1 = 0.f, a2 = 0.f;
     df aK1 = zero;
@@ -357,38 +375,12 @@ __global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__re
       if (theta) bK0 = stiff(kb, b0);
       else if (kb > 0) b1 = center(kb - 1);
     }
-    // The loads of iteration kA + 1 (five-point planes of both walks) are issued before the
-    // arithmetic of iteration kA, so their latency overlaps it.
-    struct P5 {
-      float c, w, e, s, n;
-    };
-    auto load5 = [&](int k) -> P5 {
-      const float *b = z + (long long)k * m + p;
-      P5 r;
-      r.c = __ldg(b);
-      r.w = i > 0 ? __ldg(b - 1) : 0.f;
-      r.e = i < mx - 1 ? __ldg(b + 1) : 0.f;
-      r.s = (dim == 2 && j > 0) ? __ldg(b - mx) : 0.f;
-      r.n = (dim == 2 && j < my - 1) ? __ldg(b + mx) : 0.f;
-      return r;
-    };
-    // tau K at a plane, same face order as tauK_df
-    auto stiff5 = [&](const P5 &q, float c) -> df {
-      acc_df A{0.f, 0.f};
-      face_term(A, cw, c, q.w);
-      face_term(A, ce, c, q.e);
-      if (dim == 2) {
-        face_term(A, cs, c, q.s);
-        face_term(A, cn, c, q.n);
-      }
-      return A.get();
-    };
     // planes read by iteration kA: A-walk plane kA; mirrored walk plane kB - 1 (theta) or kB
     // plus the centre of kB - 2 (BDF2)
     auto planes = [&](int kA, P5 &A, P5 &B, float &C) {
       const int kB = n - 1 - kA;
       A = load5(kA);
-      B = P5{0.f, 0.f, 0.f, 0.f, 0.f};
+      B = P5{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       C = 0.f;
       if (kB != kA) {
         if (theta) {
@@ -399,11 +391,11 @@ __global__ void __launch_bounds__(kNT, 4) k_stencil_df(Geom g, const float *__re
         }
       }
     };
-    P5 pA{0.f, 0.f, 0.f, 0.f, 0.f}, pB = pA;
+    P5 pA{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, pB = pA;
     float pC = 0.f;
     if (k0 < k1) planes(k0, pA, pB, pC);
     for (int kA = k0; kA < k1; ++kA) {
-      P5 nA{0.f, 0.f, 0.f, 0.f, 0.f}, nB = nA;
+      P5 nA{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, nB = nA;
       float nC = 0.f;
       if (kA + 1 < k1) planes(kA + 1, nA, nB, nC);
       const int kB = n - 1 - kA;
@@ -477,16 +469,10 @@ __global__ void k_rhs(Geom g, const double *__restrict__ f, const double *__rest
     if (g.scheme == ST_THETA) {
       r = g.theta * tau * f[(k + 1) * m + p] + (1.0 - g.theta) * tau * f[k * m + p];
       if (k == 0) {
-        const int i = (int)(p % g.mx), j = (int)(p / g.mx);
-        const double cw = g.cx[(long long)j * (g.mx + 1) + i];
-        const double ce = g.cx[(long long)j * (g.mx + 1) + i + 1];
-        double cs = 0.0, cn = 0.0;
-        if (g.dim == 2) {
-          cs = g.cy[(long long)j * g.mx + i];
-          cn = g.cy[(long long)(j + 1) * g.mx + i];
-        }
+        const int i = (int)(p % g.mx), row = (int)(p / g.mx);
+        const int jz = row / g.my, jy = row - jz * g.my;
         const double c = u0[p];
-        const double Kc = tauK(u0, p, i, j, g.mx, g.my, g.dim, cw, ce, cs, cn, c);
+        const double Kc = tauK(u0, p, i, jy, jz, g, faces_at(g, i, jy, jz), c);
         r += c - (1.0 - g.theta) * Kc;
       }
     } else {
@@ -523,15 +509,9 @@ __global__ void k_grad_rhs(Geom g, const double *__restrict__ lam, double *__res
       const double l1 = lam[p];
       if (g.scheme == ST_THETA) {
         if (gu0) {
-          const int i = (int)(p % g.mx), j = (int)(p / g.mx);
-          const double cw = g.cx[(long long)j * (g.mx + 1) + i];
-          const double ce = g.cx[(long long)j * (g.mx + 1) + i + 1];
-          double cs = 0.0, cn = 0.0;
-          if (g.dim == 2) {
-            cs = g.cy[(long long)j * g.mx + i];
-            cn = g.cy[(long long)(j + 1) * g.mx + i];
-          }
-          const double Kl = tauK(lam, p, i, j, g.mx, g.my, g.dim, cw, ce, cs, cn, l1);
+          const int i = (int)(p % g.mx), row = (int)(p / g.mx);
+          const int jz = row / g.my, jy = row - jz * g.my;
+          const double Kl = tauK(lam, p, i, jy, jz, g, faces_at(g, i, jy, jz), l1);
           gu0[p] = l1 - (1.0 - g.theta) * Kl;
         }
         if (gup) gup[p] = 0.0;
@@ -662,7 +642,10 @@ cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, do
   dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
   dim3 grid(t.gx, t.gy, t.nchunk);
   prof_begin(KC_STENCIL, st);
-  k_stencil_df<<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  if (g.dim == 3)
+    k_stencil_df<true><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  else
+    k_stencil_df<false><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -1032,10 +1032,18 @@ cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride
   return cudaGetLastError();
 }
 
+// y lines: mx apart, in planes of mx*my (one per time level and z), in place
 cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st) {
-  return launch_dst_tc_lines(data, data, g.my, g.mx, g.m, (long long)g.n, sop, S, gk, KC_DSTY,
-                             st);
+  return launch_dst_tc_lines(data, data, g.my, g.mx, (long long)g.mx * g.my,
+                             (long long)g.n * g.mz, sop, S, gk, KC_DSTY, st);
+}
+
+// z lines (3D): mx*my apart, in planes of m (one per time level), in place
+cudaError_t launch_dst_tc_z(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st) {
+  return launch_dst_tc_lines(data, data, g.mz, g.mx * g.my, g.m, (long long)g.n, sop, S, gk,
+                             KC_DSTY, st);
 }
 
 // The time DST alone (no scaling): lines of n values m apart, one plane of all m columns.

@@ -6,7 +6,8 @@
 Workloads (seeded, from ``workloads.synthetic``): ``cn2d`` (a = 1, Crank-Nicolson, manufactured
 rhs + N(0, 1e-3) noise), ``bdf2var`` (random a field, BDF2), ``thetavar`` (random a field,
 theta-method with --theta; with --prec Ptheta the Chebyshev inner map of --degree steps),
-``sine1d`` (1D, backward Euler).
+``sine1d`` (1D, backward Euler), ``sine3d`` (3D, a = 1, manufactured, --theta) and ``ex3``
+(the paper's Example 3: 3D, a = 1e-3, f = 0, --theta; mx + 1 = m + 1 of Tables 6-7).
 Prints one JSON line per solve with the iteration count, residuals and the time.
 """
 from __future__ import annotations
@@ -24,7 +25,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="cn2d", choices=["cn2d", "bdf2var", "thetavar", "sine1d"])
+    ap.add_argument("--workload", default="cn2d", choices=["cn2d", "bdf2var", "thetavar", "sine1d", "sine3d", "ex3"])
     ap.add_argument("--mx", type=int, default=255)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
@@ -50,10 +51,14 @@ def main(argv=None):
         w = W.config_2d_varcoef_bdf2(mx=args.mx, n=args.n)
     elif args.workload == "thetavar":
         w = W.config_2d_varcoef_theta(args.mx, args.n, args.theta, seed=5)
+    elif args.workload == "sine3d":
+        w = W.config_3d_sine(args.mx, args.n, theta=args.theta)
+    elif args.workload == "ex3":
+        w = W.paper_example3(args.mx, args.n, args.theta)
     else:
         w = W.config_1d_sine(mx=args.mx, n=args.n)
     spec = P.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, args.prec,
-                         args.precision, args.degree)
+                         args.precision, args.degree, w.mz)
     s = P.Solver(spec)
     if args.autotune:
         s.st_autotune()

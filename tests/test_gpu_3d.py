@@ -1,0 +1,192 @@
+"""3D grids (Sec. 5, Example 3) through the C ABI against the oracle: the 7-point all-at-once
+operator, the right-hand side, P_H / P_theta (constant a, and the Chebyshev inner map for a
+varying a), solves in float64 and mixed precision, and the paper's largest Example 3 systems
+against the iteration counts of Tables 6-7."""
+import numpy as np
+import pytest
+
+from oracle import heat as H
+from workloads import synthetic as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_10062_gb300 as P
+    from paper_2201_10062_gb300 import build
+
+    build.build()
+    P.load_library()
+    return P
+
+
+def _spec(P, w, prec="PH", precision="fp64", degree=0):
+    return P.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec, precision,
+                         degree, w.mz)
+
+
+def _d(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _h(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rel2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+EPS = np.finfo(np.float64).eps
+
+# (mx, my, mz, n, scheme, theta, varcoef): unequal axes, ragged 32-wide tiles, n = 1
+CASES = [
+    (7, 7, 7, 5, "theta", 1.0, False),
+    (15, 7, 3, 6, "theta", 0.5, True),
+    (3, 15, 7, 4, "bdf2", 1.0, True),
+    (31, 3, 15, 1, "theta", 0.5, True),
+    (7, 31, 31, 3, "theta", 0.3, True),
+]
+IDS = [f"{c[0]}x{c[1]}x{c[2]}-n{c[3]}-{c[4]}{c[5]}-{'var' if c[6] else 'const'}" for c in CASES]
+
+
+def _case(c, seed=3):
+    mx, my, mz, n, scheme, theta, var = c
+    return W.small_case(3, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=seed + mx,
+                        mz=mz)
+
+
+def _prec_tol(p):
+    if p.a_nodal is None:
+        return 1e-12
+    mu = H.averaged_stiffness_eigs(p)
+    return max(1e-12, 16 * EPS * mu.max() / mu.min())
+
+
+@pytest.mark.parametrize("c", CASES, ids=IDS)
+def test_operator_rhs_and_preconditioner(pkg, c):
+    w = _case(c)
+    p = H.Problem.from_workload(w)
+    s = pkg.Solver(_spec(pkg, w))
+    v = np.random.default_rng(1).standard_normal((p.n, p.m))
+    assert _rel_max(_h(s.st_apply_op(_d(v))).reshape(p.n, p.m), H.apply_op(p, v)) <= 1e-13
+    up = _d(w.u_prev) if w.u_prev is not None else None
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0), up)
+    assert _rel_max(_h(fH).reshape(p.n, p.m), H.rhs(p, w.f, w.u0, w.u_prev)) <= 1e-13
+    ref = H.apply_prec(p, v)
+    assert _rel_max(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m), ref) <= _prec_tol(p)
+    z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(p.n, p.m)
+    assert _rel2(z32, ref) <= 2e-5
+    s.close()
+
+
+@pytest.mark.parametrize("c", [CASES[1], CASES[4]], ids=[IDS[1], IDS[4]])
+@pytest.mark.parametrize("degree", [1, 3])
+def test_ptheta_chebyshev_3d(pkg, c, degree):
+    """P_theta with a varying 3D coefficient: the same Chebyshev map as the oracle's."""
+    w = _case(c)
+    if w.scheme != "theta":
+        pytest.skip("P_theta is defined for the theta-method")
+    p = H.Problem.from_workload(w, prec="Ptheta", inner_degree=degree)
+    s = pkg.Solver(_spec(pkg, w, prec="Ptheta", degree=degree))
+    v = np.random.default_rng(2).standard_normal((p.n, p.m))
+    ref = H.apply_ptheta(p, v)
+    assert _rel_max(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m), ref) <= 1e-11
+    z32 = _h(s.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(p.n, p.m)
+    assert _rel2(z32, ref) <= 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["PH", "Ptheta"])
+def test_solve_3d(pkg, precision, prec):
+    """Equal-iteration parity and natural-stop counts within one (float64); error against the
+    converged oracle solution (mixed)."""
+    w = W.small_case(3, 15, 15, 12, scheme="theta", theta=0.5, varcoef=True, seed=17, mz=15)
+    deg = 2 if prec == "Ptheta" else None
+    p = H.Problem.from_workload(w, prec=prec, inner_degree=deg)
+    fH = H.rhs(p, w.f, w.u0)
+    s = pkg.Solver(_spec(pkg, w, prec=prec, precision=precision, degree=deg or 0))
+    if precision == "fp64":
+        u, st = s.st_solve(_d(fH), tol=0.0, maxit=7, allow_not_converged=True)
+        x_or, info = H.solve(p, fH, tol=0.0, maxit=7, rule="est")
+        assert st["iterations"] == info["iterations"] == 7
+        assert _rel2(_h(u).reshape(p.n, p.m), x_or) <= 1e-10
+        u, st = s.st_solve(_d(fH), tol=1e-8, maxit=200)
+        x_or, info = H.solve(p, fH, tol=1e-8, maxit=200)
+        assert abs(st["iterations"] - info["iterations"]) <= 1
+    else:
+        x_ref, info = H.solve(p, fH, tol=1e-13, maxit=400)
+        u, st = s.st_solve(_d(fH), tol=1e-10, maxit=400)
+        assert st["true_rel_res"] <= 1e-10
+        assert _rel2(_h(u).reshape(p.n, p.m), x_ref) <= 1e-8
+    s.close()
+
+
+def test_tensor_core_y_and_z_passes(pkg):
+    """my + 1 and mz + 1 in {32, ..., 256} take the tensor-core DST in float32: against the oracle
+    and against the FFT passes (ST_DISABLE_TENSOR_CORES=1)."""
+    import os
+
+    w = W.small_case(3, 7, 31, 32, scheme="theta", theta=0.5, varcoef=True, seed=9, mz=63)
+    p = H.Problem.from_workload(w)
+    v = np.random.default_rng(4).standard_normal((p.n, p.m))
+    ref = H.apply_prec(p, v)
+    s_tc = pkg.Solver(_spec(pkg, w, precision="mixed"))
+    z_tc = _h(s_tc.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(p.n, p.m)
+    os.environ["ST_DISABLE_TENSOR_CORES"] = "1"
+    try:
+        s_ff = pkg.Solver(_spec(pkg, w, precision="mixed"))
+    finally:
+        del os.environ["ST_DISABLE_TENSOR_CORES"]
+    z_ff = _h(s_ff.st_apply_prec_f32(_d(v))).astype(np.float64).reshape(p.n, p.m)
+    assert _rel2(z_tc, ref) <= 2e-5 and _rel2(z_ff, ref) <= 2e-5 and _rel2(z_tc, z_ff) <= 2e-5
+    s_tc.close()
+    s_ff.close()
+
+
+# Example 3 at the paper's largest sizes (Tables 6-7): n = 64 with m + 1 = 64 (16,003,008
+# unknowns) and n = 32 with m + 1 = 32, tol 1e-6 as in the paper
+EX3 = [(1.0, 64, 64, "PH", 21), (1.0, 64, 64, "Ptheta", 24), (0.5, 64, 64, "PH", 21),
+       (0.5, 64, 64, "Ptheta", 26), (1.0, 32, 32, "PH", 18), (0.5, 32, 32, "Ptheta", 22)]
+
+
+@pytest.mark.parametrize("theta,n,mp1,prec,iters", EX3,
+                         ids=[f"th{c[0]}-n{c[1]}-m{c[2]}-{c[3]}" for c in EX3])
+def test_example3_iteration_counts(pkg, theta, n, mp1, prec, iters):
+    """Float64 solves of Example 3 reach the paper's iteration counts within two (the stopping
+    rule details differ), and their residual, checked by the oracle's operator, is below 1e-6."""
+    w = W.paper_example3(mp1 - 1, n, theta)
+    p = H.Problem.from_workload(w, prec=prec)
+    s = pkg.Solver(_spec(pkg, w, prec=prec, degree=1 if prec == "Ptheta" else 0))
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0))
+    u, st = s.st_solve(fH, tol=1e-6, maxit=100)
+    assert abs(st["iterations"] - iters) <= 2, st
+    fH_or = H.rhs(p, w.f, w.u0)
+    r = H.flip(fH_or, p.n) - H.apply_op(p, _h(u).reshape(p.n, p.m))
+    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-6 * (1 + 1e-6)
+    s.close()
+
+
+def test_grad_a_rejects_3d(pkg):
+    w = _case(CASES[0])
+    s = pkg.Solver(_spec(pkg, w))
+    z = torch.zeros(w.n * w.m, dtype=torch.float64, device="cuda")
+    u0 = torch.zeros(w.m, dtype=torch.float64, device="cuda")
+    g = torch.zeros((w.mx + 2) * (w.my + 2) * (w.mz + 2), dtype=torch.float64, device="cuda")
+    import ctypes
+
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    rc = s.lib.st_grad_a(s.h, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                         ctypes.c_void_p(u0.data_ptr()), ctypes.c_void_p(g.data_ptr()))
+    assert rc == ST_ERR_ARG
+    s.close()
