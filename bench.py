@@ -388,10 +388,29 @@ def _timed(stream, fn, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
+def _solve_leg(P, w, spec, stream, dev, world, reps):
+    """Time `reps` solves of workload w with spec after one warm-up (CUDA events)."""
+    import torch
+
+    s = P.Solver(spec, stream)
+    s.st_autotune()
+    up = torch.tensor(w.u_prev, device=dev) if w.u_prev is not None else None
+    fH = s.st_assemble_rhs(torch.tensor(w.f, device=dev), torch.tensor(w.u0, device=dev), up)
+    u = s.empty(w.n, w.m)
+    s.st_solve(fH, tol=TOL, maxit=600, out=u)  # warm-up
+    ms, (_, st) = _timed(stream, lambda: s.st_solve(fH, tol=TOL, maxit=600, out=u), reps)
+    ms = max_over_ranks(ms, world)
+    s.close()
+    return {"value": world * w.N / (ms * 1e-3), "ms_per_step": ms, "iterations": st["iterations"],
+            "true_rel_res": st["true_rel_res"], "steps": reps}
+
+
 def run_extra_workloads(P, W, stream, dev, world):
     """The other solve workloads, one line object each: 2D variable-coefficient BDF2 at
-    511^2 x 128 (mixed and FP64), and the 64-instance uneven batch (one captured graph, mixed)
-    against the same 64 instances solved one by one in mixed and in FP64."""
+    511^2 x 128 (mixed and FP64); 2D variable a with the theta-method at 255^2 x 256 under P_H and
+    under P_theta with its Chebyshev inner map; the paper's 3D Example 3 at 63^3 x 64; and the
+    64-instance uneven batch (one captured graph, mixed) against the same 64 instances solved one
+    by one in mixed and in FP64."""
     import torch
 
     out = {}
@@ -416,6 +435,32 @@ def run_extra_workloads(P, W, stream, dev, world):
         s.close()
     del f, u0, up
     out["bdf2_var_511x511_n128"] = {"unit": UNIT, "unknowns": w.N, "tol": TOL, **res}
+    # ---- 2D variable a, theta = 1, 255^2 x 256: P_H against P_theta (Chebyshev inner map)
+    w = W.config_2d_varcoef_theta(255, 256, 1.0, seed=5)
+
+    def spec2(prec, precision):
+        return P.ProblemSpec(2, w.mx, w.my, w.n, w.T, "theta", 1.0, w.a_nodal, prec, precision)
+
+    out["ptheta_var_255x255_n256"] = {
+        "unit": UNIT, "unknowns": w.N, "tol": TOL,
+        "inner_degree": P.ST_PTHETA_DEFAULT_DEGREE,
+        "PH_mixed": _solve_leg(P, w, spec2("PH", "mixed"), stream, dev, world, 3),
+        "Ptheta_mixed": _solve_leg(P, w, spec2("Ptheta", "mixed"), stream, dev, world, 3),
+        "Ptheta_fp64": _solve_leg(P, w, spec2("Ptheta", "fp64"), stream, dev, world, 1),
+    }
+    # ---- 3D, Sec. 5 Example 3 (a = 1e-3, f = 0), 63^3 x 64 = 16,003,008 unknowns
+    w = W.paper_example3(63, 64, 1.0)
+
+    def spec3(prec, precision):
+        return P.ProblemSpec(3, w.mx, w.my, w.n, w.T, "theta", 1.0, w.a_nodal, prec, precision,
+                             0, w.mz)
+
+    out["example3_3d_63x63x63_n64"] = {
+        "unit": UNIT, "unknowns": w.N, "tol": TOL,
+        "PH_mixed": _solve_leg(P, w, spec3("PH", "mixed"), stream, dev, world, 3),
+        "Ptheta_mixed": _solve_leg(P, w, spec3("Ptheta", "mixed"), stream, dev, world, 3),
+        "PH_fp64": _solve_leg(P, w, spec3("PH", "fp64"), stream, dev, world, 1),
+    }
     # ---- 64 uneven instances
     draws = W.batch_draws(64, seed=4)
     ws = [W.config_2d_varcoef_theta(d["mx"], d["n"], d["theta"], d["seed"]) for d in draws]

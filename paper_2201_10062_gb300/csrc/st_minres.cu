@@ -539,6 +539,7 @@ int build_tables(st_handle *h) {
   // a_j = rho_j rho_{j-1}, s_j = 2 rho_j/half.  A zero-width interval (B_k = A_k) is solved by the
   // first step: the later scalars are zero.
   std::vector<double> cheb_a((size_t)cheb * n), cheb_s((size_t)cheb * n);
+  bool cheb_all_exact = true;
   for (int k = 0; k < n && cheb; ++k) {
     const double c = lht[k] * tau;
     const double den = lh[k] + c * f_bar * mu0_max;
@@ -548,6 +549,7 @@ int build_tables(st_handle *h) {
     cheb_a[k] = 0.0;
     cheb_s[k] = 1.0 / centre;
     const bool exact = !(half > 1e-14 * centre);
+    cheb_all_exact = cheb_all_exact && exact;
     const double sigma1 = exact ? 0.0 : centre / half;
     double rho = exact ? 0.0 : 1.0 / sigma1;
     for (int j = 1; j < cheb; ++j) {
@@ -658,7 +660,9 @@ int build_tables(st_handle *h) {
   h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
   PrecPlan &pp = h->pp;
   pp.pcr = (p.prec == ST_PREC_PTHETA && p.a_nodal != nullptr && g.dim == 1) ? 1 : 0;
-  pp.cheb = cheb;
+  // every interval of zero width (a constant field): the steps after the first add exact zeros,
+  // so one step gives the same map
+  pp.cheb = (cheb > 1 && cheb_all_exact) ? 1 : cheb;
   if (cheb) {
     const size_t cb = cheb_coef_bytes(g, cheb);
     ST_TRY(cudaMalloc(&h->cheb, cb + 5 * (size_t)g.N * sizeof(double)));

@@ -344,6 +344,25 @@ def test_ptheta_cheb_solve(pkg, precision):
     s.close()
 
 
+def test_ptheta_cheb_constant_field_is_one_step(pkg):
+    """A constant field given as a_nodal: B_k = A_k, every later Chebyshev step adds zero, and the
+    handle applies one step; degrees 1 and 4 agree exactly and match the exact solve."""
+    w = W.small_case(2, 31, 15, 8, theta=0.5, varcoef=True, seed=5)
+    w.a_nodal = np.full_like(w.a_nodal, 1.3)
+    p = H.Problem.from_workload(w, prec="Ptheta")
+    v = np.random.default_rng(11).standard_normal((p.n, p.m))
+    ref = H.apply_ptheta(p, v)
+    out = []
+    for deg in (1, 4):
+        spec = _spec(pkg, w, prec="Ptheta")
+        spec.inner_degree = deg
+        s = pkg.Solver(spec)
+        out.append(_h(s.st_apply_prec(_d(v))).reshape(p.n, p.m))
+        s.close()
+    assert np.array_equal(out[0], out[1])
+    assert _rel_max(out[0], ref) <= 1e-11
+
+
 def test_ptheta_cheb_full_size(pkg):
     """2D 255^2, n = 256, theta = 1, seeded 8x8-mode coefficient field (the adjoint problem's
     shape) with the Chebyshev P_theta: full-vector apply parity (float64), and a mixed-precision
