@@ -45,6 +45,10 @@ ALG_BYTES = {
 }
 # per MINRES iteration (2D): stencil + 2 x-DST + 2 y-DST + time kernel + update
 ITER_BYTES = {"fp64": 16 + 56 + 32 + 16 + 48, "mixed": 12 + 44 + 16 + 8 + 44}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
+# mixed 2D Crank-Nicolson solve, 255^2 x 256), per kernel class, for the classes captured with the
+# current kernels: profiles/k_dst_space_traffic_cn2d_255x255_n256.md
+NCU_TRAFFIC = {("mixed", 255, 256, "dst_x"): 313.9e6}
 
 
 def _env_int(name, default):
@@ -321,7 +325,8 @@ def run_ours(args, world, rank, local):
     launches = sum(v["launches"] for v in prof.values())
     roofline = {
         "bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-        "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+        "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+        "traffic": NCU_TRAFFIC.get(("mixed", w.mx, w.n, dom)),
         "peak_source": peaks["src"], "alg_bytes_per_launch": alg_bytes,
         "avg_launch_ms": avg_ms,
         "share_of_kernel_time": d["ms"] / total_ms if total_ms else None,

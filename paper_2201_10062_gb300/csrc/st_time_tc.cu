@@ -211,9 +211,23 @@ __device__ __forceinline__ void split_h2(float a, float b, uint32_t &hi, uint32_
 // of one row).  src(t, c) gives the value.
 // For odd n the middle element (t = n-1-t) pairs with nothing: U = x_t, and D is multiplied by
 // zero columns of A (sin(pi k (n+1)/2 / (n+1)) = 0 for even k).
+// The values build_b folds for thread tid: a[q] = src(t, c) and b[q] = src(n-1-t, c) with
+// t = tb*8 + q (b = 0 for the odd middle row); zeros beyond the h/8 t-blocks.
 template <class Src>
-__device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
-                                        uint32_t colinv_off, int n, Src src, int tid) {
+__device__ __forceinline__ void load_b(int n, Src src, int tid, float (&a)[8], float (&b)[8]) {
+  const int h = (n + 1) >> 1, hb = h >> 3;
+  const int c = tid & (kTN - 1), tb = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = tb * 8 + q;
+    a[q] = (tb < hb) ? src(t, c) : 0.f;
+    b[q] = (tb < hb && n - 1 - t != t) ? src(n - 1 - t, c) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void build_b_vals(unsigned char *smem, const TcSmem &L,
+                                             uint32_t bop_off, uint32_t colinv_off, int n,
+                                             const float (&a)[8], const float (&b)[8], int tid) {
   const int h = (n + 1) >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
   unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
   float *colscale = reinterpret_cast<float *>(smem + L.colscale);
@@ -225,10 +239,8 @@ __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, ui
   if (tb < hb) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int t = tb * 8 + q;
-      const float a = src(t, c), b = (n - 1 - t == t) ? 0.f : src(n - 1 - t, c);
-      u[q] = a + b;
-      d[q] = a - b;
+      u[q] = a[q] + b[q];
+      d[q] = a[q] - b[q];
       mx = fmaxf(mx, fmaxf(fabsf(u[q]), fabsf(d[q])));
     }
   }
@@ -263,6 +275,14 @@ __device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, ui
     *reinterpret_cast<uint4 *>(bop + 2 * piece + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
     *reinterpret_cast<uint4 *>(bop + 3 * piece + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
   }
+}
+
+template <class Src>
+__device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
+                                        uint32_t colinv_off, int n, Src src, int tid) {
+  float a[8], b[8];
+  load_b(n, src, tid, a, b);
+  build_b_vals(smem, L, bop_off, colinv_off, n, a, b, tid);
 }
 
 // Issue the 2 parities x (h/16) K-steps x 3 piece products from the operand at `bop_off` into
@@ -401,6 +421,17 @@ __global__ void __launch_bounds__(kNT, 1)
   bool pend = false;  // a second transform is in flight
   long long pj0 = 0;
   int pje = 0;
+  // this thread's input values of the next tile, loaded one tile ahead so that the loads are in
+  // flight while the previous tile finishes (tiles are disjoint: the in-place write-back of one
+  // tile never touches another's input)
+  float pa[8], pb[8];
+  auto load_tile = [&](long long tl) {
+    const long long jt = tl * kTN;
+    const int jn = (int)min((long long)kTN, m - jt);
+    load_b(n, [&](int t, int c) -> float { return (c < jn) ? data[(long long)t * m + jt + c] : 0.f; },
+           tid, pa, pb);
+  };
+  if ((long long)blockIdx.x < ntiles) load_tile(blockIdx.x);
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long j0 = tile * kTN;
     const int je = (int)min((long long)kTN, m - j0);
@@ -413,14 +444,14 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       tmus[tid] = t;
     }
-    // 1. first operand from global memory (the previous tile's second transform is running)
-    build_b(smem, L, L.bop1, L.colinv1, n,
-            [&](int t, int c) -> float { return (c < je) ? data[(long long)t * m + j0 + c] : 0.f; },
-            tid);
+    // 1. first operand from the values loaded ahead (the previous tile's second transform is
+    // running)
+    build_b_vals(smem, L, L.bop1, L.colinv1, n, pa, pb, tid);
     fence_async_smem();
     __syncthreads();
     fence_after();
     if (tid == 0) issue_mmas(smem, L, L.bop1, h, dcol1, mbar1);
+    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
     // 2. while the first transform runs: finish the previous tile
     if (pend) finish_second(pj0, pje);
     // 3. first epilogue: unscale, spectral scaling, energy; scaled Y into the parity-split tile
