@@ -60,6 +60,8 @@ def _spec(**kw):
     dict(prec="Ptheta", a_nodal=np.ones((17, 17)), inner_degree=-1),
     dict(inner_degree=2), dict(prec="Ptheta", inner_degree=2),
     dict(dim=1, my=1, prec="Ptheta", a_nodal=np.ones(17), inner_degree=2),
+    dict(dim=3, mz=14), dict(dim=3, mz=1), dict(dim=4),
+    dict(dim=3, mx=1023, my=1023, mz=1023, n=4),  # n*m beyond 2^31
 ])
 def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
     from paper_2201_10062_gb300 import ST_ERR_ARG
@@ -103,6 +105,42 @@ def test_workspace_bytes_chebyshev_ptheta(lib):
     for deg in (0, 1, 16):
         b = st_workspace_bytes(_spec(mx=255, my=255, n=64, a_nodal=a, prec="Ptheta", inner_degree=deg))
         assert 5 * 8 * N <= b - base <= 5 * 8 * N + (1 << 20)
+
+
+def test_c_abi_rejects_mz_below_3d(lib):
+    """st_problem.mz must be 0 or 1 for dim 1 and 2 (the binding always passes 1 there)."""
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    p, keep = _spec(dim=2).to_c()
+    p.mz = 7
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG
+    size = ctypes.c_size_t(0)
+    assert lib.st_workspace_bytes(ctypes.byref(p), ctypes.byref(size)) == ST_ERR_ARG
+
+
+def test_setup_rejects_nonpositive_a_3d(lib):
+    from paper_2201_10062_gb300 import ST_ERR_ARG
+
+    a = np.ones((9, 17, 17))
+    a[2, 3, 4] = -1.0
+    p, keep = _spec(dim=3, mz=7, a_nodal=a).to_c()
+    h = ctypes.c_void_p()
+    assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG
+
+
+def test_workspace_bytes_3d(lib):
+    """3D: the same vectors over m = mx*my*mz; the Chebyshev P_theta adds its five scratch
+    vectors."""
+    from paper_2201_10062_gb300 import st_workspace_bytes
+
+    N = 63 * 63 * 63 * 64
+    b64 = st_workspace_bytes(_spec(dim=3, mx=63, my=63, mz=63, n=64))
+    assert 9 * 8 * N <= b64 <= 9 * 8 * N + (64 << 20)
+    a = np.ones((65, 65, 65))
+    bc = st_workspace_bytes(_spec(dim=3, mx=63, my=63, mz=63, n=64, a_nodal=a, prec="Ptheta"))
+    base = st_workspace_bytes(_spec(dim=3, mx=63, my=63, mz=63, n=64, a_nodal=a))
+    assert 5 * 8 * N <= bc - base <= 5 * 8 * N + (1 << 20)
 
 
 def test_null_arguments(lib):
