@@ -96,3 +96,38 @@ def test_batch_of_64_uneven_instances(pkg):
         r = H.flip(fH, p.n) - H.apply_op(p, outs[i].cpu().numpy().reshape(p.n, p.m))
         assert np.linalg.norm(r) / np.linalg.norm(fH) <= 1e-8 * (1 + 1e-6)
     B.close()
+
+
+def test_batch_mixes_preconditioners_and_dimensions(pkg):
+    """One graph over instances with different preconditioner paths and grids: 2D P_H, 2D P_theta
+    (Chebyshev inner map), 1D P_theta (PCR), 3D P_H and 3D P_theta.  Each instance against the
+    oracle's converged solution and against its own single solve."""
+    cases = [  # (dim, mx, my, mz, n, theta, prec, degree)
+        (2, 31, 15, 1, 24, 0.5, "PH", 0),
+        (2, 15, 31, 1, 32, 1.0, "Ptheta", 2),
+        (1, 127, 1, 1, 40, 0.5, "Ptheta", 0),
+        (3, 7, 15, 7, 16, 1.0, "PH", 0),
+        (3, 15, 7, 7, 12, 0.5, "Ptheta", 3),
+    ]
+    ws, specs, probs = [], [], []
+    for i, (dim, mx, my, mz, n, th, prec, deg) in enumerate(cases):
+        w = W.small_case(dim, mx, my, n, scheme="theta", theta=th, varcoef=True, seed=90 + i, mz=mz)
+        ws.append(w)
+        specs.append(pkg.ProblemSpec(dim, mx, my, n, w.T, "theta", th, w.a_nodal, prec, "mixed",
+                                     deg, mz))
+        probs.append(H.Problem.from_workload(
+            w, prec=prec, inner_degree=(deg or pkg.ST_PTHETA_DEFAULT_DEGREE) if dim >= 2 else None))
+    B = pkg.BatchSolver(specs)
+    fHs = [B.instance(i).st_assemble_rhs(_d(w.f), _d(w.u0)) for i, w in enumerate(ws)]
+    outs, stats = B.st_solve_batch(fHs, tol=1e-10, maxit=600)
+    for i, (w, p) in enumerate(zip(ws, probs)):
+        fH = H.rhs(p, w.f, w.u0)
+        x_ref, _ = H.solve(p, fH, tol=1e-13, maxit=600)
+        u = outs[i].cpu().numpy().reshape(p.n, p.m)
+        assert stats[i]["status"] == 0 and stats[i]["true_rel_res"] <= 1e-10, (i, stats[i])
+        assert _rel(u, x_ref) <= 1e-8, (i, _rel(u, x_ref))
+        single = pkg.Solver(specs[i])
+        _, st1 = single.st_solve(fHs[i], tol=1e-10, maxit=600)
+        assert abs(st1["iterations"] - stats[i]["iterations"]) <= 2, (i, st1, stats[i])
+        single.close()
+    B.close()
