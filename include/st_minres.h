@@ -77,8 +77,10 @@ typedef struct st_problem {
   int scheme;             /* ST_THETA or ST_BDF2                                             */
   double theta;           /* in [0,1] for ST_THETA, ignored for ST_BDF2                       */
   const double *a_nodal;  /* host, nodal a on the (my+2) x (mx+2) grid incl. boundary nodes  */
-                          /* ((mx+2) in 1D, (mz+2) x (my+2) x (mx+2) in 3D), a > 0; NULL     */
-                          /* means a = 1.  Copied by st_setup.                                */
+                          /* ((mx+2) in 1D, (mz+2) x (my+2) x (mx+2) in 3D), finite, a >= 0, */
+                          /* and every face value (the mean of the two nodes of a face on an  */
+                          /* interior grid line) > 0, so a may vanish on the boundary (Sec. 5 */
+                          /* Example 2); NULL means a = 1.  Copied by st_setup.               */
   int prec;               /* ST_PREC_PH or ST_PREC_PTHETA                                    */
   int precision;          /* ST_FP64 or ST_MIXED                                             */
   void *stream;           /* cudaStream_t; NULL = the legacy default stream                  */

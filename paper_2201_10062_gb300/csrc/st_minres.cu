@@ -278,7 +278,31 @@ int check_problem(const st_problem *p) {
                           : (p->dim == 2) ? (long long)(p->mx + 2) * (p->my + 2)
                                           : (long long)(p->mx + 2) * (p->my + 2) * (p->mz + 2);
     for (long long i = 0; i < cnt; ++i)
-      if (!(p->a_nodal[i] > 0.0) || !std::isfinite(p->a_nodal[i])) return ST_ERR_ARG;
+      if (!(p->a_nodal[i] >= 0.0) || !std::isfinite(p->a_nodal[i])) return ST_ERR_ARG;
+    // every face on an interior grid line (the mean of its two nodes) must be positive, so that
+    // K is symmetric positive definite; nodes may be zero (a can vanish on the boundary)
+    const int mx = p->mx, my = (p->dim >= 2) ? p->my : 1, mz = (p->dim == 3) ? p->mz : 1;
+    const long long sy = mx + 2, sz = (long long)(mx + 2) * (my + 2);
+    auto at = [&](int K, int J, int I) -> double {
+      if (p->dim == 1) return p->a_nodal[I];
+      if (p->dim == 2) return p->a_nodal[(long long)J * sy + I];
+      return p->a_nodal[(long long)K * sz + (long long)J * sy + I];
+    };
+    const int k0 = (p->dim == 3) ? 1 : 0, j0 = (p->dim >= 2) ? 1 : 0;
+    for (int k = k0; k < k0 + mz; ++k)
+      for (int j = j0; j < j0 + my; ++j)
+        for (int i = 0; i <= mx; ++i)
+          if (!(at(k, j, i) + at(k, j, i + 1) > 0.0)) return ST_ERR_ARG;  // x faces
+    if (p->dim >= 2)
+      for (int k = k0; k < k0 + mz; ++k)
+        for (int j = 0; j <= my; ++j)
+          for (int i = 1; i <= mx; ++i)
+            if (!(at(k, j, i) + at(k, j + 1, i) > 0.0)) return ST_ERR_ARG;  // y faces
+    if (p->dim == 3)
+      for (int k = 0; k <= mz; ++k)
+        for (int j = 1; j <= my; ++j)
+          for (int i = 1; i <= mx; ++i)
+            if (!(at(k, j, i) + at(k + 1, j, i) > 0.0)) return ST_ERR_ARG;  // z faces
   }
   return ST_OK;
 }

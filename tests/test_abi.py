@@ -74,14 +74,25 @@ def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
 
 
 def test_setup_rejects_nonpositive_a(lib):
+    """a must be finite and >= 0, with every face (mean of two nodes on an interior line) > 0."""
     import numpy as np
-    from paper_2201_10062_gb300 import ST_ERR_ARG
+    from paper_2201_10062_gb300 import ST_ERR_ARG, st_workspace_bytes
 
-    a = np.ones((17, 17))
-    a[3, 4] = 0.0
-    p, keep = _spec(a_nodal=a).to_c()
-    h = ctypes.c_void_p()
-    assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG
+    for bad in ("negative", "zero face", "nan"):
+        a = np.ones((17, 17))
+        if bad == "negative":
+            a[3, 4] = -1e-3
+        elif bad == "zero face":
+            a[3, 4] = a[3, 5] = 0.0  # the x face between them is zero
+        else:
+            a[8, 8] = np.nan
+        p, keep = _spec(a_nodal=a).to_c()
+        h = ctypes.c_void_p()
+        assert lib.st_setup(ctypes.byref(p), ctypes.byref(h)) == ST_ERR_ARG, bad
+    # a vanishing on the boundary nodes (the paper's Example 2, a = 1e-5 sin(pi x y)) is valid
+    x = np.linspace(0.0, 1.0, 17)
+    a = 1e-5 * np.sin(np.pi * np.outer(x, x))
+    assert st_workspace_bytes(_spec(a_nodal=a)) > 0
 
 
 def test_workspace_bytes(lib):
