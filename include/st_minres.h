@@ -172,9 +172,11 @@ int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const do
 
 /* Autotuner: times the candidate launch shapes of this handle's kernels on its own buffers
  * (CUDA events, `reps` launches each, 1..100) -- blocks per stencil launch, sequences per
- * spatial-DST block, column tile of the FFMA time kernel -- keeps the fastest, and caches the
- * choice per (dim, mx, my, mz, n, precision, kernel path) for the process.  Synchronous; clobbers
- * the handle's workspace (call it between solves).  st_setup_batch runs it for every instance. */
+ * spatial-DST block, column tile of the FFMA time kernel -- and, in float32, the tensor-core
+ * kernel of each stage (time DST with scaling, y and z passes) against its CUDA-core
+ * counterpart.  It keeps the fastest of each and caches the choice per (dim, mx, my, mz, n,
+ * precision, kernel path) for the process.  Synchronous; clobbers the handle's workspace (call
+ * it between solves).  st_setup_batch runs it for every instance. */
 int st_autotune(st_handle *h, int reps);
 
 /* Batched solves: `count` independent instances (each its own st_problem, precision ST_MIXED;

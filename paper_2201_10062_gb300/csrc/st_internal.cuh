@@ -380,6 +380,10 @@ cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *da
 cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
                           cudaStream_t st);
 bool time_J_fits(int n, int J, bool fp32);
+// one spatial pass along y (axis 1) or z (axis 2), float32, in place and ungated: on the tensor
+// cores with tc_img, by the shared-memory FFT when tc_img is null
+cudaError_t tune_run_pass(const Geom &g, const PrecPlan &pp, int axis,
+                          const unsigned short *tc_img, float *data, State *S, cudaStream_t st);
 
 // mixed path: double-float (df) MINRES vectors, float32 preconditioned vectors
 cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, double *partials,
@@ -490,6 +494,9 @@ struct st_handle {
   double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
   double *gfx, *gfy;     // face-gradient scratch for st_grad_a
   void *cheb;            // P_theta, 2D varying a: Chebyshev scalars and scratch vectors
+  // the tensor-core operand images the handle was built with (the autotuner may switch a stage
+  // to its CUDA-core kernel by clearing the plan's pointer; these keep the originals)
+  const unsigned short *tc_time_img, *tc_y_img, *tc_z_img;
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)

@@ -723,6 +723,9 @@ int build_tables(st_handle *h) {
                           : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopy);
   pp.sop_z = sopz.empty() ? nullptr
                           : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopz);
+  h->tc_time_img = pp.sop;
+  h->tc_y_img = pp.sop_y;
+  h->tc_z_img = pp.sop_z;
   pp.Lx = Lx;
   pp.Ly = Ly;
   pp.Lz = Lz;
@@ -1119,6 +1122,7 @@ int st_profile_end(st_handle *h, st_kernel_time *out, int nclasses) {
 namespace {
 struct Knobs {
   int st_target, dst_shift, jd, jf;
+  int tc_time, tc_y, tc_z;  // 1: the stage runs on the tensor cores (when the handle has them)
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int>, Knobs> g_tune_cache;
@@ -1129,8 +1133,14 @@ int st_autotune(st_handle *h, int reps) {
   ST_TRY(cudaSetDevice(h->device));
   const bool fp32 = h->mixed;
   const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.mz, h->g.n, (int)fp32,
-                                   (h->pp.sop ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
-                                       (h->pp.cheb ? 4 : 0));
+                                   (h->tc_time_img ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
+                                       (h->pp.cheb ? 4 : 0) + (h->tc_y_img ? 8 : 0) +
+                                       (h->tc_z_img ? 16 : 0));
+  auto apply_engines = [&](const Knobs &k) {
+    h->pp.sop = k.tc_time ? h->tc_time_img : nullptr;
+    h->pp.sop_y = k.tc_y ? h->tc_y_img : nullptr;
+    h->pp.sop_z = k.tc_z ? h->tc_z_img : nullptr;
+  };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1139,9 +1149,12 @@ int st_autotune(st_handle *h, int reps) {
       h->pp.dst_shift = it->second.dst_shift;
       h->pp.time_J_d = it->second.jd;
       h->pp.time_J_f = it->second.jf;
+      apply_engines(it->second);
       return ST_OK;
     }
   }
+  // tune from the tensor-core configuration the handle was built with
+  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1});
   cudaStream_t st = h->stream;
   const Geom &g = h->g;
   cudaEvent_t e0, e1;
@@ -1207,8 +1220,11 @@ int st_autotune(st_handle *h, int reps) {
     }
     h->pp.dst_shift = bs;
   }
-  // 3. float32/float64 FFMA time kernel (the tensor-core kernel has a fixed tile): column tile
-  if (!h->pp.sop && !h->pp.sop_long) {
+  // 3. float32/float64 FFMA time kernel (the tensor-core kernel has a fixed tile): column tile;
+  // then, where the tensor-core kernel exists, the faster of the two engines (short time axes
+  // give the tensor-core kernel little work per tile)
+  int tc_time = h->tc_time_img ? 1 : 0, tc_y = h->tc_y_img ? 1 : 0, tc_z = h->tc_z_img ? 1 : 0;
+  if (!h->pp.sop_long) {
     const int cand[] = {16, 32, 48, 64};
     float best = 1e30f;
     int bj = 0;
@@ -1222,14 +1238,39 @@ int st_autotune(st_handle *h, int reps) {
       }
     }
     if (fp32) h->pp.time_J_f = bj; else h->pp.time_J_d = bj;
+    if (fp32 && h->tc_time_img && !h->pp.pcr && !h->pp.cheb) {
+      const float ms_tc = timed([&]() {
+        return launch_time_tc((float *)h->Z[0], h->g, h->pp.spec_f, h->tc_time_img, h->S,
+                              TM_NONE, h->partials, GK_NONE, st);
+      });
+      tc_time = (ms_tc <= best) ? 1 : 0;
+    }
   }
+  // 4. spatial y and z passes (float32): tensor cores against the shared-memory FFT
+  if (fp32) {
+    const unsigned short *img[2] = {h->tc_y_img, h->tc_z_img};
+    int *use[2] = {&tc_y, &tc_z};
+    for (int axis = 1; axis <= 2; ++axis) {
+      if (!img[axis - 1]) continue;
+      const float ms_tc = timed([&]() {
+        return tune_run_pass(h->g, h->pp, axis, img[axis - 1], (float *)h->Z[0], h->S, st);
+      });
+      const float ms_fft = timed([&]() {
+        return tune_run_pass(h->g, h->pp, axis, nullptr, (float *)h->Z[0], h->S, st);
+      });
+      *use[axis - 1] = (ms_tc <= ms_fft) ? 1 : 0;
+    }
+  }
+  const Knobs chosen{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f, tc_time,
+                     tc_y, tc_z};
+  apply_engines(chosen);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) rc = map_cuda(le);
   if (rc == ST_OK) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = Knobs{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f};
+    g_tune_cache[key] = chosen;
   }
   return rc;
 }

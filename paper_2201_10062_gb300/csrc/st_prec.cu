@@ -927,6 +927,18 @@ cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *da
   return e;
 }
 
+cudaError_t tune_run_pass(const Geom &g, const PrecPlan &pp, int axis,
+                          const unsigned short *tc_img, float *data, State *S, cudaStream_t st) {
+  PrecPlan q = pp;
+  using A = SrcArray<float, float>;
+  if (axis == 1) {
+    q.sop_y = tc_img;
+    return dst_y_pass<float>(A{data}, data, g, q, S, GK_NONE, st);
+  }
+  q.sop_z = tc_img;
+  return dst_z_pass<float>(A{data}, data, g, q, S, GK_NONE, st);
+}
+
 cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
                           cudaStream_t st) {
   if (fp32)

@@ -81,3 +81,22 @@ def test_example2_ptheta_against_oracle(pkg, theta):
     _, st = s.st_solve(_d(fH), tol=1e-6, maxit=100)
     assert abs(st["iterations"] - info["iterations"]) <= 1, (st, info["iterations"])
     s.close()
+
+
+def test_table5_errors_on_gpu(pkg):
+    """Example 2's backward-Euler errors printed in Table 5 (m + 1 = 32, three digits), from the
+    GPU's float64 P_H solves at the paper's tolerance."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "table5_backward_euler.json")))
+    for n, ref in zip(g["n"], g["error"]):
+        w = W.paper_example2(g["m_plus_1"] - 1, n, 1.0)
+        s = pkg.Solver(pkg.ProblemSpec(2, w.mx, w.my, w.n, w.T, "theta", 1.0, w.a_nodal, "PH",
+                                       "fp64"))
+        fH = s.st_assemble_rhs(_d(w.f), _d(w.u0))
+        u, _ = s.st_solve(fH, tol=1e-6, maxit=100)
+        err = np.abs(u.cpu().numpy().reshape(w.n, w.m) - w.u_exact).max()
+        assert float(f"{err:.2e}") == ref, (n, err, ref)
+        s.close()

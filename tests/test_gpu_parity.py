@@ -411,9 +411,11 @@ def test_full_size_2d_varcoef_bdf2(pkg, precision):
                                   (1, 255, 1, 40, "bdf2", 1.0, True)],
                          ids=["2d-63x31-n65", "2d-127-n64", "1d-255-n40-bdf2"])
 def test_autotune_keeps_results(pkg, case, precision):
-    """The tuned knobs only change launch shapes: the operator and preconditioner outputs stay
-    bit-identical, and the solve still meets the oracle's residual with the same iteration count
-    up to one (the dot-product partial sums are grouped differently)."""
+    """The tuned knobs change launch shapes and, in float32, may move a preconditioner stage
+    between its tensor-core and CUDA-core kernels: the float64 operator and preconditioner
+    outputs stay bit-identical, the float32 preconditioner agrees to float32 accuracy (each engine
+    is within 2e-5 of the oracle), and the solve still meets the oracle's residual with the same
+    iteration count up to one (the dot-product partial sums are grouped differently)."""
     dim, mx, my, n, scheme, theta, var = case
     w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=77)
     p = H.Problem.from_workload(w)
@@ -428,7 +430,7 @@ def test_autotune_keeps_results(pkg, case, precision):
     s.st_autotune(reps=2)  # second call is served from the per-shape cache
     assert torch.equal(s.st_apply_op(v), op0)
     assert torch.equal(s.st_apply_prec(v), pr0)
-    assert torch.equal(s.st_apply_prec_f32(v), pf0)
+    assert _rel2(_h(s.st_apply_prec_f32(v)).astype(np.float64), _h(pf0).astype(np.float64)) <= 4e-5
     u1, st1 = s.st_solve(fH, tol=1e-9, maxit=600)
     assert abs(st1["iterations"] - st0["iterations"]) <= 1, (st0, st1)
     fH_or = H.rhs(p, w.f, w.u0, w.u_prev)
