@@ -493,7 +493,7 @@ struct st_handle {
   st::State *S;          // device scalars
   double *hbuf_in, *hbuf_out;  // device staging for st_solve_host
   double *gfx, *gfy;     // face-gradient scratch for st_grad_a
-  void *cheb;            // P_theta, 2D varying a: Chebyshev scalars and scratch vectors
+  void *cheb;            // P_theta, 2D/3D varying a: Chebyshev scalars and scratch vectors
   // the tensor-core operand images the handle was built with (the autotuner may switch a stage
   // to its CUDA-core kernel by clearing the plan's pointer; these keep the originals)
   const unsigned short *tc_time_img, *tc_y_img, *tc_z_img;

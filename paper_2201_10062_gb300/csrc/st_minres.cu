@@ -371,7 +371,7 @@ size_t table_floats(const Geom &g) {
   return spec + tw;
 }
 
-// Chebyshev steps of the 2D varying-a P_theta, 0 for every other preconditioner
+// Chebyshev steps of the 2D/3D varying-a P_theta, 0 for every other preconditioner
 int cheb_degree(const st_problem *p) {
   if (p->prec != ST_PREC_PTHETA || p->a_nodal == nullptr || p->dim < 2) return 0;
   return p->inner_degree > 0 ? p->inner_degree : ST_PTHETA_DEFAULT_DEGREE;

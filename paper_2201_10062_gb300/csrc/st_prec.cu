@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
-// ------------------------------------------------------------------------- P_theta, 2D a(x, y)
-// Step 2 of the P_theta apply (Sec. 3.1.4) when K is not sine-diagonalisable in 2D.  The paper
+// ---------------------------------------------------------------- P_theta, 2D/3D a(x, y[, z])
+// Step 2 of the P_theta apply (Sec. 3.1.4) when K is not sine-diagonalisable (2D, 3D).  The paper
 // leaves the solver of the shifted systems A_k = lam_H,k I + lam_Htheta,k tau K open; here each
 // one gets a fixed number of preconditioned Chebyshev steps (Saad, Iterative Methods for Sparse
 // Linear Systems, Alg. 12.1) with B_k = lam_H,k I + lam_Htheta,k tau abar K0 (K0 the a = 1
@@ -752,7 +752,7 @@ cudaError_t time_single(Tc *in, Tc *out, const Geom &g, const PrecPlan &pp, Stat
   return launch_time<Tc>(in, g, spec_of<Tc>(pp), S, TM_NONE, 1, partials, gk, Jo, st, out);
 }
 
-// P_theta with a varying 2D coefficient: time DST, pp.cheb Chebyshev steps per frequency, time
+// P_theta with a varying 2D/3D coefficient: time DST, pp.cheb Chebyshev steps per frequency, time
 // DST (see k_cheb_resid).  zc receives the source, then the transformed v, then the result (the
 // last step leaves its iterate in R, from which the inverse time DST writes zc).
 template <class Tc, class Src>
