@@ -314,7 +314,7 @@ struct PrecPlan {
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
   const unsigned short *sop_t1;  // fp16 S_n image for unscaled single time transforms on the
                                  // tensor cores (mixed P_theta with varying a), or null
-  // P_theta with varying a in 2D: Chebyshev steps per apply (0: not this path), the per-step,
+  // P_theta with varying a in 2D/3D: Chebyshev steps per apply (0: not this path), the per-step,
   // per-frequency scalars [cheb][n] (a: carry-over of the previous direction, s: factor of
   // B_k^-1 r), and five N-vectors of float64 scratch (used as the transform type: residual,
   // transformed residual, iterate, two directions)
