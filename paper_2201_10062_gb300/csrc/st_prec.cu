@@ -451,20 +451,25 @@ __device__ __forceinline__ float face_c<float>(const double *, const df *cd, lon
 // d_j = a_k d_{j-1} + w into dnext (its own buffer: the stencil reads neighbours of d_{j-1}),
 // x = x + d_j (x = d_j when first), r = rsrc - A_k d_j with tau K the 5-point (2D) or 7-point
 // (3D) stencil of the face coefficients cx, cy, cz (tau a / h^2).  r may alias rsrc.
+// Blocks of 32 x 8 nodes: x by threadIdx.x and blockIdx.y, the my*mz rows by threadIdx.y and
+// blockIdx.x, the frequency k by blockIdx.z, so no index is recovered by division.
+constexpr int kChebBX = 32, kChebBY = 8;
+
 template <class Tc>
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kChebBX * kChebBY)
     k_cheb_resid(Geom g, const Tc *__restrict__ dprev, const Tc *__restrict__ w,
                  Tc *__restrict__ dnext, const Tc *rsrc, Tc *r, Tc *__restrict__ x,
                  const Tc *__restrict__ acoef, const Tc *__restrict__ lh,
                  const Tc *__restrict__ lht, int first, const State *S, int gk) {
   if (gate_closed(S, gk)) return;
   const int mx = g.mx, my = g.my, mz = g.mz;
-  const long long m = g.m, pl = (long long)mx * my;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.N;
-       e += (long long)gridDim.x * blockDim.x) {
-    const unsigned ue = (unsigned)e;
-    const unsigned k = ue / (unsigned)m, rr = ue - k * (unsigned)m;
-    const int row = (int)(rr / (unsigned)mx), ix = (int)(rr - (unsigned)row * mx);
+  const int ix = blockIdx.y * kChebBX + threadIdx.x;
+  const int row = blockIdx.x * kChebBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (ix >= mx || row >= my * mz) return;
+  const long long pl = (long long)mx * my;
+  {
+    const long long e = (long long)k * g.m + (long long)row * mx + ix;
     const int jz = row / my, jy = row - jz * my;
     const Tc ak = first ? Tc(0) : acoef[k];
     auto dv = [&](long long q) -> Tc { return first ? w[q] : ak * dprev[q] + w[q]; };
@@ -798,9 +803,12 @@ cudaError_t cheb_stages(const Geom &g, const PrecPlan &pp, Src src, Tc *zc, Stat
     if ((e = yz_pass(W)) != cudaSuccess) return e;
     const Tc *aj = acoef + (size_t)j * g.n;
     if (j + 1 < pp.cheb) {
+      const dim3 rb(kChebBX, kChebBY);
+      const dim3 rg((unsigned)((g.my * g.mz + kChebBY - 1) / kChebBY),
+                    (unsigned)((g.mx + kChebBX - 1) / kChebBX), (unsigned)g.n);
       prof_begin(KC_TIME, st);
-      k_cheb_resid<Tc><<<kChebBlocks, kNT, 0, st>>>(g, Dd[cur], W, Dd[cur ^ 1], j == 0 ? zc : R, R,
-                                                    X, aj, sp.lh, sp.lht, j == 0 ? 1 : 0, S, gk);
+      k_cheb_resid<Tc><<<rg, rb, 0, st>>>(g, Dd[cur], W, Dd[cur ^ 1], j == 0 ? zc : R, R, X, aj,
+                                          sp.lh, sp.lht, j == 0 ? 1 : 0, S, gk);
       prof_end(st);
       cur ^= 1;
     } else {
