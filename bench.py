@@ -137,14 +137,23 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest per-rank value (the slowest rank's time) on every rank: an NCCL all-reduce on a
+    device scalar, or a host scalar under the gloo backend."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job unknowns/s of N independent replicas (weak scaling): every rank solves its own
+    copy, and the job takes as long as the slowest rank."""
+    return world * units_per_rank / seconds
 
 
 # ------------------------------------------------------------------------------ oracle legs
@@ -302,7 +311,7 @@ def run_ours(args, world, rank, local):
                 s.st_solve_host(fH_host, u_host, tol=TOL, maxit=400)
             t_e2e = (time.perf_counter() - t0) / e2e_steps
             t_e2e = max_over_ranks(t_e2e, world)
-            results["e2e"] = {"value": world * N / t_e2e, "unit": UNIT,
+            results["e2e"] = {"value": job_throughput(world, N, t_e2e), "unit": UNIT,
                               "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
                               "ms_per_step": t_e2e * 1e3}
         s.close()
@@ -340,7 +349,7 @@ def run_ours(args, world, rank, local):
                  for k, v in prof.items()}
     fp = results["fp64"]
     cpu = oracle_sample(seconds_budget=12.0)
-    value = world * N / (mixed["ms"] * 1e-3)
+    value = job_throughput(world, N, mixed["ms"] * 1e-3)
     line = {
         "metric": METRIC,
         "value": value,
@@ -368,7 +377,7 @@ def run_ours(args, world, rank, local):
         "roofline": roofline,
         "solve_hbm_frac": solve_frac,
         "kernels": per_class,
-        "fp64": {"value": world * N / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"],
+        "fp64": {"value": job_throughput(world, N, fp["ms"] * 1e-3), "ms_per_step": fp["ms"],
                  "iterations": fp["stats"]["iterations"], "true_rel_res": fp["stats"]["true_rel_res"],
                  "steps": fp["steps"], "clocks": fp["clocks"], "dtype": "f64",
                  "solve_hbm_frac": (ITER_BYTES["fp64"] * N * fp["stats"]["iterations"]
@@ -406,7 +415,7 @@ def _solve_leg(P, w, spec, stream, dev, world, reps):
     ms, (_, st) = _timed(stream, lambda: s.st_solve(fH, tol=TOL, maxit=600, out=u), reps)
     ms = max_over_ranks(ms, world)
     s.close()
-    return {"value": world * w.N / (ms * 1e-3), "ms_per_step": ms, "iterations": st["iterations"],
+    return {"value": job_throughput(world, w.N, ms * 1e-3), "ms_per_step": ms, "iterations": st["iterations"],
             "true_rel_res": st["true_rel_res"], "steps": reps}
 
 
@@ -434,7 +443,7 @@ def run_extra_workloads(P, W, stream, dev, world):
         s.st_solve(fH, tol=TOL, maxit=600, out=u)  # warm-up
         ms, (_, st) = _timed(stream, lambda: s.st_solve(fH, tol=TOL, maxit=600, out=u), reps)
         ms = max_over_ranks(ms, world)
-        res[precision] = {"value": world * w.N / (ms * 1e-3), "ms_per_step": ms,
+        res[precision] = {"value": job_throughput(world, w.N, ms * 1e-3), "ms_per_step": ms,
                           "iterations": st["iterations"], "true_rel_res": st["true_rel_res"],
                           "steps": reps}
         s.close()
@@ -494,14 +503,14 @@ def run_extra_workloads(P, W, stream, dev, world):
 
         ms, st = _timed(stream, one_by_one, 1)
         ms = max_over_ranks(ms, world)
-        seq[precision] = {"value": world * total / (ms * 1e-3), "ms_per_step": ms,
+        seq[precision] = {"value": job_throughput(world, total, ms * 1e-3), "ms_per_step": ms,
                           "iterations_total": sum(q["iterations"] for q in st)}
         for sv in solvers:
             sv.close()
     del fHs, outs
     out["batch_64_uneven"] = {
         "unit": UNIT, "instances": 64, "unknowns": total, "tol": TOL,
-        "graph": {"value": world * total / (ms_b * 1e-3), "ms_per_step": ms_b, "steps": 2,
+        "graph": {"value": job_throughput(world, total, ms_b * 1e-3), "ms_per_step": ms_b, "steps": 2,
                   "all_converged": ok, "iterations_total": sum(q["iterations"] for q in stats)},
         "one_by_one_mixed": seq["mixed"], "one_by_one_fp64": seq["fp64"],
     }

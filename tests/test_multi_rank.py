@@ -1,0 +1,59 @@
+"""The N > 1 host path of bench.py (replicas only, one process per GPU) with world size 2 on the
+gloo backend: the barrier, the maximum over ranks of the per-rank time, the whole-job value of
+weak-scaled replicas, and the reference arm, which rank 0 alone runs and prints."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, outdir):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    bench.barrier(world)
+    # per-rank times: the job is as slow as its slowest rank
+    t = bench.max_over_ranks(0.5 + rank, world)
+    value = bench.job_throughput(world, 1000, t)
+    bench.barrier(world)
+    with open(os.path.join(outdir, f"rank{rank}.json"), "w") as fh:
+        json.dump({"t": t, "value": value}, fh)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_the_slowest_time(tmp_path):
+    import torch.multiprocessing as mp
+
+    world, port = 2, _free_port()
+    mp.spawn(_worker, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    assert res[0]["t"] == res[1]["t"] == 1.5
+    assert res[0]["value"] == res[1]["value"] == 2 * 1000 / 1.5
+
+
+def test_reference_arm_prints_on_rank_zero_only(capsys):
+    """Rank 1 of the reference arm does no work and prints nothing."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        steps, warmup, gpus = 1, 0, 2
+
+    bench.run_reference(Args, world=2, rank=1)
+    assert capsys.readouterr().out == ""
