@@ -187,6 +187,17 @@ def test_space_order():
     assert abs(math.log2(e[0] / e[1]) - 2.0) < 0.1
 
 
+def test_space_order_3d():
+    """Second order in space on the 3D 7-point grid (Crank-Nicolson with many steps isolates the
+    spatial error): u = sin(pi x) sin(pi y) sin(pi z) e^t."""
+    e = []
+    for mx in (7, 15):
+        w = W.config_3d_sine(mx, 512, theta=0.5)
+        p = H.Problem.from_workload(w)
+        e.append(np.abs(H.march(p, w.f, w.u0) - w.u_exact).max())
+    assert abs(math.log2(e[0] / e[1]) - 2.0) < 0.1
+
+
 def test_table5_backward_euler_errors():
     """Example 2 errors printed in Table 5 (backward Euler, m+1 = 32), three digits."""
     g = json.load(open(os.path.join(GOLDEN, "table5_backward_euler.json")))
