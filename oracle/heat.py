@@ -35,8 +35,8 @@ Pins (tests/test_oracle_*.py) tie each function to something other than itself:
   * 3D (Sec. 5, Example 3): the 7-point K equals the Kronecker sum of 1D second
     differences for constant a and the face energy form for varying a; the 3D
     transform diagonalises it in the stated order; Y T symmetric, marching, the
-    block matrix of P_H^2 and the Chebyshev interval in 3D; the iteration counts of
-    Tables 6-7 within one.
+    block matrix of P_H^2 and the Chebyshev interval in 3D; second-order spatial
+    convergence on a manufactured 3D solution; the iteration counts of Tables 6-7 within one.
   * minres: the ideal preconditioner sqrt(T^T T) converges in at most two
     steps (Proposition absC); each iterate's preconditioned residual equals the
     brute-force least-squares minimum over the explicit Krylov basis; residual
