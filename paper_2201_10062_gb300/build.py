@@ -2,10 +2,13 @@
 
 Each .cu file compiles to an object in parallel, then one link step produces
 ``libstminres.so`` next to this file.  The CUDA runtime is linked statically so
-the library only needs the driver at load time.
+the library only needs the driver at load time.  Concurrent calls (one per rank of a
+multi-process run) are serialised by a file lock: the first one builds, the others
+find the library up to date.
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -33,6 +36,15 @@ def sources():
 
 def build(verbose: bool = False, extra_flags=None, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, extra_flags, force)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra_flags, force) -> str:
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     deps.append(os.path.join(HERE, "..", "include", "st_minres.h"))
