@@ -348,7 +348,8 @@ def run_ours(args, world, rank, local):
                      "share": (v["ms"] / total_ms if total_ms else None)}
                  for k, v in prof.items()}
     fp = results["fp64"]
-    cpu = oracle_sample(seconds_budget=12.0)
+    # the oracle baseline runs at N = 1 only (under torchrun the other ranks have already left)
+    cpu = oracle_sample(seconds_budget=12.0) if world == 1 else None
     value = job_throughput(world, N, mixed["ms"] * 1e-3)
     line = {
         "metric": METRIC,
@@ -382,7 +383,8 @@ def run_ours(args, world, rank, local):
                  "steps": fp["steps"], "clocks": fp["clocks"], "dtype": "f64",
                  "solve_hbm_frac": (ITER_BYTES["fp64"] * N * fp["stats"]["iterations"]
                                     / (peaks["hbm_gbs"] * 1e9)) / (fp["ms"] * 1e-3)},
-        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+                         if cpu is not None else None),
     }
     line.update(extra)
     print(json.dumps(line), flush=True)
