@@ -89,7 +89,8 @@ typedef struct st_problem {
                           /* 0 otherwise.  The map is symmetric positive definite at any     */
                           /* degree (its error polynomial stays below one on the spectrum).    */
   int mz;                 /* dim 3: interior points along z, mz+1 a power of two in [4, 1024]; */
-                          /* otherwise 0 or 1.  n*mx*my*mz must stay below 2^31.              */
+                          /* otherwise 0 or 1.  n*mx*my*mz must stay below 2^31, and in 3D    */
+                          /* my*mz at most 524,280 (the stencil grid's row axis).             */
 } st_problem;
 
 typedef struct st_stats {

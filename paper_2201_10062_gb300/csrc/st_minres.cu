@@ -261,6 +261,8 @@ int check_problem(const st_problem *p) {
     // element indices of a space-time vector stay below 2^31 (32-bit index arithmetic)
     const long long mz = (p->dim == 3) ? p->mz : 1;
     if ((long long)p->n * p->mx * p->my * mz > 2147483647LL) return ST_ERR_ARG;
+    // the stencil kernels put the my*mz rows, 8 per block, on the grid's second axis
+    if (p->dim == 3 && (long long)p->my * mz > 65535LL * 8) return ST_ERR_ARG;
   }
   if (!(p->T > 0.0) || !std::isfinite(p->T)) return ST_ERR_ARG;
   if (p->scheme != ST_THETA && p->scheme != ST_BDF2) return ST_ERR_ARG;

@@ -62,6 +62,7 @@ def _spec(**kw):
     dict(dim=1, my=1, prec="Ptheta", a_nodal=np.ones(17), inner_degree=2),
     dict(dim=3, mz=14), dict(dim=3, mz=1), dict(dim=4),
     dict(dim=3, mx=1023, my=1023, mz=1023, n=4),  # n*m beyond 2^31
+    dict(dim=3, mx=3, my=1023, mz=1023, n=2),  # my*mz beyond the stencil grid's row axis
 ])
 def test_setup_rejects_bad_problems_before_touching_the_gpu(lib, bad):
     from paper_2201_10062_gb300 import ST_ERR_ARG
