@@ -40,7 +40,11 @@ extern "C" {
 #define ST_ERR_CUDA 2           /* a CUDA runtime call or kernel launch failed              */
 #define ST_ERR_NOT_CONVERGED 3  /* maxit reached; the output holds the last iterate          */
 #define ST_ERR_BREAKDOWN 4      /* <v, P^-1 v> <= 0 or a non-finite Lanczos/Givens scalar     */
-#define ST_ERR_TIMEOUT 5        /* a device-side bounded wait gave up                       */
+#define ST_ERR_TIMEOUT 5        /* a device-side bounded wait gave up.  If a tensor-core    */
+                                /* kernel then could not confirm that its matrix operations  */
+                                /* had finished, it keeps its tensor memory rather than free */
+                                /* it under a running operation, and every later call on     */
+                                /* that device (st_setup included) returns ST_ERR_TIMEOUT.   */
 #define ST_ERR_OOM 6            /* device or pinned-host allocation failed                  */
 
 /* time discretisation */
@@ -204,14 +208,20 @@ void st_destroy_batch(st_batch *b);
  * is not acceptable, or hosts that give all device memory to their own arena up front.  This call
  * needs no handle and no cudaMalloc/cudaFree: its per-block partial sums live in a fixed static
  * __device__ array of 64 KB (room for 4096 blocks; every GPU that loads the library keeps it until
- * the process exits).  All valid st_problem sizes fit; anything else returns ST_ERR_ARG.
+ * the process exits).  It covers 1D and 2D problems only (every 1D/2D size st_setup accepts
+ * fits); a 3D problem, or a size beyond the array, returns ST_ERR_ARG.
  * prob: sizes, scheme, theta, T and stream (prob->a_nodal must be NULL); a_nodal_dev: device copy
- * of the nodal a grid (layout as st_problem.a_nodal) or NULL for a = 1; fH_dev, u_dev: N entries.
- * Outputs: r_dev (N entries, may be NULL) = Y f_H - Y T u; sums_dev[0] = ||r||^2 and
- * sums_dev[1] = ||f_H||^2 (two device doubles), both written on prob->stream.
+ * of the nodal a grid (layout as st_problem.a_nodal) or NULL for a = 1.  It must meet the same
+ * conditions as st_problem.a_nodal (finite, >= 0, every interior face value > 0) but, unlike
+ * st_setup, this call does not check them (reading the array would need a copy to the host):
+ * a field that breaks them gives a meaningless residual, not an error.  fH_dev, u_dev: N entries.
+ * Outputs: r_dev (N entries, may be NULL) = Y f_H - Y T u; it must not overlap fH_dev or u_dev
+ * (ST_ERR_ARG otherwise); sums_dev[0] = ||r||^2 and sums_dev[1] = ||f_H||^2 (two device doubles),
+ * both written on prob->stream.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call shares the
- * one array, so calls that overlap on the GPU (other streams, other host threads) race. */
+ * that device current; make that first call before any stream capture (a lookup that fails is
+ * retried by the next call).  Every call shares the one array, so calls that overlap on the GPU
+ * (other streams, other host threads) race. */
 int st_residual_noalloc(const st_problem *prob, const double *a_nodal_dev, const double *fH_dev,
                         const double *u_dev, double *r_dev, double *sums_dev);
 

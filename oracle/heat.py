@@ -41,6 +41,8 @@ Pins (tests/test_oracle_*.py) tie each function to something other than itself:
     steps (Proposition absC); each iterate's preconditioned residual equals the
     brute-force least-squares minimum over the explicit Krylov basis; residual
     estimate monotone; iteration counts of Tables 1-3 within +-2.
+  * forward_substitution: equals the sparse LU solve of the explicit all-at-once matrix on
+    tiny sizes and the sequential time stepping of march when f_H = rhs(f, u0).
   * adjoint_gradients: central finite differences of the forward solve.
 """
 from __future__ import annotations
@@ -423,11 +425,6 @@ def apply_prec(prob: Problem, v: np.ndarray) -> np.ndarray:
     return spatial_dst(prob, time_dst(prob, zt))
 
 
-def prec_energy(prob: Problem, v: np.ndarray) -> float:
-    """<v, P^{-1} v>, computed directly from the definition."""
-    return float(np.vdot(np.asarray(v).reshape(-1), apply_prec(prob, v).reshape(-1)))
-
-
 # --------------------------------------------------------------------------------------
 # Modified preconditioner P_theta (Sec. 1 eq. def:matrix_mod_P; Sec. 3.1.4)
 # --------------------------------------------------------------------------------------
@@ -786,6 +783,30 @@ def solve_transpose(prob: Problem, g: np.ndarray, tol: float = 1e-8, maxit: int 
     stop, state = true_residual_rule(Aop, g, tol)
     mu, info = minres(Aop, _prec_apply(prob, K), g, tol, maxit, stop=stop)
     return flip(mu, prob.n), info
+
+
+def forward_substitution(prob: Problem, fH: np.ndarray) -> np.ndarray:
+    """Direct solve of T u = f_H (the reference solution of the all-at-once system, Sec. 1).
+
+    T is block lower triangular and Toeplitz with the blocks of time_blocks (eq. theta; Sec. 4
+    for BDF2), so block row k reads A0 u_k + A1 u_{k-1} (+ A2 u_{k-2}) = f_H,k and the unknown
+    blocks follow one after the other: u_k = A0^{-1} (f_H,k - A1 u_{k-1} - A2 u_{k-2}), with one
+    sparse LU factorisation of the SPD block A0.  For f_H = rhs(f, u0) this is the sequential
+    time stepping of march; for any other f_H (e.g. one with added noise) it is still exact up
+    to the rounding of the LU solves.
+    """
+    n, m = prob.n, prob.m
+    A = time_blocks(prob)
+    F = np.asarray(fH, dtype=np.float64).reshape(n, m)
+    lu = spla.splu(A[0].tocsc())
+    U = np.zeros((n, m))
+    for k in range(n):
+        r = F[k].copy()
+        for d in range(1, len(A)):
+            if k - d >= 0:
+                r -= A[d] @ U[k - d]
+        U[k] = lu.solve(r)
+    return U
 
 
 def march(prob: Problem, f: np.ndarray, u0: np.ndarray, u_prev: Optional[np.ndarray] = None):

@@ -45,7 +45,7 @@ __global__ void k_df_to_double_gated(long long N, const df *__restrict__ src,
 
 struct BatchInfo {
   double rho, est;
-  int done, status, total, outer;
+  int done, status, total, outer, tmem_held;
 };
 
 __global__ void k_gather(State *const *states, int count, BatchInfo *out) {
@@ -59,6 +59,7 @@ __global__ void k_gather(State *const *states, int count, BatchInfo *out) {
   b.status = S->status;
   b.total = S->total;
   b.outer = S->outer;
+  b.tmem_held = S->tmem_held;
   out[i] = b;
 }
 
@@ -254,6 +255,7 @@ int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_d
   for (int i = 0; i < b->count; ++i)
     if (!fH_devs[i] || !u_devs[i] || fH_devs[i] == u_devs[i]) return ST_ERR_ARG;
   BT_TRY(cudaSetDevice(b->device));
+  if (device_closed(b->device)) return ST_ERR_TIMEOUT;
   // start of every instance (regular launches on the instance streams, after the caller's work)
   BT_TRY(cudaEventRecord(b->fork, b->stream));
   for (int i = 0; i < b->count; ++i) {
@@ -269,7 +271,7 @@ int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_d
     S.maxit = maxit;
     S.inner_floor = inner_floor();
     S.target = std::max(0.5 * tol, S.inner_floor);
-    BT_TRY(cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, s));
+    BT_TRY(cudaMemcpyAsync(h->S, h->hS, kStatePushBytes, cudaMemcpyHostToDevice, s));
     BT_TRY(cudaMemsetAsync(h->Xdf, 0, g.N * sizeof(df), s));
     BT_TRY(cudaMemsetAsync(u_devs[i], 0, g.N * sizeof(double), s));
     BT_TRY(cudaMemsetAsync(h->D[0], 0, g.N * sizeof(df), s));
@@ -301,7 +303,13 @@ int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_d
                            cudaMemcpyDeviceToHost, b->cstream));
     BT_TRY(cudaStreamSynchronize(b->cstream));
     all_done = true;
-    for (int i = 0; i < b->count; ++i) all_done = all_done && b->h_info[i].done;
+    for (int i = 0; i < b->count; ++i) {
+      all_done = all_done && b->h_info[i].done;
+      if (b->h_info[i].tmem_held) {
+        close_device(b->device);
+        return ST_ERR_TIMEOUT;
+      }
+    }
   }
   // later work on the caller's stream sees the solutions
   BT_TRY(cudaEventRecord(b->done_ev, b->cstream));

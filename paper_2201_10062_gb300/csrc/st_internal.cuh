@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/st_minres.h"
@@ -109,7 +110,15 @@ struct State {
   // double-float copies of the per-iteration scalars, refreshed by whoever sets the float64
   // values, so that the double-float vector kernels read them without float64 instructions
   df dfs[8];
+  // Set (never cleared on the device) by a tensor-core kernel whose bounded waits ran out twice,
+  // so that it exited without releasing its tensor memory (an MMA might still have been writing
+  // it).  It is the last member: the host pushes the state up to it (kStatePushBytes) and so
+  // never overwrites it; once the host reads it set, the device is closed to further calls.
+  int tmem_held;
 };
+
+// bytes of State the host writes to the device: everything before tmem_held
+constexpr size_t kStatePushBytes = offsetof(State, tmem_held);
 
 enum { DFS_IB = 0, DFS_LA, DFS_LB, DFS_DZ, DFS_D1, DFS_D2, DFS_XC };
 
@@ -328,6 +337,11 @@ struct PrecPlan {
 // 1e-7, where the float32 preconditioner still lets the estimate fall steadily (ST_INNER_FLOOR
 // overrides it, for measurements).
 double inner_floor();
+
+// A device on which a tensor-core kernel kept its tensor memory after a timeout is closed: every
+// later call there returns ST_ERR_TIMEOUT (the host learns it from State::tmem_held).
+void close_device(int dev);
+bool device_closed(int dev);
 
 bool time_tc_supported(int n);
 size_t time_tc_sop_halves(int n);

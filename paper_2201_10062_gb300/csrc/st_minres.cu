@@ -13,6 +13,7 @@
 // iterations to learn whether the device-side stopping test has fired, and sizes the next chunk
 // from the observed convergence rate.  Kernels launched after that point return at entry.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -137,6 +138,22 @@ __global__ void k_df_to_double(long long N, const df *__restrict__ src, double *
     dst[e] = df_to_double(src[e]);
 }
 }  // namespace
+
+// Devices on which a tensor-core kernel had to exit without releasing its tensor memory (see
+// State::tmem_held): a later kernel that allocates tensor memory there could wait for it forever,
+// so every call on such a device returns ST_ERR_TIMEOUT for the rest of the process.
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_device_closed[kMaxDevices];
+}  // namespace
+
+void close_device(int dev) {
+  if (dev >= 0 && dev < kMaxDevices) g_device_closed[dev].store(1);
+}
+
+bool device_closed(int dev) {
+  return dev >= 0 && dev < kMaxDevices && g_device_closed[dev].load() != 0;
+}
 
 double inner_floor() {
   static const double f = [] {
@@ -319,6 +336,13 @@ int map_cuda(cudaError_t e) {
   do {                                    \
     cudaError_t _e = (expr);              \
     if (_e != cudaSuccess) return map_cuda(_e); \
+  } while (0)
+
+// start of a call on handle h: its device current, and not closed (see close_device)
+#define ST_ENTER(h)                                         \
+  do {                                                      \
+    ST_TRY(cudaSetDevice((h)->device));                     \
+    if (device_closed((h)->device)) return ST_ERR_TIMEOUT;  \
   } while (0)
 
 // Enough per-block partial sums for every launch shape the autotuner may pick: the stencil with
@@ -824,12 +848,17 @@ cudaError_t launch_iteration_mixed(st_handle *h, int k) {
 int sync_state(st_handle *h) {
   ST_TRY(cudaMemcpyAsync(h->hS, h->S, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
   ST_TRY(cudaStreamSynchronize(h->stream));
+  if (h->hS->tmem_held) {
+    close_device(h->device);
+    return ST_ERR_TIMEOUT;
+  }
   return ST_OK;
 }
 
+// the device keeps tmem_held: only the members before it are written
 int push_state(st_handle *h) {
   refresh_df(h->hS);
-  ST_TRY(cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, h->stream));
+  ST_TRY(cudaMemcpyAsync(h->S, h->hS, kStatePushBytes, cudaMemcpyHostToDevice, h->stream));
   return ST_OK;
 }
 
@@ -1071,7 +1100,7 @@ int st_version(void) { return 1; }
 
 int st_profile_begin(st_handle *h, int capacity) {
   if (!h || capacity < 1 || capacity > (1 << 20)) return ST_ERR_ARG;
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   prof_free(h->prof);
   Prof &p = h->prof;
   std::memset(p.launches, 0, sizeof(p.launches));
@@ -1100,7 +1129,7 @@ int st_profile_begin(st_handle *h, int capacity) {
 
 int st_profile_end(st_handle *h, st_kernel_time *out, int nclasses) {
   if (!h || !out || nclasses < 1) return ST_ERR_ARG;
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   Prof &p = h->prof;
   if (!p.ev) return ST_ERR_ARG;
   ST_TRY(cudaStreamSynchronize(h->stream));
@@ -1132,7 +1161,7 @@ std::map<std::tuple<int, int, int, int, int, int, int>, Knobs> g_tune_cache;
 
 int st_autotune(st_handle *h, int reps) {
   if (!h || reps < 1 || reps > 100) return ST_ERR_ARG;
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   const bool fp32 = h->mixed;
   const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.mz, h->g.n, (int)fp32,
                                    (h->tc_time_img ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
@@ -1190,7 +1219,7 @@ int st_autotune(st_handle *h, int reps) {
     s.inv_beta = 1.0;
     refresh_df(&s);
     *h->hS = s;
-    cudaMemcpyAsync(h->S, h->hS, sizeof(State), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(h->S, h->hS, kStatePushBytes, cudaMemcpyHostToDevice, st);
     float best = 1e30f;
     int bt = 0;
     for (int t : cand) {
@@ -1321,6 +1350,10 @@ int st_setup(const st_problem *prob, st_handle **out) {
     delete h;
     return ST_ERR_CUDA;
   }
+  if (device_closed(h->device)) {
+    delete h;
+    return ST_ERR_TIMEOUT;
+  }
   const Geom g = h->g;
   const size_t N = (size_t)g.N;
   auto fail = [&](int code) {
@@ -1380,7 +1413,7 @@ int st_assemble_rhs(st_handle *h, const double *f_dev, const double *u0_dev,
                     const double *uprev_dev, const double *extra_dev, double *fH_dev) {
   if (!h || !f_dev || !u0_dev || !fH_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY(launch_rhs(h->g, f_dev, u0_dev, uprev_dev, extra_dev, fH_dev, h->stream));
   return ST_OK;
 }
@@ -1388,7 +1421,7 @@ int st_assemble_rhs(st_handle *h, const double *f_dev, const double *u0_dev,
 int st_apply_op(st_handle *h, const double *v_dev, double *y_dev) {
   if (!h || !v_dev || !y_dev || v_dev == y_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY(launch_stencil<double>(h->g, SM_APPLY, v_dev, y_dev, nullptr, h->S, h->partials, 0,
                                 h->stream));
   return ST_OK;
@@ -1397,7 +1430,7 @@ int st_apply_op(st_handle *h, const double *v_dev, double *y_dev) {
 int st_apply_prec(st_handle *h, const double *v_dev, double *z_dev) {
   if (!h || !v_dev || !z_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY((launch_prec<double, double, double>(h->g, h->pp, v_dev, z_dev, h->S, TM_NONE,
                                               h->partials, h->stream)));
   return ST_OK;
@@ -1406,7 +1439,7 @@ int st_apply_prec(st_handle *h, const double *v_dev, double *z_dev) {
 int st_apply_prec_f32(st_handle *h, const double *v_dev, float *z_dev) {
   if (!h || !v_dev || !z_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY((launch_prec<float, double, float>(h->g, h->pp, v_dev, z_dev, h->S, TM_NONE,
                                             h->partials, h->stream)));
   return ST_OK;
@@ -1416,7 +1449,7 @@ int st_solve(st_handle *h, const double *fH_dev, double *u_dev, double tol, int 
              st_stats *stats) {
   if (!h || !fH_dev || !u_dev || fH_dev == u_dev || !(tol >= 0.0) || maxit < 1) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   const double t0 = now_s();
   st_stats local{};
   int r = h->mixed ? solve_mixed(h, fH_dev, u_dev, tol, maxit, &local)
@@ -1435,7 +1468,7 @@ int st_solve_host(st_handle *h, const double *fH_host, double *u_host, double to
                   st_stats *stats) {
   if (!h || !fH_host || !u_host) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   const double t0 = now_s();
   const size_t bytes = (size_t)h->g.N * sizeof(double);
   ST_TRY(cudaMemcpyAsync(h->hbuf_in, fH_host, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -1455,7 +1488,7 @@ int st_solve_transpose(st_handle *h, const double *g_dev, double *lam_dev, doubl
                        st_stats *stats) {
   if (!h || !g_dev || !lam_dev || g_dev == lam_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   // (Y T) mu = g is st_solve with f_H = Y g; then lam = Y mu.
   ST_TRY(launch_flip(h->g, g_dev, h->hbuf_in, h->stream));
   int r = st_solve(h, h->hbuf_in, lam_dev, tol, maxit, stats);
@@ -1470,7 +1503,7 @@ int st_grad_rhs(st_handle *h, const double *lam_dev, double *grad_f_dev, double 
                 double *grad_uprev_dev) {
   if (!h || !lam_dev || !grad_f_dev) return ST_ERR_ARG;
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY(launch_grad_rhs(h->g, lam_dev, grad_f_dev, grad_u0_dev, grad_uprev_dev, h->stream));
   return ST_OK;
 }
@@ -1480,7 +1513,7 @@ int st_grad_a(st_handle *h, const double *lam_dev, const double *u_dev, const do
   if (!h || !lam_dev || !u_dev || !u0_dev || !grad_dev) return ST_ERR_ARG;
   if (h->g.dim == 3) return ST_ERR_ARG;  // the face gradient is written for 1D and 2D grids
   ProfScope prof_scope(h);
-  ST_TRY(cudaSetDevice(h->device));
+  ST_ENTER(h);
   ST_TRY(launch_grad_a(h->g, lam_dev, u_dev, u0_dev, h->gfx, h->gfy, grad_dev, h->stream));
   return ST_OK;
 }

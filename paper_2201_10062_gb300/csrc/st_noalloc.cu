@@ -22,23 +22,37 @@ constexpr int kMaxBlocks = 4096;  // capacity of the static scratch (partial sum
 static __device__ __align__(256) double g_scratch[2 * kMaxBlocks + 32];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
+void *g_scratch_addr[kMaxDevices];  // resolved device address per device (null: not yet)
+std::mutex g_scratch_mu;
 
 // The array's name is a host-side stand-in in host code; the device address comes from the
-// runtime, once per device, with that device current.
+// runtime, per device, with that device current.  Only a successful lookup is kept: a lookup
+// that failed (for instance one made while a stream was being captured) is tried again by the
+// next call.
 cudaError_t scratch_for_current_device(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_scratch_once[dev], [dev] {
-    g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_addr[dev], g_scratch);
-  });
-  if (g_scratch_err[dev] != cudaSuccess) return g_scratch_err[dev];
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // the failed lookup must not surface in a later, unrelated check
+      return e;
+    }
+    g_scratch_addr[dev] = p;
+  }
   *out = static_cast<double *>(g_scratch_addr[dev]);
   return cudaSuccess;
+}
+
+// [a, a + n) and [b, b + n) share an element
+bool overlaps(const double *a, const double *b, long long n) {
+  const char *pa = reinterpret_cast<const char *>(a), *pb = reinterpret_cast<const char *>(b);
+  const long long bytes = n * (long long)sizeof(double);
+  return pa < pb + bytes && pb < pa + bytes;
 }
 
 __device__ __forceinline__ double anode(const double *a, int dim, int mx, int J, int I) {
@@ -160,6 +174,9 @@ extern "C" int st_residual_noalloc(const st_problem *prob, const double *a_nodal
   g.scheme = prob->scheme;
   g.tau = prob->T / prob->n;
   g.theta = (prob->scheme == ST_THETA) ? prob->theta : 1.0;
+  // every block reads f_H and u across time levels while other blocks write r: an r that shares
+  // memory with either input would be read after it has been overwritten
+  if (r_dev && (overlaps(r_dev, fH_dev, g.N) || overlaps(r_dev, u_dev, g.N))) return ST_ERR_ARG;
   dim3 block = (g.dim == 1) ? dim3(256, 1) : dim3(32, 8);
   const int gx = (g.mx + (int)block.x - 1) / (int)block.x;
   const int gy = (g.my + (int)block.y - 1) / (int)block.y;

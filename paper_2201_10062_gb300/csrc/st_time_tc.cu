@@ -18,7 +18,11 @@
 // swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the mbarrier, and
 // every warp reads 32 rows x 16 columns of one parity's accumulators with tcgen05.ld.  Every
 // wait on an mbarrier is bounded; on timeout the block records ST_ERR_TIMEOUT in the MINRES
-// state and stops.
+// state and stops.  Before it releases its tensor memory it gives every MMA batch whose commit
+// it has not seen complete one more bounded wait: MMAs still in flight may be writing that
+// memory.  If that wait runs out as well, the block keeps the memory (it is never handed to
+// another block while an MMA may write it) and sets State::tmem_held, which closes the device to
+// further calls on the host side.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -112,6 +116,37 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+
+// End of a tensor-core block: after a timeout (ok false), one more bounded wait on each commit
+// barrier whose last wait ran out (pendN, waited with phase phN).  Tensor memory is released only
+// when every MMA batch has completed and no other asynchronous copy is left in flight
+// (copies_done, uniform); otherwise the block records that it keeps it.  The decision is uniform
+// across the block (one __syncthreads_and); warp 0 releases COLS columns at tmem.
+template <int COLS>
+__device__ __forceinline__ void tc_release_cols(bool ok, bool pend1, uint32_t mbar1, uint32_t ph1,
+                                                bool pend2, uint32_t mbar2, uint32_t ph2,
+                                                uint32_t tmem, State *S, bool copies_done = true) {
+  bool drained = true;
+  if (!ok) {
+    // every thread waits (bounded) on the barriers that still owe a completion; the results are
+    // combined so that the whole block takes the same decision
+    bool d = copies_done;
+    if (pend1) d = mbar_wait(mbar1, ph1) && d;
+    if (pend2) d = mbar_wait(mbar2, ph2) && d;
+    drained = __syncthreads_and(d ? 1 : 0) != 0;
+    if (threadIdx.x == 0) {
+      S->status = ST_ERR_TIMEOUT;
+      if (!drained) atomicExch(&S->tmem_held, 1);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (drained && (threadIdx.x >> 5) == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(COLS)
+                 : "memory");
+  }
+}
 
 // Shared-memory layout, offsets in bytes from the dynamic base.
 struct TcSmem {
@@ -385,6 +420,8 @@ __global__ void __launch_bounds__(kNT, 1)
   const uint32_t dcol1 = tmem, dcol2 = tmem + 2u * kTN;  // 64 accumulator columns each
   uint32_t ph1 = 0, ph2 = 0;
   bool ok = true;
+  // a commit to mbar1 / mbar2 whose completion has not been seen (its phase is ph1 / ph2)
+  bool out1 = false, out2 = false;
   float esum = 0.f, ecomp = 0.f;
   // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
   const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
@@ -400,6 +437,8 @@ __global__ void __launch_bounds__(kNT, 1)
   auto finish_second = [&](long long pj0, int pje) {
     const bool w = __syncthreads_and(mbar_wait(mbar2, ph2) ? 1 : 0) != 0;
     ok = ok && w;
+    if (!w) return;  // uniform: the accumulators may still be written; nothing is read
+    out2 = false;
     ph2 ^= 1u;
     fence_after();
     float v[16];
@@ -451,6 +490,7 @@ __global__ void __launch_bounds__(kNT, 1)
     __syncthreads();
     fence_after();
     if (tid == 0) issue_mmas(smem, L, L.bop1, h, dcol1, mbar1);
+    out1 = true;
     if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
     // 2. while the first transform runs: finish the previous tile
     if (pend) finish_second(pj0, pje);
@@ -458,7 +498,9 @@ __global__ void __launch_bounds__(kNT, 1)
     {
       const bool w = __syncthreads_and(mbar_wait(mbar1, ph1) ? 1 : 0) != 0;
       ok = ok && w;
+      if (!w) break;  // uniform; the commit stays outstanding for the release below
     }
+    out1 = false;
     ph1 ^= 1u;
     fence_after();
     {
@@ -490,17 +532,12 @@ __global__ void __launch_bounds__(kNT, 1)
     fence_after();
     if (tid == 0 && ok) issue_mmas(smem, L, L.bop2, h, dcol2, mbar2);
     pend = ok;
+    out2 = out2 || ok;
     pj0 = j0;
     pje = je;
   }
-  if (pend) finish_second(pj0, pje);
-  if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
-  }
+  if (pend && ok) finish_second(pj0, pje);
+  tc_release_cols<128>(ok, out1, mbar1, ph1, out2, mbar2, ph2, tmem, S);
   if (tmode != TM_NONE) {
     const double e = (double)esum - (double)ecomp;
     double tot;
@@ -578,6 +615,7 @@ __global__ void __launch_bounds__(kNT, 1)
   const uint32_t tmem = *tmem_slot;
   uint32_t phase = 0;
   bool ok = true;
+  bool outstanding = false;  // a commit to mbar whose completion has not been seen
   // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
   const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
   const int r = (q << 5) + lane;
@@ -597,9 +635,12 @@ __global__ void __launch_bounds__(kNT, 1)
     __syncthreads();
     fence_after();
     if (tid == 0) issue_mmas(smem, L, L.bop1, h, tmem, mbar);
+    outstanding = true;
     // the stage buffer is free: load the next tile while the tensor cores work
     if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
     ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
+    if (!ok) break;  // uniform; the commit stays outstanding for the release below
+    outstanding = false;
     phase ^= 1u;
     fence_after();
     float v[16];
@@ -618,13 +659,7 @@ __global__ void __launch_bounds__(kNT, 1)
     }
   }
   cp_async_wait_all();
-  if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
-  }
+  tc_release_cols<64>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
 }
 
 // ------------------------------------------------------------------ long time axes (n > 256)
@@ -749,11 +784,13 @@ __device__ __forceinline__ void build_b_long(unsigned char *smem, const Tc2Smem 
 }
 
 // Issued by one thread: one transform (16 streamed A chunks x 4 K steps x 3 products into the
-// four accumulators), then a commit to `done`.  The ring phases persist across calls.  Returns
-// false if a wait ran out (the caller records the timeout).
+// four accumulators), then a commit to `done`, which tracks every MMA issued before it.  The ring
+// phases persist across calls.  Returns false if a wait ran out (the caller records the
+// timeout); *fills_drained is false if, after such a timeout, a bulk copy into the ring could
+// still be in flight.
 __device__ __forceinline__ bool stream_mmas(unsigned char *smem, const Tc2Smem &L,
                                             const unsigned char *A_g, uint32_t tmem,
-                                            uint32_t *fph, uint32_t *eph) {
+                                            uint32_t *fph, uint32_t *eph, bool *fills_drained) {
   const uint32_t full0 = smem_u32(smem + L.mbar), empty0 = full0 + 16, done = full0 + 32;
   const uint32_t ring = smem_u32(smem + L.ring), bbase = smem_u32(smem + L.bop);
   const uint32_t bpiece = (uint32_t)kTN * kKP2 * 2u;
@@ -810,7 +847,7 @@ __device__ __forceinline__ bool stream_mmas(unsigned char *smem, const Tc2Smem &
   } else {
     // after a timeout: wait (bounded) for copies still in flight before the block moves on
     for (int sl = 0; sl < 2; ++sl)
-      if (pending[sl] > 0) mbar_wait(full0 + 8u * sl, fph[sl]);
+      if (pending[sl] > 0 && !mbar_wait(full0 + 8u * sl, fph[sl])) *fills_drained = false;
   }
   mma_commit(done);
   return ok;
@@ -855,6 +892,8 @@ __global__ void __launch_bounds__(kNT, 1)
   const uint32_t tmem = *tmem_slot;
   uint32_t fph[2] = {0u, 0u}, eph[2] = {0u, 0u}, dph = 0u;  // phases (used by thread 0)
   bool ok = true;
+  bool out_done = false;      // a commit to `done` whose completion has not been seen
+  bool fills_drained = true;  // thread 0: no bulk copy into the ring left in flight
   float esum = 0.f, ecomp = 0.f;
   // accumulator view: TMEM lanes 32q.. (rows r = mt*128 + 32q + lane), parity P, columns 16ch..
   const int qq = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
@@ -872,9 +911,13 @@ __global__ void __launch_bounds__(kNT, 1)
     __syncthreads();
     fence_after();
     bool w = true;
-    if (tid == 0) w = stream_mmas(smem, L, A_g, tmem, fph, eph);
-    const bool d = mbar_wait(done, dph);
-    dph ^= 1u;
+    if (tid == 0) w = stream_mmas(smem, L, A_g, tmem, fph, eph, &fills_drained);
+    const bool d = __syncthreads_and(mbar_wait(done, dph) ? 1 : 0) != 0;
+    if (d) {
+      dph ^= 1u;
+    } else {
+      out_done = true;
+    }
     ok = (__syncthreads_and((w && d) ? 1 : 0) != 0) && ok;
     fence_after();
   };
@@ -896,6 +939,7 @@ __global__ void __launch_bounds__(kNT, 1)
                  },
                  tid);
     run_mmas();
+    if (!ok) break;  // uniform
     // unscale, spectral scaling, energy; Y into the parity-split tile
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -923,6 +967,7 @@ __global__ void __launch_bounds__(kNT, 1)
     fence_after();
     build_b_long(smem, L, L.colinv2, n, [&](int t, int c) -> float { return ycell(t, c); }, tid);
     run_mmas();
+    if (!ok) break;  // uniform
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
       float v[16];
@@ -943,13 +988,10 @@ __global__ void __launch_bounds__(kNT, 1)
     }
     __syncthreads();
   }
-  if (!ok && tid == 0) S->status = ST_ERR_TIMEOUT;
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
-  }
+  // a bulk copy that may still land in the ring keeps the block from handing its resources back
+  // as well: it counts as an outstanding completion
+  const bool fills_ok = __syncthreads_and(fills_drained ? 1 : 0) != 0;
+  tc_release_cols<128>(ok, out_done, done, dph, false, 0u, 0u, tmem, S, fills_ok);
   if (tmode != TM_NONE) {
     const double e = (double)esum - (double)ecomp;
     double tot;

@@ -110,3 +110,42 @@ def test_adjoint_workload_finite_differences(pkg, precision):
         fd = (loss_of(*fp) - loss_of(*fm)) / (2 * eps)
         ad = float((g * dd).sum())
         assert abs(fd - ad) <= 1e-5 * abs(ad), (name, fd, ad)
+
+
+def _sampled_rel(u, d):
+    idx = np.asarray(d["idx"])
+    ref = np.asarray(d["val"])
+    return float(np.linalg.norm(np.asarray(u).reshape(-1)[idx] - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_workload_against_oracle_direct_solves(pkg, precision):
+    """The adjoint workload at full size (2D 255^2 x 256, backward Euler): forward solution,
+    adjoint lam = T^-T (u - u_obs) and the f, u0 and a gradients of L = 1/2 ||u - u_obs||^2,
+    each against the oracle's direct solves (tests/golden/oracle_digest.json, sampled at seeded
+    indices), relative error <= 1e-8 with both solves at a true relative residual of 1e-10."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "oracle_digest.json")) as fh:
+        d = json.load(fh)["workloads"]["adjoint_255_n256"]
+    w = W.config_adjoint()
+    p_true = H.Problem.from_workload(w)
+    u_true = H.march(p_true, w.f, w.u0)
+    u_obs = u_true + 0.01 * np.sqrt(np.mean(u_true ** 2)) * w.extra["obs_normal"]
+    a_eval = 0.5 * (w.a_nodal + 1.0)
+    spec = pkg.ProblemSpec(2, w.mx, w.my, w.n, w.T, "theta", 1.0, a_eval, "PH", precision)
+    s = pkg.Solver(spec)
+    fH = s.st_assemble_rhs(_d(w.f), _d(w.u0))
+    u, st = s.st_solve(fH, tol=1e-10, maxit=800)
+    lam, st2 = s.st_solve_transpose(u - _d(u_obs).reshape(-1), tol=1e-10, maxit=800)
+    gf, gu0, _ = s.st_grad_rhs(lam)
+    ga = s.st_grad_a(lam, u, _d(w.u0))
+    got = {"u": u, "lam": lam, "grad_f": gf, "grad_u0": gu0, "grad_a": ga}
+    for k, v in got.items():
+        err = _sampled_rel(v.detach().cpu().numpy(), d[k])
+        assert err <= 1e-8, (precision, k, err)
+    loss = 0.5 * float(((u - _d(u_obs).reshape(-1)) ** 2).sum())
+    assert abs(loss - d["loss"]) <= 1e-8 * d["loss"]
+    s.close()

@@ -159,6 +159,26 @@ def test_all_at_once_equals_time_marching(dim, scheme, theta):
     assert np.allclose(u_direct, u_march, rtol=1e-11, atol=1e-11)
 
 
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("scheme,theta", [("theta", 1.0), ("theta", 0.5), ("theta", 0.3), ("bdf2", 1.0)])
+def test_forward_substitution_is_the_direct_solve(dim, scheme, theta):
+    """The block forward substitution solves T u = f_H exactly for any f_H: it equals the sparse
+    LU solve of the explicit all-at-once matrix (Sec. 1) for an arbitrary right-hand side, and the
+    sequential time stepping for f_H = rhs(f, u0).  A dropped block, a sign error on A1 or A2 or
+    a wrong block index fails the first comparison."""
+    w, p = _tiny(dim, scheme, theta=theta, mx=5, my=4, n=7)
+    T = H.all_at_once_matrix(p).tocsc()
+    g = np.random.default_rng(8).standard_normal((p.n, p.m))
+    ref = spla.spsolve(T, g.reshape(-1)).reshape(p.n, p.m)
+    assert np.allclose(H.forward_substitution(p, g), ref, rtol=1e-11, atol=1e-11)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    assert np.allclose(H.forward_substitution(p, fH), H.march(p, w.f, w.u0, w.u_prev),
+                       rtol=1e-11, atol=1e-11)
+    # the transposed system through T^T = Y T Y: lam = Y T^-1 Y g
+    lam = H.flip(H.forward_substitution(p, H.flip(g, p.n)), p.n)
+    assert np.allclose(T.T @ lam.reshape(-1), g.reshape(-1), rtol=1e-10, atol=1e-10)
+
+
 def _error_1d(scheme, theta, mx, n):
     if scheme == "bdf2":
         w = W.config_1d_sine(mx, n, theta=1.0)
