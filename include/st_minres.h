@@ -230,8 +230,9 @@ int st_residual_noalloc(const st_problem *prob, const double *a_nodal_dev, const
  * counted).  st_profile_end synchronises the stream, writes per-class totals for classes
  * 0..nclasses-1 (ST_KC_* below) and stops profiling. */
 #define ST_KC_STENCIL 0  /* flipped space-time stencil                                        */
-#define ST_KC_LANCZOS 1  /* Lanczos three-term update                                         */
-#define ST_KC_DSTX 2     /* spatial DST along x                                               */
+#define ST_KC_LANCZOS 1  /* Lanczos three-term update fused into the first spatial DST along */
+                         /* x of the preconditioner pass (that whole launch)                  */
+#define ST_KC_DSTX 2     /* spatial DST along x (the other launches)                          */
 #define ST_KC_DSTY 3     /* spatial DST along y                                               */
 #define ST_KC_TIME 4     /* time DST, spectral scaling, time DST                              */
 #define ST_KC_UPDATE 5   /* MINRES direction / solution update                                */

@@ -31,7 +31,7 @@ EXPORTS = (
     "st_kernel_class_name", "st_residual_noalloc", "st_grad_rhs", "st_setup_batch",
     "st_solve_batch", "st_batch_instance", "st_destroy_batch", "st_autotune",
 )
-KERNEL_CLASSES = ("stencil", "lanczos", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
+KERNEL_CLASSES = ("stencil", "lanczos_dst_x", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
 
 

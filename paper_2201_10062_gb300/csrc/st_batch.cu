@@ -1,14 +1,17 @@
 // Batched mixed-precision solves: many independent instances of uneven size (mx, my, n, theta,
-// a(x)) run concurrently, one stream each, and the whole iteration is captured into one CUDA graph
-// that the host relaunches until every instance reports done.
+// a(x)) run concurrently in one CUDA graph, launched once per solve.
 //
-// A graph segment of one instance is two MINRES iterations (even and odd buffer parity) followed
-// by a refinement block: convert the double-float x to float64, recompute the float64 residual,
-// and let the residual kernel's last block decide (done, or restart the inner run with the
-// residual as right-hand side).  A restart zeroes the direction buffers and re-initialises the
-// inner run through a preconditioner pass gated on the state's `restart` flag, so the next
-// segment starts again at even parity.  Kernels of finished or idle instances return at entry;
-// no host decision sits inside the graph.
+// The graph holds one conditional WHILE node per instance; the nodes have no dependencies, so the
+// instances run side by side.  The body of instance i is two MINRES iterations (even and odd
+// buffer parity) followed by a refinement block: convert the double-float x to float64,
+// recompute the float64 residual, and let the residual kernel's last block decide (done, or
+// restart the inner run with the residual as right-hand side).  A restart zeroes the direction
+// buffers and re-initialises the inner run through a preconditioner pass gated on the state's
+// `restart` flag, so the next trip starts again at even parity.  The body ends with a one-thread
+// kernel that sets the loop's condition from the device state: the loop of an instance ends as
+// soon as it is done, so a finished instance launches nothing more, and no host decision sits
+// anywhere inside the solve.  Each loop also stops after a fixed number of trips (maxit + 64),
+// whatever the state says, and the instance then reports ST_ERR_NOT_CONVERGED.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -22,7 +25,6 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kStreamBlocks = 152 * 8;
-constexpr int kSegments = 4;  // graph segments (pairs of iterations + refinement) per launch
 
 __global__ void k_zero3_gated(long long N, df *a, df *b, df *c, const State *S) {
   if (!S->restart) return;
@@ -41,6 +43,22 @@ __global__ void k_df_to_double_gated(long long N, const df *__restrict__ src,
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
        e += (long long)gridDim.x * blockDim.x)
     dst[e] = df_to_double(src[e]);
+}
+
+// End of one trip of an instance's loop: continue while the instance is not done and the trip
+// budget lasts; a loop stopped by the budget marks the instance done and not converged.
+__global__ void k_loop_control(cudaGraphConditionalHandle cond, State *S, int *trips,
+                               int max_trips) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int t = ++(*trips);
+  bool go = !S->done;
+  if (go && t >= max_trips) {
+    go = false;
+    S->done = 1;
+    S->active = 0;
+    if (S->status == 0) S->status = ST_ERR_NOT_CONVERGED;
+  }
+  cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
 struct BatchInfo {
@@ -115,9 +133,11 @@ struct st_batch {
   cudaEvent_t fork, cfork, done_ev;
   State **d_states;
   BatchInfo *d_info, *h_info;
+  int *d_trips;                       // per instance: trips of its loop in the current solve
   cudaGraphExec_t exec;
   std::vector<const double *> cap_fH;  // pointers the graph was captured with
   std::vector<double *> cap_u;
+  int cap_maxit;                       // trip budget the graph was built with
 };
 
 namespace {
@@ -135,6 +155,7 @@ void free_batch(st_batch *b) {
   if (b->cstream) cudaStreamDestroy(b->cstream);
   cudaFree(b->d_states);
   cudaFree(b->d_info);
+  cudaFree(b->d_trips);
   if (b->h_info) cudaFreeHost(b->h_info);
   delete b;
 }
@@ -145,35 +166,54 @@ void free_batch(st_batch *b) {
     if (_e != cudaSuccess) return map_err(_e); \
   } while (0)
 
-int capture(st_batch *b, const double *const *fH, double *const *u) {
+// Build the graph: one WHILE node per instance, its body captured from the instance's own stream.
+int capture(st_batch *b, const double *const *fH, double *const *u, int maxit) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
   cudaGraph_t graph = nullptr;
-  BT_TRY(cudaStreamBeginCapture(b->cstream, cudaStreamCaptureModeRelaxed));
-  cudaError_t e = cudaEventRecord(b->cfork, b->cstream);
+  BT_TRY(cudaGraphCreate(&graph, 0));
+  cudaError_t e = cudaSuccess;
+  const int max_trips = maxit + 64;
   for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
     cudaStream_t s = b->streams[i];
-    e = cudaStreamWaitEvent(s, b->cfork, 0);
-    for (int seg = 0; seg < kSegments && e == cudaSuccess; ++seg) {
-      e = iteration(b->h[i], 0, s);
-      if (e == cudaSuccess) e = iteration(b->h[i], 1, s);
-      if (e == cudaSuccess) e = refine(b->h[i], fH[i], u[i], s);
+    e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
+    e = iteration(b->h[i], 0, s);
+    if (e == cudaSuccess) e = iteration(b->h[i], 1, s);
+    if (e == cudaSuccess) e = refine(b->h[i], fH[i], u[i], s);
+    if (e == cudaSuccess) {
+      k_loop_control<<<1, 32, 0, s>>>(cond, b->h[i]->S, b->d_trips + i, max_trips);
+      e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaEventRecord(b->cevents[i], s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cstream, b->cevents[i], 0);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &captured);
+    if (e == cudaSuccess) e = e2;
   }
-  cudaError_t e2 = cudaStreamEndCapture(b->cstream, &graph);
-  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
+  cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
     return map_err(e);
   }
   b->cap_fH.assign(fH, fH + b->count);
   b->cap_u.assign(u, u + b->count);
+  b->cap_maxit = maxit;
   return ST_OK;
 }
 
@@ -234,6 +274,7 @@ int st_setup_batch(const st_problem *probs, int count, void *stream, st_batch **
       cudaSuccess)
     return fail(ST_ERR_CUDA);
   if (cudaMalloc(&b->d_info, count * sizeof(BatchInfo)) != cudaSuccess) return fail(ST_ERR_OOM);
+  if (cudaMalloc(&b->d_trips, count * sizeof(int)) != cudaSuccess) return fail(ST_ERR_OOM);
   if (cudaMallocHost(&b->h_info, count * sizeof(BatchInfo)) != cudaSuccess)
     return fail(ST_ERR_OOM);
   *out = b;
@@ -284,31 +325,25 @@ int st_solve_batch(st_batch *b, const double *const *fH_devs, double *const *u_d
     BT_TRY(cudaEventRecord(b->events[i], s));
     BT_TRY(cudaStreamWaitEvent(b->cstream, b->events[i], 0));
   }
-  bool same = b->exec && b->cap_fH.size() == (size_t)b->count;
+  bool same = b->exec && b->cap_fH.size() == (size_t)b->count && b->cap_maxit == maxit;
   for (int i = 0; same && i < b->count; ++i)
     same = (b->cap_fH[i] == fH_devs[i] && b->cap_u[i] == u_devs[i]);
   if (!same) {
-    int r = capture(b, fH_devs, u_devs);
+    int r = capture(b, fH_devs, u_devs, maxit);
     if (r) return r;
   }
-  // relaunch the graph until every instance is done (bounded: each launch is 2*kSegments
-  // iterations of every unfinished instance)
-  const int max_launches = maxit / (2 * kSegments) + 64;
-  bool all_done = false;
-  for (int it = 0; it < max_launches && !all_done; ++it) {
-    BT_TRY(cudaGraphLaunch(b->exec, b->cstream));
-    k_gather<<<(b->count + 127) / 128, 128, 0, b->cstream>>>(b->d_states, b->count, b->d_info);
-    BT_TRY(cudaGetLastError());
-    BT_TRY(cudaMemcpyAsync(b->h_info, b->d_info, b->count * sizeof(BatchInfo),
-                           cudaMemcpyDeviceToHost, b->cstream));
-    BT_TRY(cudaStreamSynchronize(b->cstream));
-    all_done = true;
-    for (int i = 0; i < b->count; ++i) {
-      all_done = all_done && b->h_info[i].done;
-      if (b->h_info[i].tmem_held) {
-        close_device(b->device);
-        return ST_ERR_TIMEOUT;
-      }
+  // one launch runs every instance's loop to its end
+  BT_TRY(cudaMemsetAsync(b->d_trips, 0, b->count * sizeof(int), b->cstream));
+  BT_TRY(cudaGraphLaunch(b->exec, b->cstream));
+  k_gather<<<(b->count + 127) / 128, 128, 0, b->cstream>>>(b->d_states, b->count, b->d_info);
+  BT_TRY(cudaGetLastError());
+  BT_TRY(cudaMemcpyAsync(b->h_info, b->d_info, b->count * sizeof(BatchInfo),
+                         cudaMemcpyDeviceToHost, b->cstream));
+  BT_TRY(cudaStreamSynchronize(b->cstream));
+  for (int i = 0; i < b->count; ++i) {
+    if (b->h_info[i].tmem_held) {
+      close_device(b->device);
+      return ST_ERR_TIMEOUT;
     }
   }
   // later work on the caller's stream sees the solutions

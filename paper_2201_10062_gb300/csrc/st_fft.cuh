@@ -9,6 +9,8 @@
 // tw[t] = W_L^t for t < L/2.
 #pragma once
 
+#include "st_dd.cuh"
+
 namespace st {
 
 template <class T>
@@ -43,6 +45,10 @@ struct PadShift<float> {
 template <>
 struct PadShift<double> {
   static constexpr int v = 3;  // 8 complex doubles per 128-byte bank row
+};
+template <>
+struct PadShift<dd> {
+  static constexpr int v = 3;  // 8 complex double-floats (16 bytes each) per 128-byte bank row
 };
 
 template <class T>

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/st_minres.h"
+#include "st_dd.cuh"
 #include "st_df.cuh"
 
 namespace st {
@@ -26,6 +27,8 @@ struct Geom {
   int mz;               // interior points along z: 1 unless 3D
   const double *cz;     // [mz+1][my][mx] tau * a(z-face) / hz^2 (NULL unless 3D)
   const df *czd;
+  int c_uniform;        // every face coefficient equals c_uni (constant a, equal spacing)
+  df c_uni;             // that coefficient as a double-float pair
 };
 
 // The six face coefficients (tau a / h^2) around interior node (i, jy, jz): west/east along x,
@@ -265,7 +268,7 @@ __device__ inline void minres_givens_dev(State *S, double E) {
 // the launching stream; the host sums the elapsed times per kernel class afterwards.
 enum {
   KC_STENCIL = 0,  // flipped space-time stencil (MINRES and apply modes)
-  KC_LANCZOS = 1,  // Lanczos three-term update
+  KC_LANCZOS = 1,  // Lanczos three-term update fused into the first x-pass of the preconditioner
   KC_DSTX = 2,     // spatial DST along x (contiguous lines)
   KC_DSTY = 3,     // spatial DST along y (strided lines)
   KC_TIME = 4,     // time DST -> spectral scaling -> time DST (+ energy, Givens)
@@ -331,6 +334,13 @@ struct PrecPlan {
   const double *cheb_a_d, *cheb_s_d;
   const float *cheb_a_f, *cheb_s_f;
   void *cheb_work;
+  // float64 preconditioner (P_H / P-hat path): the transforms and the scaling in double-float
+  // arithmetic on the float32 pipes (1) or in float64 (0); the intermediate vectors between the
+  // passes are then stored as double-floats in the output buffer.  Tables in double-float:
+  Spec<dd> spec_dd;
+  const dd *twx_dd, *twy_dd, *twz_dd;
+  int fp64_dd;
+  int time_J_dd;  // spatial columns per double-float time-kernel block (0: default)
 };
 
 // Lowest relative target of an inner (float32-preconditioned) MINRES run of the mixed solve:
@@ -393,6 +403,8 @@ cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *da
                           cudaStream_t st);
 cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
                           cudaStream_t st);
+// the double-float time kernel alone (float64 preconditioner's double-float engine), ungated
+cudaError_t tune_run_time_dd(const Geom &g, const PrecPlan &pp, void *data, cudaStream_t st);
 bool time_J_fits(int n, int J, bool fp32);
 // one spatial pass along y (axis 1) or z (axis 2), float32, in place and ungated: on the tensor
 // cores with tc_img, by the shared-memory FFT when tc_img is null
@@ -422,6 +434,12 @@ template <class Tc>
 __device__ __forceinline__ Tc to_real(float v) { return (Tc)v; }
 template <class Tc>
 __device__ __forceinline__ Tc to_real(df v) { return (Tc)v.hi; }
+// double-float storage of the float64 preconditioner's intermediate vectors, read by the
+// double-float transforms
+template <class Tc>
+__device__ __forceinline__ Tc to_real(dd v) { return (Tc)v; }
+template <>
+__device__ __forceinline__ dd to_real<dd>(dd v) { return v; }
 
 // Element sources for the first stage of a preconditioner pass.  prepare() runs once per thread
 // after the gate; operator() returns element i in the transform type.
@@ -511,6 +529,7 @@ struct st_handle {
   // the tensor-core operand images the handle was built with (the autotuner may switch a stage
   // to its CUDA-core kernel by clearing the plan's pointer; these keep the originals)
   const unsigned short *tc_time_img, *tc_y_img, *tc_z_img;
+  int fp64_dd_ok;        // the float64 preconditioner may take the double-float engine
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)

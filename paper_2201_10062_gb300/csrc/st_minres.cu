@@ -421,6 +421,7 @@ size_t workspace_bytes(const Geom &g, bool mixed, int cheb) {
   b += sizeof(State);
   b += ((size_t)g.my * (g.mx + 1) + (size_t)(g.my + 1) * g.mx) * sizeof(double);  // grad faces
   b += table_doubles(g) * sizeof(double) + table_floats(g) * sizeof(float) + 256;
+  b += table_floats(g) * sizeof(dd) + 256;  // double-float copies of the spectral tables
   b += (faces_x(g) + faces_y(g) + faces_z(g)) * sizeof(df) + 256;  // df faces
   if (mixed && time_tc_supported(g.n)) b += time_tc_sop_halves(g.n) * 2;
   if (mixed && !time_tc_supported(g.n) && time_tc_long_supported(g.n))
@@ -681,7 +682,12 @@ int build_tables(st_handle *h) {
   }
   const size_t o_sopy = (o_cdf + cdf.size() * sizeof(df) + 255) / 256 * 256;
   const size_t o_sopz = (o_sopy + sopy.size() * sizeof(unsigned short) + 255) / 256 * 256;
-  const size_t bytes = o_sopz + sopz.size() * sizeof(unsigned short);
+  // double-float copies of the spectral tables and twiddles for the float64 preconditioner's
+  // double-float engine (each value split exactly: hi the nearest float, lo the rest)
+  std::vector<dd> hdd(nd - o_mux);
+  for (size_t i = o_mux; i < nd; ++i) hdd[i - o_mux] = dd(hd[i]);
+  const size_t o_dd = (o_sopz + sopz.size() * sizeof(unsigned short) + 255) / 256 * 256;
+  const size_t bytes = o_dd + hdd.size() * sizeof(dd);
   ST_TRY(cudaMalloc(&h->tables, bytes));
   ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice));
@@ -696,6 +702,8 @@ int build_tables(st_handle *h) {
   if (!sopz.empty())
     ST_TRY(cudaMemcpy((char *)h->tables + o_sopz, sopz.data(),
                       sopz.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+  ST_TRY(cudaMemcpy((char *)h->tables + o_dd, hdd.data(), hdd.size() * sizeof(dd),
+                    cudaMemcpyHostToDevice));
   const double *D = (const double *)h->tables;
   const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
   h->g.cx = D + o_cx;
@@ -705,6 +713,16 @@ int build_tables(st_handle *h) {
   h->g.cxd = CD;
   h->g.cyd = (g.dim >= 2) ? CD + cx.size() : nullptr;
   h->g.czd = (g.dim == 3) ? CD + cx.size() + cy.size() : nullptr;
+  {
+    // one face coefficient for the whole grid: the double-float stencil's uniform form
+    const double c0 = cx.empty() ? 0.0 : cx[0];
+    bool uni = !cx.empty() && !(std::getenv("ST_STENCIL_GENERAL") != nullptr);
+    for (double v : cx) uni = uni && (v == c0);
+    for (double v : cy) uni = uni && (v == c0);
+    for (double v : cz) uni = uni && (v == c0);
+    h->g.c_uniform = uni ? 1 : 0;
+    h->g.c_uni = df_of_double(c0);
+  }
   h->g.th_d = df_of_double(h->g.theta);
   h->g.omth_d = df_of_double(1.0 - h->g.theta);
   h->g.th_exact = (h->g.theta == 0.0 || h->g.theta == 0.5 || h->g.theta == 1.0) ? 1 : 0;
@@ -765,6 +783,20 @@ int build_tables(st_handle *h) {
                            D + o_sin, p.prec, p.scheme, th};
   pp.spec_f = Spec<float>{F + o_mux, F + o_muy, F + o_hk, F + o_ck, F + o_sk, F + o_lh, F + o_lht,
                           F + o_sin, p.prec, p.scheme, (float)th};
+  const dd *DD = reinterpret_cast<const dd *>((const char *)h->tables + o_dd) - o_mux;
+  pp.spec_dd = Spec<dd>{DD + o_mux, DD + o_muy, DD + o_hk, DD + o_ck, DD + o_sk, DD + o_lh,
+                        DD + o_lht, DD + o_sin, p.prec, p.scheme, dd(th)};
+  pp.twx_dd = DD + o_twx;
+  pp.twy_dd = DD + o_twy;
+  pp.twz_dd = DD + o_twz;
+  // the float64 P_H / P-hat preconditioner runs its transforms in double-float unless
+  // ST_FP64_ENGINE=dfma asks for float64 arithmetic; st_autotune times both and keeps the faster
+  const char *eng = std::getenv("ST_FP64_ENGINE");
+  pp.fp64_dd = (p.precision == ST_FP64 && !pp.pcr && !pp.cheb &&
+                !(eng && std::strcmp(eng, "dfma") == 0))
+                   ? 1
+                   : 0;
+  h->fp64_dd_ok = (p.precision == ST_FP64 && !pp.pcr && !pp.cheb) ? 1 : 0;
   return ST_OK;
 }
 
@@ -1154,6 +1186,7 @@ namespace {
 struct Knobs {
   int st_target, dst_shift, jd, jf;
   int tc_time, tc_y, tc_z;  // 1: the stage runs on the tensor cores (when the handle has them)
+  int fp64_dd, jdd;         // float64 preconditioner: double-float engine, its time-kernel tile
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int>, Knobs> g_tune_cache;
@@ -1171,6 +1204,8 @@ int st_autotune(st_handle *h, int reps) {
     h->pp.sop = k.tc_time ? h->tc_time_img : nullptr;
     h->pp.sop_y = k.tc_y ? h->tc_y_img : nullptr;
     h->pp.sop_z = k.tc_z ? h->tc_z_img : nullptr;
+    h->pp.fp64_dd = h->fp64_dd_ok ? k.fp64_dd : 0;
+    h->pp.time_J_dd = k.jdd;
   };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1185,7 +1220,7 @@ int st_autotune(st_handle *h, int reps) {
     }
   }
   // tune from the tensor-core configuration the handle was built with
-  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1});
+  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1, 1, 0});
   cudaStream_t st = h->stream;
   const Geom &g = h->g;
   cudaEvent_t e0, e1;
@@ -1292,8 +1327,36 @@ int st_autotune(st_handle *h, int reps) {
       *use[axis - 1] = (ms_tc <= ms_fft) ? 1 : 0;
     }
   }
+  // 5. float64 preconditioner: double-float engine (its own time-kernel tile first) against the
+  // float64 one, the whole P_H pass each
+  int fp64_dd = 0, jdd = 0;
+  if (!fp32 && h->fp64_dd_ok) {
+    const int cand[] = {16, 32, 48, 64};
+    float best = 1e30f;
+    h->pp.fp64_dd = 1;
+    for (int J : cand) {
+      if (!time_J_fits(g.n, J, false)) continue;
+      h->pp.time_J_dd = J;
+      const float ms = timed([&]() { return tune_run_time_dd(h->g, h->pp, h->Z[0], st); });
+      if (ms < best) {
+        best = ms;
+        jdd = J;
+      }
+    }
+    h->pp.time_J_dd = jdd;
+    const float ms_dd = timed([&]() {
+      return launch_prec<double, double, double>(h->g, h->pp, h->V[0], (double *)h->Z[0], h->S,
+                                                 TM_NONE, h->partials, st);
+    });
+    h->pp.fp64_dd = 0;
+    const float ms_d = timed([&]() {
+      return launch_prec<double, double, double>(h->g, h->pp, h->V[0], (double *)h->Z[0], h->S,
+                                                 TM_NONE, h->partials, st);
+    });
+    fp64_dd = (ms_dd <= ms_d) ? 1 : 0;
+  }
   const Knobs chosen{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f, tc_time,
-                     tc_y, tc_z};
+                     tc_y, tc_z, fp64_dd, jdd};
   apply_engines(chosen);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1307,7 +1370,7 @@ int st_autotune(st_handle *h, int reps) {
 }
 
 const char *st_kernel_class_name(int c) {
-  static const char *names[KC_COUNT] = {"stencil", "lanczos", "dst_x", "dst_y",
+  static const char *names[KC_COUNT] = {"stencil", "lanczos_dst_x", "dst_x", "dst_y",
                                         "time_dst_scale", "update", "residual", "aux"};
   return (c >= 0 && c < KC_COUNT) ? names[c] : "unknown";
 }

@@ -28,6 +28,7 @@ constexpr int kNT = 256;
 
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ dd rsq(dd x) { return rsqrt_dd(x); }
 
 // Inside a MINRES iteration only the first kernel (the stencil) looks at `finish`; it clears
 // `active` so that the rest of that iteration is skipped.  The preconditioner kernels check
@@ -195,11 +196,11 @@ __device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
       kk[i] = odd ? 2 * r + 1 : 2 * r + 2;
       ix[i] = 0;
     }
-    Tc acc[KT][JT];
+    MacAcc<Tc> acc[KT][JT];
 #pragma unroll
     for (int i = 0; i < KT; ++i)
 #pragma unroll
-      for (int c = 0; c < JT; ++c) acc[i][c] = Tc(0);
+      for (int c = 0; c < JT; ++c) acc[i][c].zero();
     const Tc *Fb = X + jg * JT;
     for (int t = 1; t <= h; ++t) {
       const Tc *F = Fb + (odd ? (t - 1) : (n - t)) * J;
@@ -213,7 +214,7 @@ __device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
         ix[i] = q;
         const Tc sv = sintab[q];
 #pragma unroll
-        for (int c = 0; c < JT; ++c) acc[i][c] = fma(sv, f[c], acc[i][c]);
+        for (int c = 0; c < JT; ++c) acc[i][c].add(sv, f[c]);
       }
     }
     if (odd && nodd_mid) {
@@ -222,7 +223,7 @@ __device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
       for (int i = 0; i < KT; ++i) {
         const Tc sv = sintab[(int)(((long long)kk[i] * tm) % P2)];
 #pragma unroll
-        for (int c = 0; c < JT; ++c) acc[i][c] = fma(sv, F[c], acc[i][c]);
+        for (int c = 0; c < JT; ++c) acc[i][c].add(sv, F[c]);
       }
     }
 #pragma unroll
@@ -230,7 +231,7 @@ __device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
       if (rg * KT + i < cnt) {
         Tc *Yr = Y + (kk[i] - 1) * J + jg * JT;
 #pragma unroll
-        for (int c = 0; c < JT; ++c) Yr[c] = acc[i][c];
+        for (int c = 0; c < JT; ++c) Yr[c] = acc[i][c].get();
       }
     }
   }
@@ -547,6 +548,16 @@ __global__ void k_copy_to(long long N, Src src, Tc *z, const State *S, int gk) {
     z[e] = src(e);
 }
 
+// the x pass that carries the fused Lanczos step is timed as its own kernel class
+template <class Src>
+struct is_lanczos_src {
+  static constexpr bool value = false;
+};
+template <class Tc, class Tv>
+struct is_lanczos_src<SrcLanczos<Tc, Tv>> {
+  static constexpr bool value = true;
+};
+
 template <class Tc>
 size_t dst_smem(int L, int PB) {
   return (size_t)(L / 2) * sizeof(cpx<Tc>) + (size_t)PB * fft_seq_stride<Tc>(L) * sizeof(cpx<Tc>);
@@ -577,7 +588,7 @@ cudaError_t launch_dst_l(Src in, Tout *out, int len, long long nlines, int mx, l
   auto kern = k_dst_space<Tc, Src, Tout, XL, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  prof_begin(XL ? KC_DSTX : KC_DSTY, st);
+  prof_begin(XL ? (is_lanczos_src<Src>::value ? KC_LANCZOS : KC_DSTX) : KC_DSTY, st);
   kern<<<(unsigned)blocks, kNTD, sm, st>>>(in, out, len, nlines, mx, m, tw, PB, S, gk);
   prof_end(st);
   return cudaGetLastError();
@@ -610,6 +621,10 @@ struct TimeTile<double> {
 template <>
 struct TimeTile<float> {
   static constexpr int KT = 8, JT = 4;
+};
+template <>
+struct TimeTile<dd> {
+  static constexpr int KT = 4, JT = 4;
 };
 
 template <class Tc>
@@ -677,6 +692,10 @@ template <>
 const float *tw_of<float>(const PrecPlan &pp, bool x) {
   return x ? pp.twx_f : pp.twy_f;
 }
+template <>
+const dd *tw_of<dd>(const PrecPlan &pp, bool x) {
+  return x ? pp.twx_dd : pp.twy_dd;
+}
 template <class Tc>
 static const Spec<Tc> &spec_of(const PrecPlan &pp);
 template <>
@@ -686,6 +705,10 @@ const Spec<double> &spec_of<double>(const PrecPlan &pp) {
 template <>
 const Spec<float> &spec_of<float>(const PrecPlan &pp) {
   return pp.spec_f;
+}
+template <>
+const Spec<dd> &spec_of<dd>(const PrecPlan &pp) {
+  return pp.spec_dd;
 }
 
 template <class Tc>
@@ -733,6 +756,10 @@ const double *twz_of<double>(const PrecPlan &pp) {
 template <>
 const float *twz_of<float>(const PrecPlan &pp) {
   return pp.twz_f;
+}
+template <>
+const dd *twz_of<dd>(const PrecPlan &pp) {
+  return pp.twz_dd;
 }
 
 template <class Tc, class Src>
@@ -823,6 +850,51 @@ cudaError_t cheb_stages(const Geom &g, const PrecPlan &pp, Src src, Tc *zc, Stat
   return time_single<Tc>(R, zc, g, pp, S, partials, gk, Jo, st);
 }
 
+// The same source with double-float as its transform type.
+template <class Src>
+struct AsDd;
+template <class Tin>
+struct AsDd<SrcArray<double, Tin>> {
+  static SrcArray<dd, Tin> of(const SrcArray<double, Tin> &s) { return SrcArray<dd, Tin>{s.p}; }
+};
+template <>
+struct AsDd<SrcLanczos<double, double>> {
+  static SrcLanczos<dd, double> of(const SrcLanczos<double, double> &s) {
+    SrcLanczos<dd, double> r{};
+    r.q = s.q;
+    r.vk = s.vk;
+    r.vp = s.vp;
+    return r;
+  }
+};
+
+// The float64 preconditioner's P_H / P-hat pass with every transform and the scaling in
+// double-float arithmetic: the first x pass reads the float64 source and stores double-floats in
+// z; the y (z) passes and the time kernel work on that double-float copy in place; the last x pass
+// reads it and writes float64 back into z.  Same stages and order as the float64 pass.
+template <class Src>
+cudaError_t prec_stages_dd(const Geom &g, const PrecPlan &pp, Src src, double *z, State *S,
+                           int tmode, double *partials, cudaStream_t st, cudaEvent_t after_time) {
+  using Inner = SrcArray<dd, dd>;
+  const int gk = gate_kind_of(tmode);
+  dd *zd = reinterpret_cast<dd *>(z);
+  const long long nx = (long long)g.n * g.my * g.mz;
+  cudaError_t e;
+  e = launch_dst<dd, decltype(AsDd<Src>::of(src)), dd, true>(AsDd<Src>::of(src), zd, g.mx, pp.Lx,
+                                                             nx, g.mx, g.m, pp.twx_dd, S, gk,
+                                                             pp.dst_shift, st);
+  if (e != cudaSuccess) return e;
+  if (g.dim >= 2 && (e = dst_y_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
+  if (g.dim == 3 && (e = dst_z_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
+  e = launch_time<dd>(zd, g, pp.spec_dd, S, tmode, 0, partials, gk, pp.time_J_dd, st);
+  if (e != cudaSuccess) return e;
+  if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
+  if (g.dim == 3 && (e = dst_z_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
+  if (g.dim >= 2 && (e = dst_y_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
+  return launch_dst<dd, Inner, double, true>(Inner{zd}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_dd,
+                                             S, gk, pp.dst_shift, st);
+}
+
 // The stages of one preconditioner pass; `src` feeds the first one.
 // after_time (optional) is recorded once the time kernel (which performs the MINRES scalar step)
 // has been enqueued.
@@ -833,6 +905,11 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
   using Inner = SrcArray<Tc, Tout>;
   const int gk = gate_kind_of(tmode);
   cudaError_t e;
+  if constexpr (sizeof(Tc) == sizeof(double)) {
+    if (pp.fp64_dd && !pp.cheb && !pp.pcr)
+      return prec_stages_dd(g, pp, src, reinterpret_cast<double *>(z), S, tmode, partials, st,
+                            after_time);
+  }
   if (pp.cheb)
     return cheb_stages<Tc>(g, pp, src, reinterpret_cast<Tc *>(z), S, tmode, partials, st,
                            after_time);
@@ -945,6 +1022,11 @@ cudaError_t tune_run_pass(const Geom &g, const PrecPlan &pp, int axis,
   }
   q.sop_z = tc_img;
   return dst_z_pass<float>(A{data}, data, g, q, S, GK_NONE, st);
+}
+
+cudaError_t tune_run_time_dd(const Geom &g, const PrecPlan &pp, void *data, cudaStream_t st) {
+  return launch_time<dd>((dd *)data, g, pp.spec_dd, nullptr, TM_NONE, 0, nullptr, GK_NONE,
+                         pp.time_J_dd, st);
 }
 
 cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,

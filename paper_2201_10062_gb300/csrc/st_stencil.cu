@@ -270,7 +270,11 @@ __device__ __forceinline__ void face_term(acc_df &A, df c, float a, float b) {
 
 // D3: the 3D grid (7-point stencil; planes mx*my apart), at three resident blocks per SM so that
 // its two extra planes stay in registers.  The 1D/2D instantiation carries no z terms.
-template <bool D3>
+// UNI: every face coefficient has the same value c (a constant coefficient on a grid with equal
+// spacing along every axis, g.c_uniform): tau K z = c (f z_c - sum_f z_f) over the f faces of the
+// node, so the face terms reduce to one exactly summed difference (TwoSum chain over floats) and
+// one double-float product, in place of one product per face.
+template <bool D3, bool UNI>
 __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const float *__restrict__ z,
                                                     df *__restrict__ out, State *S,
                                                     double *__restrict__ partials, int kc) {
@@ -296,7 +300,9 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
   if (valid) {
     const int jz = D3 ? j / my : 0, jy = j - jz * my;
     const long long p = (long long)j * mx + i;
-    const Faces6<df> fc = faces_df_at(g, i, jy, jz);
+    const df zero_f{0.f, 0.f};
+    const Faces6<df> fc = UNI ? Faces6<df>{zero_f, zero_f, zero_f, zero_f, zero_f, zero_f}
+                              : faces_df_at(g, i, jy, jz);
     const df cw = fc.w, ce = fc.e, cs = fc.s, cn = fc.n, cd = fc.d, cu = fc.u;
     const df th = g.th_d, omth = g.omth_d;
     const bool theta = (g.scheme == ST_THETA);
@@ -345,6 +351,22 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
     };
     // tau K at a plane: the face terms in a fixed order
     auto stiff5 = [&](const P5 &q, float c) -> df {
+      if (UNI) {
+        // c_uni (f z_c - z_w - z_e - ...): f z_c is exact (f = 2, 4, or 4 + 2 in 3D)
+        acc_df A{(dim >= 2) ? 4.f * c : 2.f * c, 0.f};
+        if (D3) A.add(2.f * c, 0.f);
+        A.add(-q.w, 0.f);
+        A.add(-q.e, 0.f);
+        if (dim >= 2) {
+          A.add(-q.s, 0.f);
+          A.add(-q.n, 0.f);
+        }
+        if (D3) {
+          A.add(-q.d, 0.f);
+          A.add(-q.u, 0.f);
+        }
+        return df_mul(g.c_uni, A.get());
+      }
       acc_df A{0.f, 0.f};
       face_term(A, cw, c, q.w);
       face_term(A, ce, c, q.e);
@@ -642,10 +664,17 @@ cudaError_t launch_stencil_df(const Geom &g, const float *z, df *q, State *S, do
   dim3 block = (g.dim == 1) ? dim3(kBX1, 1) : dim3(kBX2, kBY2);
   dim3 grid(t.gx, t.gy, t.nchunk);
   prof_begin(KC_STENCIL, st);
-  if (g.dim == 3)
-    k_stencil_df<true><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
-  else
-    k_stencil_df<false><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  if (g.dim == 3) {
+    if (g.c_uniform)
+      k_stencil_df<true, true><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+    else
+      k_stencil_df<true, false><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  } else {
+    if (g.c_uniform)
+      k_stencil_df<false, true><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+    else
+      k_stencil_df<false, false><<<grid, block, 0, st>>>(g, z, q, S, partials, t.kc);
+  }
   prof_end(st);
   return cudaGetLastError();
 }

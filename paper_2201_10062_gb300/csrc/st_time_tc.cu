@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdlib>
 
 #include "st_internal.cuh"
 
@@ -126,18 +127,20 @@ template <int COLS>
 __device__ __forceinline__ void tc_release_cols(bool ok, bool pend1, uint32_t mbar1, uint32_t ph1,
                                                 bool pend2, uint32_t mbar2, uint32_t ph2,
                                                 uint32_t tmem, State *S, bool copies_done = true) {
-  bool drained = true;
+  // every thread that saw a timeout waits (bounded) on the barriers that still owe a completion;
+  // the results are combined over the whole block (ok may differ between the tile pipelines of
+  // one block), so that every thread takes the same decision
+  bool d = true;
   if (!ok) {
-    // every thread waits (bounded) on the barriers that still owe a completion; the results are
-    // combined so that the whole block takes the same decision
-    bool d = copies_done;
+    d = copies_done;
     if (pend1) d = mbar_wait(mbar1, ph1) && d;
     if (pend2) d = mbar_wait(mbar2, ph2) && d;
-    drained = __syncthreads_and(d ? 1 : 0) != 0;
-    if (threadIdx.x == 0) {
-      S->status = ST_ERR_TIMEOUT;
-      if (!drained) atomicExch(&S->tmem_held, 1);
-    }
+  }
+  const bool drained = __syncthreads_and(d ? 1 : 0) != 0;
+  const bool failed = __syncthreads_or(ok ? 0 : 1) != 0;
+  if (failed && threadIdx.x == 0) {
+    S->status = ST_ERR_TIMEOUT;
+    if (!drained) atomicExch(&S->tmem_held, 1);
   }
   fence_before();
   __syncthreads();
@@ -552,6 +555,390 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
+// ------------------------------------------------------------------ two tile pipelines per block
+// The same transform, scaling and energy as k_time_tc, organised for more overlap: S_n (both
+// parities, hi and lo) lives in tensor memory as the A operand of tcgen05.mma (256 of the 512
+// columns), which leaves shared memory for two independent tile pipelines of 8 warps each.  Each
+// group has its own B operands, Y tile, accumulators (64 + 64 columns), mbarriers and named
+// barrier, so one group's fold/split/scale phases run while the other waits on its barriers or
+// its MMAs; the MMAs read only B from shared memory.  Group g of block b takes the tiles
+// 2b + g, 2b + g + 2 gridDim.x, ...
+constexpr int kGroups = 2;
+constexpr int kGT = 256;  // threads per group
+
+__device__ __forceinline__ void mma_f16_ta(uint32_t dtmem, uint32_t atmem, uint64_t bd,
+                                           uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
+}
+
+// barrier of the `nthreads` threads of named barrier `id`
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// barrier that also returns whether v holds in every participating thread
+__device__ __forceinline__ bool group_sync_and(bool v, int id, int nthreads) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+      : "memory");
+  return out != 0;
+}
+
+// Per-group shared-memory layout, offsets from the group's base (the base is 1024-aligned).
+struct TcGroupSmem {
+  uint32_t bop1, bop2, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar1, mbar2, total;
+};
+
+__host__ __device__ inline TcGroupSmem tcg_layout(int n) {
+  const int h = n / 2;
+  const uint32_t bop = 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
+  TcGroupSmem L{};
+  uint32_t o = 0;
+  L.bop1 = o;
+  o += bop;
+  L.bop2 = o;
+  o += bop;
+  L.ytile = o;
+  o += (uint32_t)n * kYS * 4u;
+  L.colscale = o;
+  o += kTN * 4u;
+  L.colinv1 = o;
+  o += kTN * 4u;
+  L.colinv2 = o;
+  o += kTN * 4u;
+  L.colmax = o;
+  o += kTN * 4u;
+  L.tmu = o;
+  o += kTN * 4u;
+  L.mbar1 = o;
+  o += 8;
+  L.mbar2 = o;
+  o += 8;
+  L.total = (o + 1023u) & ~1023u;
+  return L;
+}
+
+// whole block: group 0, group 1, then the tensor-memory address slot
+__host__ __device__ inline uint32_t tcg_block_bytes(int n) { return kGroups * tcg_layout(n).total + 16u; }
+
+// Fold, scale and split of one tile for a group of 256 threads: thread (column c, t-block tb) with
+// tb = gt / 32 and tb + 8 (h/8 <= 16 t-blocks).  Same arithmetic as build_b_vals.
+__device__ __forceinline__ void load_b_g(int n, int gt, const float *data, long long m,
+                                         long long j0, int je, float (&a)[2][8],
+                                         float (&b)[2][8]) {
+  const int h = n >> 1, hb = h >> 3;
+  const int c = gt & (kTN - 1);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = (gt >> 5) + 8 * it;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = tb * 8 + q;
+      const bool ok = tb < hb && c < je;
+      a[it][q] = ok ? data[(long long)t * m + j0 + c] : 0.f;
+      b[it][q] = ok ? data[(long long)(n - 1 - t) * m + j0 + c] : 0.f;
+    }
+  }
+}
+
+template <class Src>
+__device__ __forceinline__ void load_b_g_src(int n, int gt, Src src, float (&a)[2][8],
+                                             float (&b)[2][8]) {
+  const int h = (n + 1) >> 1, hb = h >> 3;
+  const int c = gt & (kTN - 1);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = (gt >> 5) + 8 * it;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int t = tb * 8 + q;
+      a[it][q] = (tb < hb) ? src(t, c) : 0.f;
+      b[it][q] = (tb < hb && n - 1 - t != t) ? src(n - 1 - t, c) : 0.f;  // odd middle row once
+    }
+  }
+}
+
+template <class Lay>
+__device__ __forceinline__ void build_b_g(unsigned char *gs, const Lay &L,
+                                          uint32_t bop_off, uint32_t colinv_off, int n,
+                                          const float (&a)[2][8], const float (&b)[2][8], int gt,
+                                          int bar) {
+  const int h = (n + 1) >> 1, hb = h >> 3;
+  unsigned int *colmax = reinterpret_cast<unsigned int *>(gs + L.colmax);
+  float *colscale = reinterpret_cast<float *>(gs + L.colscale);
+  float *colinv = reinterpret_cast<float *>(gs + colinv_off);
+  const int c = gt & (kTN - 1);
+  if (gt < kTN) colmax[gt] = 0u;
+  float u[2][8], d[2][8];
+  float mx = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = (gt >> 5) + 8 * it;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      u[it][q] = a[it][q] + b[it][q];
+      d[it][q] = a[it][q] - b[it][q];
+      if (tb < hb) mx = fmaxf(mx, fmaxf(fabsf(u[it][q]), fabsf(d[it][q])));
+    }
+  }
+  group_sync(bar, kGT);
+  atomicMax(&colmax[c], __float_as_uint(mx));
+  group_sync(bar, kGT);
+  if (gt < kTN) {
+    const float mm = __uint_as_float(colmax[gt]);
+    float sc = 1.0f;
+    if (mm > 0.f && isfinite(mm)) {
+      int e;
+      frexpf(mm, &e);
+      sc = ldexpf(1.0f, 14 - e);
+    }
+    colscale[gt] = sc;
+    colinv[gt] = 1.0f / (sc * kSScale);
+  }
+  group_sync(bar, kGT);
+  const float sc = colscale[c];
+  unsigned char *bop = gs + bop_off;
+  const uint32_t piece = (uint32_t)kTN * h * 2u;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int tb = (gt >> 5) + 8 * it;
+    if (tb < hb) {
+      uint32_t uh[4], ul[4], dh[4], dl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split_h2(u[it][2 * q] * sc, u[it][2 * q + 1] * sc, uh[q], ul[q]);
+        split_h2(d[it][2 * q] * sc, d[it][2 * q + 1] * sc, dh[q], dl[q]);
+      }
+      const uint32_t off = canon_off(c, tb * 8, h);
+      *reinterpret_cast<uint4 *>(bop + 0 * piece + off) = make_uint4(uh[0], uh[1], uh[2], uh[3]);
+      *reinterpret_cast<uint4 *>(bop + 1 * piece + off) = make_uint4(ul[0], ul[1], ul[2], ul[3]);
+      *reinterpret_cast<uint4 *>(bop + 2 * piece + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+      *reinterpret_cast<uint4 *>(bop + 3 * piece + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+    }
+  }
+}
+
+// 2 parities x (h/16) K steps x 3 piece products: A pieces from tensor memory (piece 2P + hi/lo at
+// column a_base + 64 (2P + lo) + 8 ks), B from shared memory; commit to mbar.
+__device__ __forceinline__ void issue_mmas_ta(uint32_t a_base, uint32_t bbase, int h,
+                                              uint32_t dcol, uint32_t mbar) {
+  const uint32_t bpiece = (uint32_t)kTN * h * 2u;
+  for (int P = 0; P < 2; ++P) {
+    const uint32_t d = dcol + (uint32_t)(P * kTN);
+    const uint32_t a_hi = a_base + (uint32_t)(2 * P) * 64u, a_lo = a_hi + 64u;
+    const uint32_t b_hi = bbase + (2 * P) * bpiece, b_lo = b_hi + bpiece;
+    for (int ks = 0; ks < h / 16; ++ks) {
+      const uint32_t koff = (uint32_t)ks * 256u;  // two core matrices along K in B
+      const uint32_t acol = (uint32_t)ks * 8u;    // 16 fp16 values of A per lane
+      mma_f16_ta(d, a_hi + acol, make_desc(b_hi + koff, h), ks > 0 ? 1u : 0u);
+      mma_f16_ta(d, a_hi + acol, make_desc(b_lo + koff, h), 1u);
+      mma_f16_ta(d, a_lo + acol, make_desc(b_hi + koff, h), 1u);
+    }
+  }
+  mma_commit(mbar);
+}
+
+__global__ void __launch_bounds__(kNT, 1)
+    k_time_tc2(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
+               State *S, int tmode, double *__restrict__ partials, int gk) {
+  __shared__ double red[32];
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = n >> 1;
+  const TcGroupSmem L = tcg_layout(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = warp >> 3, gt = tid & (kGT - 1), w8 = warp & 7;
+  const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
+  unsigned char *gs = smem + (uint32_t)grp * L.total;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kGroups * L.total);
+  const float *colinv1 = reinterpret_cast<const float *>(gs + L.colinv1);
+  const float *colinv2 = reinterpret_cast<const float *>(gs + L.colinv2);
+  float *ytile = reinterpret_cast<float *>(gs + L.ytile);
+  float *tmus = reinterpret_cast<float *>(gs + L.tmu);
+  const uint32_t mbar1 = smem_u32(gs + L.mbar1), mbar2 = smem_u32(gs + L.mbar2);
+  const long long ntiles = (m + kTN - 1) / kTN;
+  if (gt == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar2) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_base = tmem;  // columns 0..255: S_n pieces
+  const uint32_t dcol1 = tmem + 256u + (uint32_t)grp * 128u, dcol2 = dcol1 + 64u;
+  // A into tensor memory: warp w writes piece w / 4 for the lanes of its quadrant w % 4; row r's
+  // 16-byte chunks of 8 K values sit at canon_off(r, 8j, h) in the shared-memory image
+  {
+    const int q = warp & 3, piece = warp >> 2;
+    const int r = q * 32 + lane;
+    const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
+                               (size_t)piece * kM * h * 2u;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    for (int ks = 0; ks < h / 16; ++ks) {
+      uint32_t w[8];
+      const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
+      const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
+      w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+      w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
+      tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  uint32_t ph1 = 0, ph2 = 0;
+  bool ok = true;
+  bool out1 = false, out2 = false;
+  float esum = 0.f, ecomp = 0.f;
+  // accumulator view of this warp: TMEM lanes 32q.. (rows r), parity P, all 32 columns
+  const int q = warp & 3, P = w8 >> 2;
+  const int r = (q << 5) + lane;
+  const uint32_t lanes = (uint32_t)(q * 32) << 16, cview = (uint32_t)(P * kTN);
+  const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
+  float *yrow = ytile + (P * h + r) * kYS;
+  auto ycell = [&](int t, int c) -> float & { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
+  const long long tstride = (long long)kGroups * gridDim.x;
+  auto finish_second = [&](long long pj0, int pje) {
+    const bool w = group_sync_and(mbar_wait(mbar2, ph2), bar, kGT);
+    ok = ok && w;
+    if (!w) return;
+    out2 = false;
+    ph2 ^= 1u;
+    fence_after();
+    float v[32];
+    tmem_ld16(dcol2 + lanes + cview, v);
+    tmem_ld16(dcol2 + lanes + cview + 16u, v + 16);
+    if (r < h) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) yrow[c] = v[c] * colinv2[c];
+    }
+    fence_before();
+    group_sync(bar, kGT);
+    fence_after();
+    for (int idx = gt; idx < n * kTN; idx += kGT) {
+      const int t = idx >> 5, c = idx & (kTN - 1);
+      if (c < pje) data[(long long)t * m + pj0 + c] = ycell(t, c);
+    }
+    group_sync(bar, kGT);
+  };
+  bool pend = false;
+  long long pj0 = 0;
+  int pje = 0;
+  float pa[2][8], pb[2][8];
+  const long long first = (long long)blockIdx.x * kGroups + grp;
+  if (first < ntiles) {
+    const long long jt = first * kTN;
+    load_b_g(n, gt, data, m, jt, (int)min((long long)kTN, m - jt), pa, pb);
+  }
+  for (long long tile = first; tile < ntiles && ok; tile += tstride) {
+    const long long j0 = tile * kTN;
+    const int je = (int)min((long long)kTN, m - j0);
+    if (gt < kTN) {
+      float t = 0.f;
+      if (gt < je) {
+        const long long j = j0 + gt;
+        const long long jy = j / mx, jx = j - jy * mx;
+        t = sp.mux[jx] + sp.muy[jy];
+      }
+      tmus[gt] = t;
+    }
+    build_b_g(gs, L, L.bop1, L.colinv1, n, pa, pb, gt, bar);
+    fence_async_smem();
+    group_sync(bar, kGT);
+    fence_after();
+    if (gt == 0) issue_mmas_ta(a_base, smem_u32(gs + L.bop1), h, dcol1, mbar1);
+    out1 = true;
+    if (tile + tstride < ntiles) {
+      const long long jt = (tile + tstride) * kTN;
+      load_b_g(n, gt, data, m, jt, (int)min((long long)kTN, m - jt), pa, pb);
+    }
+    if (pend) finish_second(pj0, pje);
+    {
+      const bool w = group_sync_and(mbar_wait(mbar1, ph1), bar, kGT);
+      ok = ok && w;
+      if (!w) break;
+    }
+    out1 = false;
+    ph1 ^= 1u;
+    fence_after();
+    {
+      float v[32];
+      tmem_ld16(dcol1 + lanes + cview, v);
+      tmem_ld16(dcol1 + lanes + cview + 16u, v + 16);
+      if (r < h) {
+        float rs = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float y = v[c] * colinv1[c];
+          const float yi = y * inv_sym(sp, sr, tmus[c]);
+          if (c < je) rs = fmaf(y, yi, rs);
+          yrow[c] = yi;
+        }
+        const float term = rs - ecomp;
+        const float t = esum + term;
+        ecomp = (t - esum) - term;
+        esum = t;
+      }
+    }
+    fence_before();
+    group_sync(bar, kGT);
+    fence_after();
+    {
+      float a2[2][8], b2[2][8];
+      load_b_g_src(n, gt, [&](int t, int c) -> float { return ycell(t, c); }, a2, b2);
+      build_b_g(gs, L, L.bop2, L.colinv2, n, a2, b2, gt, bar);
+    }
+    fence_async_smem();
+    group_sync(bar, kGT);
+    fence_after();
+    if (gt == 0 && ok) issue_mmas_ta(a_base, smem_u32(gs + L.bop2), h, dcol2, mbar2);
+    pend = ok;
+    out2 = out2 || ok;
+    pj0 = j0;
+    pje = je;
+  }
+  if (pend && ok) finish_second(pj0, pje);
+  tc_release_cols<512>(ok, out1, mbar1, ph1, out2, mbar2, ph2, tmem, S);
+  if (tmode != TM_NONE) {
+    const double e = (double)esum - (double)ecomp;
+    double tot;
+    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                               &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT || tmode == TM_RESTART)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
+}
+
 // Spatial DST-I along y on the tensor cores (float32 transforms of the mixed-precision
 // preconditioner, Sec. 3.1.1 steps 1 and 3 along y), in place: the lines of one time level at
 // fixed x are len = my values mx apart, and a tile is 32 adjacent lines (x0..x0+31) of one time
@@ -660,6 +1047,163 @@ __global__ void __launch_bounds__(kNT, 1)
   }
   cp_async_wait_all();
   tc_release_cols<64>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
+}
+
+// Two-pipeline form of k_dst_tc_y: S_len (both parities, hi and lo) in tensor memory as the A
+// operand, two groups of 8 warps, each with its own staged input tile, B operand, Y tile,
+// accumulator (64 columns) and named barrier.  Same arithmetic and output.
+struct TcYSmem {
+  uint32_t bop, ytile, stage, colscale, colinv, colmax, mbar, total;
+};
+
+__host__ __device__ inline TcYSmem tcy_layout(int len) {
+  const int h = (len + 1) / 2;
+  TcYSmem L{};
+  uint32_t o = 0;
+  L.bop = o;
+  o += 2u * 2u * kTN * h * 2u;
+  L.ytile = o;
+  o += 2u * h * kYS * 4u;
+  L.stage = o;
+  o += (uint32_t)len * kTN * 4u;
+  L.colscale = o;
+  o += kTN * 4u;
+  L.colinv = o;
+  o += kTN * 4u;
+  L.colmax = o;
+  o += kTN * 4u;
+  L.mbar = o;
+  o += 8;
+  L.total = (o + 1023u) & ~1023u;
+  return L;
+}
+
+__host__ __device__ inline uint32_t tcy_block_bytes(int len) { return kGroups * tcy_layout(len).total + 16u; }
+
+__global__ void __launch_bounds__(kNT, 1)
+    k_dst_tc_y2(const float *data, float *out, int len, int mx, long long m, long long nplanes,
+                const __half *sop_g, State *S, int gk) {
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = (len + 1) >> 1;
+  const TcYSmem L = tcy_layout(len);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = warp >> 3, gt = tid & (kGT - 1), w8 = warp & 7;
+  const int bar = 1 + grp;
+  unsigned char *gs = smem + (uint32_t)grp * L.total;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kGroups * L.total);
+  const float *colinv = reinterpret_cast<const float *>(gs + L.colinv);
+  float *stage = reinterpret_cast<float *>(gs + L.stage);
+  float *ytile = reinterpret_cast<float *>(gs + L.ytile);
+  const uint32_t mbar = smem_u32(gs + L.mbar);
+  const int tpp = (mx + kTN - 1) / kTN;  // tiles per plane
+  const long long ntiles = nplanes * tpp;
+  auto tile_at = [&](long long tile, long long &base, int &je) {
+    const long long t = tile / tpp;
+    const int x0 = (int)(tile - t * tpp) * kTN;
+    base = t * m + x0;
+    je = min(kTN, mx - x0);
+  };
+  auto prefetch = [&](long long tile) {
+    long long base;
+    int je;
+    tile_at(tile, base, je);
+    const uint32_t sbase = smem_u32(stage);
+    for (int idx = gt; idx < len * kTN; idx += kGT) {
+      const int e = idx >> 5, c = idx & (kTN - 1);
+      if (c < je)
+        cp_async4(sbase + 4u * (uint32_t)idx, data + base + (long long)e * mx + c);
+      else
+        stage[idx] = 0.f;
+    }
+    cp_async_commit();
+  };
+  const long long first = (long long)blockIdx.x * kGroups + grp;
+  const long long tstride = (long long)kGroups * gridDim.x;
+  if (first < ntiles) prefetch(first);
+  if (gt == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_base = tmem;
+  const uint32_t dcol = tmem + 256u + (uint32_t)grp * 64u;
+  {
+    const int q = warp & 3, piece = warp >> 2;
+    const int r = q * 32 + lane;
+    const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
+                               (size_t)piece * kM * h * 2u;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    for (int ks = 0; ks < h / 16; ++ks) {
+      uint32_t w[8];
+      const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
+      const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
+      w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+      w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
+      tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  uint32_t phase = 0;
+  bool ok = true;
+  bool outstanding = false;
+  const int q = warp & 3, P = w8 >> 2;
+  const int r = (q << 5) + lane;
+  const uint32_t tl = dcol + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN);
+  const bool row_ok = r < h && (P == 0 ? 2 * r + 1 : 2 * r + 2) <= len;
+  float *yrow = ytile + (P * h + r) * kYS;
+  for (long long tile = first; tile < ntiles && ok; tile += tstride) {
+    long long base;
+    int je;
+    tile_at(tile, base, je);
+    cp_async_wait_all();
+    group_sync(bar, kGT);
+    {
+      float a[2][8], b[2][8];
+      load_b_g_src(len, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, b);
+      build_b_g(gs, L, L.bop, L.colinv, len, a, b, gt, bar);
+    }
+    fence_async_smem();
+    group_sync(bar, kGT);
+    fence_after();
+    if (gt == 0) issue_mmas_ta(a_base, smem_u32(gs + L.bop), h, dcol, mbar);
+    outstanding = true;
+    // the stage buffer is free (every thread has read its values): load the next tile
+    if (tile + tstride < ntiles) prefetch(tile + tstride);
+    ok = group_sync_and(mbar_wait(mbar, phase), bar, kGT);
+    if (!ok) break;
+    outstanding = false;
+    phase ^= 1u;
+    fence_after();
+    float v[32];
+    tmem_ld16(tl, v);
+    tmem_ld16(tl + 16u, v + 16);
+    if (row_ok) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) yrow[c] = v[c] * colinv[c];
+    }
+    fence_before();
+    group_sync(bar, kGT);
+    fence_after();
+    for (int idx = gt; idx < len * kTN; idx += kGT) {
+      const int e = idx >> 5, c = idx & (kTN - 1);
+      if (c < je) out[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+    }
+  }
+  cp_async_wait_all();
+  tc_release_cols<512>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
 }
 
 // ------------------------------------------------------------------ long time axes (n > 256)
@@ -1011,7 +1555,8 @@ __global__ void __launch_bounds__(kNT, 1)
 // n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
 // within the 227 KB a block may opt into
 bool time_tc_supported(int n) {
-  return n >= 32 && n <= 256 && (n % 32) == 0 && tc_layout(n).total + 1024u <= 227u * 1024u;
+  return n >= 32 && n <= 256 && (n % 32) == 0 && tc_layout(n).total + 1024u <= 227u * 1024u &&
+         tcg_block_bytes(n) + 1024u <= 227u * 1024u;
 }
 
 size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * ((n + 1) / 2); }
@@ -1046,7 +1591,8 @@ void time_tc_build_sop(int len, unsigned short *out) {
 bool dst_tc_supported(int len) {
   const int L1 = len + 1;
   return (L1 == 32 || L1 == 64 || L1 == 128 || L1 == 256) &&
-         dst_layout(len).total + 1024u <= 227u * 1024u;
+         dst_layout(len).total + 1024u <= 227u * 1024u &&
+         tcy_block_bytes(len) + 1024u <= 227u * 1024u;
 }
 
 int time_tc_grid() {
@@ -1063,6 +1609,27 @@ int time_tc_grid() {
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st) {
+  static const bool v1 = [] {
+    const char *e = std::getenv("ST_TIME_TC_V1");
+    return e && e[0] == '1';
+  }();
+  if (!v1) {
+    // two tile pipelines per block, S_n in tensor memory
+    const uint32_t smem_bytes = tcg_block_bytes(g.n);
+    cudaError_t e = cudaFuncSetAttribute(k_time_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (g.m + kTN - 1) / kTN;
+    const long long need = (ntiles + kGroups - 1) / kGroups;
+    int grid = time_tc_grid();
+    if (need < grid) grid = (int)need;
+    prof_begin(KC_TIME, st);
+    k_time_tc2<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
+                                              reinterpret_cast<const __half *>(sop), S, tmode,
+                                              partials, gk);
+    prof_end(st);
+    return cudaGetLastError();
+  }
   const uint32_t smem_bytes = tc_layout(g.n).total;
   cudaError_t e = cudaFuncSetAttribute(k_time_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
@@ -1083,7 +1650,8 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
 bool dst_tc_len_supported(int len) {
   if (dst_tc_supported(len)) return true;
   return len >= 32 && len <= 256 && (len % 32) == 0 &&
-         dst_layout(len).total + 1024u <= 227u * 1024u;
+         dst_layout(len).total + 1024u <= 227u * 1024u &&
+         tcy_block_bytes(len) + 1024u <= 227u * 1024u;
 }
 
 // One DST-I of length len along lines `stride` apart, nplanes planes `plane` apart, 32 adjacent
@@ -1091,6 +1659,26 @@ bool dst_tc_len_supported(int len) {
 cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride, long long plane,
                                 long long nplanes, const unsigned short *sop, State *S, int gk,
                                 int kc, cudaStream_t st) {
+  static const bool v1 = [] {
+    const char *e = std::getenv("ST_TIME_TC_V1");
+    return e && e[0] == '1';
+  }();
+  if (!v1) {
+    // two tile pipelines per block, S_len in tensor memory
+    const uint32_t smem_bytes = tcy_block_bytes(len);
+    cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
+    const long long need = (ntiles + kGroups - 1) / kGroups;
+    int grid = time_tc_grid();
+    if (need < grid) grid = (int)need;
+    prof_begin(kc, st);
+    k_dst_tc_y2<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
+                                               reinterpret_cast<const __half *>(sop), S, gk);
+    prof_end(st);
+    return cudaGetLastError();
+  }
   const uint32_t smem_bytes = dst_layout(len).total;
   cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);

@@ -65,10 +65,13 @@ def _case(c, seed=3):
 
 
 def _prec_tol(p):
+    """float64 path, double-float transform engine (the default): 48-bit significands, 1e-11
+    (the float64 engine stays within 1e-12); a varying coefficient amplifies last-bit differences
+    of the averaged eigenvalues by max(mu)/min(mu)."""
     if p.a_nodal is None:
-        return 1e-12
+        return 1e-11
     mu = H.averaged_stiffness_eigs(p)
-    return max(1e-12, 16 * EPS * mu.max() / mu.min())
+    return max(1e-11, 16 * EPS * mu.max() / mu.min())
 
 
 @pytest.mark.parametrize("c", CASES, ids=IDS)

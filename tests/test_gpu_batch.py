@@ -131,3 +131,30 @@ def test_batch_mixes_preconditioners_and_dimensions(pkg):
         assert abs(st1["iterations"] - stats[i]["iterations"]) <= 2, (i, st1, stats[i])
         single.close()
     B.close()
+
+
+def test_batch_loops_end_on_budget_and_zero_rhs(pkg):
+    """Each instance's device-side loop ends by itself: an instance whose iteration budget runs out
+    reports ST_ERR_NOT_CONVERGED with its iterations capped, a zero right-hand side is done at
+    once with u = 0, and the other instances of the same graph still converge."""
+    ws = _instances(SMALL[:3], seed0=70)
+    specs = [pkg.ProblemSpec(2, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, "PH", "mixed")
+             for w in ws]
+    B = pkg.BatchSolver(specs)
+    fHs = [B.instance(i).st_assemble_rhs(_d(w.f), _d(w.u0)) for i, w in enumerate(ws)]
+    fHs[1] = torch.zeros_like(fHs[1])
+    outs, stats = B.st_solve_batch(fHs, tol=1e-10, maxit=600)
+    assert stats[0]["status"] == 0 and stats[2]["status"] == 0
+    assert stats[1]["status"] == 0 and stats[1]["iterations"] == 0
+    assert float(outs[1].abs().max()) == 0.0
+    # a budget of 3 iterations: no instance converges, each stops at the budget
+    outs3, stats3 = B.st_solve_batch(fHs, tol=1e-10, maxit=3, allow_not_converged=True)
+    for i in (0, 2):
+        assert stats3[i]["status"] == pkg.ST_ERR_NOT_CONVERGED, stats3[i]
+        assert stats3[i]["iterations"] <= 4, stats3[i]
+    assert stats3[1]["status"] == 0
+    # and the graph built for the full budget still solves afterwards
+    outs4, stats4 = B.st_solve_batch(fHs, tol=1e-10, maxit=600)
+    for a, b in zip(outs, outs4):
+        assert torch.equal(a, b)
+    B.close()

@@ -57,3 +57,61 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
 
     bench.run_reference(Args, world=2, rank=1)
     assert capsys.readouterr().out == ""
+
+
+def _shard_worker(rank, world, port, outdir):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from workloads import synthetic as W
+
+    draws = W.batch_draws(64, seed=4)
+    unknowns = [d["mx"] * d["mx"] * d["n"] for d in draws]
+    mine = bench.batch_shard(draws, unknowns, world, rank)
+    parts = [None] * world
+    dist.all_gather_object(parts, mine)
+    with open(os.path.join(outdir, f"shard{rank}.json"), "w") as fh:
+        json.dump({"mine": mine, "parts": parts, "unknowns": unknowns,
+                   "thetas": [d["theta"] for d in draws]}, fh)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batch_partition_over_gloo_ranks(tmp_path, world):
+    """The 64-instance batch split over ranks with no collective on the data path: every rank
+    computes the same partition on its own, the parts are disjoint and cover every instance, and
+    the largest load stays within the greedy bound (total / ranks + largest instance)."""
+    import torch.multiprocessing as mp
+
+    from paper_2201_10062_gb300 import shard
+
+    port = _free_port()
+    mp.spawn(_shard_worker, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    res = [json.load(open(tmp_path / f"shard{r}.json")) for r in range(world)]
+    parts = res[0]["parts"]
+    for r in range(world):
+        assert res[r]["parts"] == parts  # the same split on every rank
+        assert res[r]["mine"] == parts[r]
+    flat = sorted(i for p in parts for i in p)
+    assert flat == list(range(64))  # complete and disjoint
+    costs = [shard.instance_cost(u, t) for u, t in zip(res[0]["unknowns"], res[0]["thetas"])]
+    loads = shard.loads(costs, parts)
+    assert max(loads) <= sum(costs) / world + max(costs)
+    assert all(len(p) > 0 for p in parts)
+
+
+def test_partition_edge_cases():
+    from paper_2201_10062_gb300 import shard
+
+    assert shard.partition([], 3) == [[], [], []]
+    assert shard.partition([5.0], 2) == [[0], []]
+    # equal costs spread round-robin by index
+    assert shard.partition([1.0] * 4, 2) == [[0, 2], [1, 3]]
+    # one rank holds everything
+    assert shard.partition([3.0, 1.0, 2.0], 1) == [[0, 1, 2]]
+    with pytest.raises(ValueError):
+        shard.partition([1.0], 0)
