@@ -57,10 +57,16 @@ CLASS_BYTES = {
     "fp64": {"stencil": 16, "lanczos_dst_x": 40, "dst_x": 16, "dst_y": 16, "time_dst_scale": 16,
              "update": 48, "residual": 24},
 }
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture), per
-# kernel class of the mixed 2D Crank-Nicolson solve at 255^2 x 256, for the kernels whose code is
-# unchanged since: profiles/launches_bench_cn2d_255x255_n256.md
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of every
+# launch of one mixed 2D Crank-Nicolson solve at 255^2 x 256), per kernel class, for the kernels
+# whose code is unchanged since: profiles/dram_traffic_mixed_cn2d_255x255_n256.md
+NCU_TRAFFIC = {("mixed", "stencil"): 136.3e6, ("mixed", "lanczos_dst_x"): 540.0e6,
+               ("mixed", "dst_x"): 70.3e6, ("mixed", "dst_y"): 72.6e6,
+               ("mixed", "time_dst_scale"): 72.9e6, ("mixed", "update"): 661.7e6,
+               ("mixed", "residual"): 373.2e6}
+# the same capture summed over one MINRES iteration (stencil, fused Lanczos x pass, y, time, y,
+# x, update), per unknown
+NCU_ITER_TRAFFIC = {"mixed": 97.7}
 
 
 def _env_int(name, default):
@@ -439,7 +445,9 @@ def run_ours(args, world, rank, local):
     roof = roofline_iter("mixed", N, iters, outer, mixed["ms"] * 1e-3, peaks)
     roof["scope"] = ("whole solve: every kernel of every MINRES iteration plus the refinement "
                      "residuals, algorithmic bytes of Sec. 8(d)")
-    roof["traffic"] = None
+    # DRAM bytes of one iteration's launches from ncu, per iteration like alg_bytes_per_iteration
+    roof["traffic"] = NCU_ITER_TRAFFIC["mixed"] * N if (w.mx, w.n) == (255, 256) else None
+    roof["traffic_unit"] = "bytes per MINRES iteration"
     kern = kernel_table(mixed["prof"], "mixed", N, steps, peaks)
     launches = sum(v["launches"] for v in mixed["prof"].values())
     fp = results["fp64"]

@@ -473,26 +473,54 @@ struct SrcLanczos<Tc, double> {
   }
 };
 
+// Double-float vectors: q holds Y T z_k without the 1/beta_k factor (the double-float stencil
+// leaves that scaling to this pass), so v_{k+1} = q / beta_k - lz_a v_k - lz_b v_{k-1}.
 template <class Tc>
 struct SrcLanczos<Tc, df> {
   const df *q, *vk;
   df *vp;
-  df a, b;
+  df a, b, sc;
   __device__ __forceinline__ void prepare(const State *S) {
     a = df_neg(S->dfs[DFS_LA]);
     b = df_neg(S->dfs[DFS_LB]);
+    sc = S->dfs[DFS_IB];
   }
-  __device__ __forceinline__ Tc operator()(long long i) const {
+  // the three loads of element i, issued apart from the arithmetic and the store so that a
+  // thread can have all of its elements' loads in flight before the first store (fetch, then
+  // finish); operator() does both for one element
+  struct Raw {
+    float2 q, v, p;
+  };
+  __device__ __forceinline__ Raw fetch(long long i) const {
     // q and v_k are read-only in this pass (see the float64 source)
-    const float2 q2 = __ldg(reinterpret_cast<const float2 *>(q) + i);
-    const float2 v2 = __ldg(reinterpret_cast<const float2 *>(vk) + i);
-    float s = q2.x, t = q2.y;
-    dacc_prod(s, t, a, df{v2.x, v2.y});
-    dacc_prod(s, t, b, vp[i]);
+    Raw r;
+    r.q = __ldg(reinterpret_cast<const float2 *>(q) + i);
+    r.v = __ldg(reinterpret_cast<const float2 *>(vk) + i);
+    r.p = *(reinterpret_cast<const float2 *>(vp) + i);
+    return r;
+  }
+  __device__ __forceinline__ Tc finish(long long i, const Raw &r) const {
+    // (s, t) = q / beta_k with the product's error kept (TwoProd)
+    float s = sc.hi * r.q.x;
+    float t = fmaf(sc.hi, r.q.x, -s);
+    t = fmaf(sc.hi, r.q.y, fmaf(sc.lo, r.q.x, t));
+    dacc_prod(s, t, a, df{r.v.x, r.v.y});
+    dacc_prod(s, t, b, df{r.p.x, r.p.y});
     const df v = df_from_sum(s, t);
     vp[i] = v;
     return to_real<Tc>(v);
   }
+  __device__ __forceinline__ Tc operator()(long long i) const { return finish(i, fetch(i)); }
+};
+
+// sources whose loads can be issued ahead of their stores (SrcLanczos over double-floats)
+template <class Src>
+struct has_fetch {
+  static constexpr bool value = false;
+};
+template <class Tc>
+struct has_fetch<SrcLanczos<Tc, df>> {
+  static constexpr bool value = true;
 };
 
 // vector kernels

@@ -58,9 +58,10 @@ struct StockhamPasses {
   }
 };
 
-// float32 transforms: three 512-thread blocks per SM (at most 40 registers); float64: two
+// float32 transforms: three 512-thread blocks per SM (at most 40 registers); float64, double-float
+// and the fused Lanczos source (its loads held in registers ahead of the stores): two
 template <class Tc, class Src, class Tout, bool XL, int LOGL>
-__global__ void __launch_bounds__(kNTD, sizeof(Tc) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kNTD, (sizeof(Tc) == 4 && !has_fetch<Src>::value) ? 3 : 2)
     k_dst_space(Src src, Tout *out, int len, long long nlines, int mx, long long m,
                 const Tc *tw, int PB, const State *S, int gk) {
   if (gate_closed(S, gk)) return;
@@ -86,7 +87,37 @@ __global__ void __launch_bounds__(kNTD, sizeof(Tc) == 4 ? 3 : 2)
   // one work item per (sequence, element): both lines of the pair, stored as one complex value
   // at e+1 and its negative at L-1-e (odd extension).  Index maps avoid divisions: len + 1 =
   // L/2 and PB are powers of two.
-  if (XL) {
+  if constexpr (XL && has_fetch<Src>::value) {
+    // the fused Lanczos source: every load of the thread's elements first (at most four work
+    // items of two lines each: PB * L <= 8 * kNTD), then the arithmetic, the v_{k+1} stores and
+    // the shared-memory writes, so that the loads are not held behind the stores
+    constexpr int kItems = 4;
+    typename Src::Raw ra[kItems], rb[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int idx = tid + u * kNTD;
+      const int pp = idx >> logH, e = idx & (half - 1);
+      const int la = 2 * pp, lb = la + 1;
+      const long long i0 = (line0 + la) * len + e;
+      if (idx < (PB << logH) && e < len) {
+        if (la < nl) ra[u] = src.fetch(i0);
+        if (lb < nl) rb[u] = src.fetch(i0 + len);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int idx = tid + u * kNTD;
+      const int pp = idx >> logH, e = idx & (half - 1);
+      if (idx >= (PB << logH) || e >= len) continue;
+      const int la = 2 * pp, lb = la + 1;
+      const long long i0 = (line0 + la) * len + e;
+      const Tc a = (la < nl) ? src.finish(i0, ra[u]) : Tc(0);
+      const Tc b = (lb < nl) ? src.finish(i0 + len, rb[u]) : Tc(0);
+      cpx<Tc> *bq = buf + pp * Ls;
+      bq[fft_pad<Tc>(e + 1)] = cpx<Tc>{a, b};
+      bq[fft_pad<Tc>(L - 1 - e)] = cpx<Tc>{-a, -b};
+    }
+  } else if (XL) {
     // lines 2pp and 2pp+1 are consecutive rows: one base pointer serves both
     for (int idx = tid; idx < (PB << logH); idx += kNTD) {
       const int pp = idx >> logH, e = idx & (half - 1);

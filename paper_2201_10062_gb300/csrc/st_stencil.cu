@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
 }
 
 // ------------------------------------------------------------------ double-float stencil
-// Mixed-precision MINRES: z_k is float32, the output p = Y T z_k / beta_k is a double-float.
+// Mixed-precision MINRES: z_k is float32, the output Y T z_k is a double-float; the 1/beta_k
+// of p = Y T z_k / beta_k is applied by the pass that reads it (SrcLanczos over double-floats).
 // Every face term a_f (z_c - z_f) uses the exact float difference (TwoSum) and a TwoProd
 // product with the double-float coefficient, and the terms are summed with the high parts
 // added error-free, so the result carries ~46 significant bits with no float64 instruction per
@@ -295,7 +296,6 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
   const int half = (n + 1) >> 1;
   const int k0 = blockIdx.z * kc;
   const int k1 = min(half, k0 + kc);
-  const df s = S->dfs[DFS_IB];
   acc_df D{0.f, 0.f};
   if (valid) {
     const int jz = D3 ? j / my : 0, jy = j - jz * my;
@@ -310,9 +310,8 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
     auto combine = [&](float c, float c1, float c2, df Kc, df K1) -> df {
       acc_df A{0.f, 0.f};
       if (theta) {
-        float dh, dl;
-        two_sum(c, -c1, dh, dl);
-        A.add(dh, dl);
+        // the exact difference c - c1 starts the sum
+        two_sum(c, -c1, A.s, A.t);
         if (g.th_exact) {
           // theta and 1 - theta are 0, 1/2 or 1: the products are exact scalings (the same
           // values add_prod gives), and a zero weight adds nothing
@@ -452,10 +451,10 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
           b1 = nb2;
         }
       }
-      out[(long long)kB * m + p] = df_mul(s, yA);
+      out[(long long)kB * m + p] = yA;
       D.add_prod(yA, zB);
       if (twin) {
-        out[(long long)kA * m + p] = df_mul(s, yB);
+        out[(long long)kA * m + p] = yB;
         D.add_prod(yB, cA);
       }
       pA = nA;

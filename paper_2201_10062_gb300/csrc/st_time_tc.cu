@@ -9,14 +9,13 @@
 // hi*hi + hi*lo + lo*hi accumulate in float32 in tensor memory.  Columns of B are scaled by a
 // power of two so that fp16 keeps its range; S is scaled by 8.
 //
-// One persistent block of 16 warps per SM keeps A (both parities, both pieces, 128 KB for
-// n = 256) in shared memory and walks column tiles of 32 as a two-stage software pipeline: the
-// two transforms have their own B operand buffer, tensor-memory accumulator and mbarrier, so the
-// second transform of tile i-1 runs on the tensor cores while tile i's first operand is built,
-// and the first transform of tile i runs while tile i-1 is scaled back and written out.  One
-// thread issues tcgen05.mma (M = 128, N = 32, K = 16, A and B from shared-memory descriptors, no
-// swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the mbarrier, and
-// every warp reads 32 rows x 16 columns of one parity's accumulators with tcgen05.ld.  Every
+// S (both parities, both pieces: 128 KB for n = 256) lives in tensor memory as the A operand of
+// tcgen05.mma; one block of 16 warps per SM runs two independent tile pipelines of 8 warps
+// (k_time_tc2, k_dst_tc_y2), each walking column tiles of 32 as a two-stage software pipeline.
+// One thread per pipeline issues tcgen05.mma (M = 128, N = 32, K = 16; B from a shared-memory
+// descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the
+// pipeline's mbarrier, and its warps read the accumulators with tcgen05.ld.  For 256 < n <= 512
+// (k_time_tc_long) S is streamed from global memory through a shared-memory ring instead.  Every
 // wait on an mbarrier is bounded; on timeout the block records ST_ERR_TIMEOUT in the MINRES
 // state and stops.  Before it releases its tensor memory it gives every MMA batch whose commit
 // it has not seen complete one more bounded wait: MMAs still in flight may be writing that
@@ -151,76 +150,7 @@ __device__ __forceinline__ void tc_release_cols(bool ok, bool pend1, uint32_t mb
   }
 }
 
-// Shared-memory layout, offsets in bytes from the dynamic base.
-struct TcSmem {
-  uint32_t sop, bop1, bop2, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar1, mbar2, tmem;
-  uint32_t stage;  // spatial-DST kernel only: staged input tile
-  uint32_t total;
-};
-
 constexpr int kYS = kTN + 1;  // padded row of the parity-split Y tile (conflict-free row writes)
-
-__host__ __device__ inline TcSmem tc_layout(int n) {
-  const int h = n / 2;
-  const uint32_t bop = 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
-  TcSmem L;
-  uint32_t o = 0;
-  L.sop = o;
-  o += 2u * 2u * kM * h * 2u;  // [parity][piece][128][h] fp16
-  L.bop1 = o;                  // operand of the first transform
-  o += bop;
-  L.bop2 = o;                  // operand of the second transform
-  o += bop;
-  L.ytile = o;
-  o += (uint32_t)n * kYS * 4u;  // float [parity][h][33]
-  L.colscale = o;
-  o += kTN * 4u;
-  L.colinv1 = o;
-  o += kTN * 4u;
-  L.colinv2 = o;
-  o += kTN * 4u;
-  L.colmax = o;
-  o += kTN * 4u;
-  L.tmu = o;
-  o += kTN * 4u;
-  L.mbar1 = o;
-  o += 8;
-  L.mbar2 = o;
-  o += 8;
-  L.tmem = o;
-  o += 16;
-  L.stage = 0;
-  L.total = o;
-  return L;
-}
-
-// Layout of the spatial-DST kernel for lines of `len` values (h = (len+1)/2 folded rows):
-// [A operands][B operand][Y tile][staged input][column scales][mbarrier][tmem address]
-__host__ __device__ inline TcSmem dst_layout(int len) {
-  const int h = (len + 1) / 2;
-  TcSmem L{};
-  uint32_t o = 0;
-  L.sop = o;
-  o += 2u * 2u * kM * h * 2u;
-  L.bop1 = o;
-  o += 2u * 2u * kTN * h * 2u;
-  L.ytile = o;
-  o += 2u * h * kYS * 4u;  // float [parity][h][33]
-  L.stage = o;
-  o += (uint32_t)len * kTN * 4u;  // float [len][32]
-  L.colscale = o;
-  o += kTN * 4u;
-  L.colinv1 = o;
-  o += kTN * 4u;
-  L.colmax = o;
-  o += kTN * 4u;
-  L.mbar1 = o;
-  o += 8;
-  L.tmem = o;
-  o += 8;
-  L.total = o;
-  return L;
-}
 
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const float *g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
@@ -239,108 +169,6 @@ __device__ __forceinline__ void split_h2(float a, float b, uint32_t &hi, uint32_
   const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
   hi = *reinterpret_cast<const uint32_t *>(&h);
   lo = *reinterpret_cast<const uint32_t *>(&l);
-}
-
-// Fold rows t and n-1-t of a float tile column (sum for odd k, difference for even k), scale each
-// column by a power of two so that its largest folded value lies in [2^13, 2^14), and write the
-// fp16 (hi, lo) pieces of both parities in canonical layout at `bop`, with 1/(scale * 8) in
-// `colinv`.  Thread (column c, block of 8 t) keeps its folded values in registers between the
-// maximum and the split, and stores each piece as one 16-byte chunk (8 consecutive K elements
-// of one row).  src(t, c) gives the value.
-// For odd n the middle element (t = n-1-t) pairs with nothing: U = x_t, and D is multiplied by
-// zero columns of A (sin(pi k (n+1)/2 / (n+1)) = 0 for even k).
-// The values build_b folds for thread tid: a[q] = src(t, c) and b[q] = src(n-1-t, c) with
-// t = tb*8 + q (b = 0 for the odd middle row); zeros beyond the h/8 t-blocks.
-template <class Src>
-__device__ __forceinline__ void load_b(int n, Src src, int tid, float (&a)[8], float (&b)[8]) {
-  const int h = (n + 1) >> 1, hb = h >> 3;
-  const int c = tid & (kTN - 1), tb = tid >> 5;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int t = tb * 8 + q;
-    a[q] = (tb < hb) ? src(t, c) : 0.f;
-    b[q] = (tb < hb && n - 1 - t != t) ? src(n - 1 - t, c) : 0.f;
-  }
-}
-
-__device__ __forceinline__ void build_b_vals(unsigned char *smem, const TcSmem &L,
-                                             uint32_t bop_off, uint32_t colinv_off, int n,
-                                             const float (&a)[8], const float (&b)[8], int tid) {
-  const int h = (n + 1) >> 1, hb = h >> 3;  // hb <= 16 t-blocks, one per thread group
-  unsigned int *colmax = reinterpret_cast<unsigned int *>(smem + L.colmax);
-  float *colscale = reinterpret_cast<float *>(smem + L.colscale);
-  float *colinv = reinterpret_cast<float *>(smem + colinv_off);
-  const int c = tid & (kTN - 1), tb = tid >> 5;
-  if (tid < kTN) colmax[tid] = 0u;
-  float u[8], d[8];
-  float mx = 0.f;
-  if (tb < hb) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      u[q] = a[q] + b[q];
-      d[q] = a[q] - b[q];
-      mx = fmaxf(mx, fmaxf(fabsf(u[q]), fabsf(d[q])));
-    }
-  }
-  __syncthreads();
-  if (tb < hb) atomicMax(&colmax[c], __float_as_uint(mx));
-  __syncthreads();
-  if (tid < kTN) {
-    const float m = __uint_as_float(colmax[tid]);
-    float s = 1.0f;
-    if (m > 0.f && isfinite(m)) {
-      int e;
-      frexpf(m, &e);             // m in [2^(e-1), 2^e)
-      s = ldexpf(1.0f, 14 - e);  // scaled maximum below 2^14
-    }
-    colscale[tid] = s;
-    colinv[tid] = 1.0f / (s * kSScale);  // exact: a power of two
-  }
-  __syncthreads();
-  if (tb < hb) {
-    const float s = colscale[c];
-    unsigned char *bop = smem + bop_off;
-    const uint32_t piece = (uint32_t)kTN * h * 2u;
-    uint32_t uh[4], ul[4], dh[4], dl[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      split_h2(u[2 * q] * s, u[2 * q + 1] * s, uh[q], ul[q]);
-      split_h2(d[2 * q] * s, d[2 * q + 1] * s, dh[q], dl[q]);
-    }
-    const uint32_t off = canon_off(c, tb * 8, h);
-    *reinterpret_cast<uint4 *>(bop + 0 * piece + off) = make_uint4(uh[0], uh[1], uh[2], uh[3]);
-    *reinterpret_cast<uint4 *>(bop + 1 * piece + off) = make_uint4(ul[0], ul[1], ul[2], ul[3]);
-    *reinterpret_cast<uint4 *>(bop + 2 * piece + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
-    *reinterpret_cast<uint4 *>(bop + 3 * piece + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
-  }
-}
-
-template <class Src>
-__device__ __forceinline__ void build_b(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
-                                        uint32_t colinv_off, int n, Src src, int tid) {
-  float a[8], b[8];
-  load_b(n, src, tid, a, b);
-  build_b_vals(smem, L, bop_off, colinv_off, n, a, b, tid);
-}
-
-// Issue the 2 parities x (h/16) K-steps x 3 piece products from the operand at `bop_off` into
-// the accumulators at tensor-memory column `dcol`, and commit to `mbar`.
-__device__ __forceinline__ void issue_mmas(unsigned char *smem, const TcSmem &L, uint32_t bop_off,
-                                           int h, uint32_t dcol, uint32_t mbar) {
-  const uint32_t sbase = smem_u32(smem + L.sop), bbase = smem_u32(smem + bop_off);
-  const uint32_t apiece = (uint32_t)kM * h * 2u, bpiece = (uint32_t)kTN * h * 2u;
-  for (int P = 0; P < 2; ++P) {
-    const uint32_t d = dcol + (uint32_t)(P * kTN);
-    const uint32_t a_hi = sbase + (2 * P) * apiece, a_lo = a_hi + apiece;
-    const uint32_t b_hi = bbase + (2 * P) * bpiece, b_lo = b_hi + bpiece;
-    for (int ks = 0; ks < h / 16; ++ks) {
-      const uint32_t koff = (uint32_t)ks * 256u;  // two core matrices along K
-      mma_f16(d, make_desc(a_hi + koff, h), make_desc(b_hi + koff, h), ks > 0 ? 1u : 0u);
-      mma_f16(d, make_desc(a_hi + koff, h), make_desc(b_lo + koff, h), 1u);
-      mma_f16(d, make_desc(a_lo + koff, h), make_desc(b_hi + koff, h), 1u);
-    }
-  }
-  mma_commit(mbar);
 }
 
 // Per-row (time frequency k) constants of 1/p(k, tau mu), hoisted out of the column loop.
@@ -380,179 +208,6 @@ __device__ __forceinline__ float inv_sym(const Spec<float> &sp, const SymRow &r,
     im = r.c;
   }
   return rsqrtf(re * re + im * im);
-}
-
-__global__ void __launch_bounds__(kNT, 1)
-    k_time_tc(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
-              State *S, int tmode, double *__restrict__ partials, int gk) {
-  __shared__ double red[32];
-  if (gate_closed(S, gk)) return;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int h = n >> 1;
-  const TcSmem L = tc_layout(n);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
-  const float *colinv1 = reinterpret_cast<const float *>(smem + L.colinv1);
-  const float *colinv2 = reinterpret_cast<const float *>(smem + L.colinv2);
-  float *ytile = reinterpret_cast<float *>(smem + L.ytile);
-  float *tmus = reinterpret_cast<float *>(smem + L.tmu);
-  const uint32_t mbar1 = smem_u32(smem + L.mbar1), mbar2 = smem_u32(smem + L.mbar2);
-  const long long ntiles = (m + kTN - 1) / kTN;
-  // A operands: straight copy of the precomputed canonical image
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(sop_g);
-    uint4 *dst = reinterpret_cast<uint4 *>(smem + L.sop);
-    const int cnt = (int)((2u * 2u * kM * h * 2u) / 16u);
-    for (int i = tid; i < cnt; i += kNT) dst[i] = src[i];
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar2) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-                     smem_u32(tmem_slot))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t dcol1 = tmem, dcol2 = tmem + 2u * kTN;  // 64 accumulator columns each
-  uint32_t ph1 = 0, ph2 = 0;
-  bool ok = true;
-  // a commit to mbar1 / mbar2 whose completion has not been seen (its phase is ph1 / ph2)
-  bool out1 = false, out2 = false;
-  float esum = 0.f, ecomp = 0.f;
-  // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
-  const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
-  const int r = (q << 5) + lane;
-  const int c0 = ch * 16;
-  const uint32_t lanes = (uint32_t)(q * 32) << 16, cview = (uint32_t)(P * kTN + c0);
-  const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
-  float *yrow = ytile + (P * h + r) * kYS;  // this thread's row of the parity-split tile
-  auto ycell = [&](int t, int c) -> float & { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
-  // second transform of the previous tile: accumulators -> Y tile (unscaled) -> columns of data
-  // (every issued MMA batch is waited for, with the bounded wait, before its resources are reused
-  // or released)
-  auto finish_second = [&](long long pj0, int pje) {
-    const bool w = __syncthreads_and(mbar_wait(mbar2, ph2) ? 1 : 0) != 0;
-    ok = ok && w;
-    if (!w) return;  // uniform: the accumulators may still be written; nothing is read
-    out2 = false;
-    ph2 ^= 1u;
-    fence_after();
-    float v[16];
-    tmem_ld16(dcol2 + lanes + cview, v);
-    if (r < h) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv2[c0 + c];
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // coalesced write-back: one warp per time row
-    for (int idx = tid; idx < n * kTN; idx += kNT) {
-      const int t = idx >> 5, c = idx & (kTN - 1);
-      if (c < pje) data[(long long)t * m + pj0 + c] = ycell(t, c);
-    }
-    __syncthreads();
-  };
-  bool pend = false;  // a second transform is in flight
-  long long pj0 = 0;
-  int pje = 0;
-  // this thread's input values of the next tile, loaded one tile ahead so that the loads are in
-  // flight while the previous tile finishes (tiles are disjoint: the in-place write-back of one
-  // tile never touches another's input)
-  float pa[8], pb[8];
-  auto load_tile = [&](long long tl) {
-    const long long jt = tl * kTN;
-    const int jn = (int)min((long long)kTN, m - jt);
-    load_b(n, [&](int t, int c) -> float { return (c < jn) ? data[(long long)t * m + jt + c] : 0.f; },
-           tid, pa, pb);
-  };
-  if ((long long)blockIdx.x < ntiles) load_tile(blockIdx.x);
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const long long j0 = tile * kTN;
-    const int je = (int)min((long long)kTN, m - j0);
-    if (tid < kTN) {
-      float t = 0.f;
-      if (tid < je) {
-        const long long j = j0 + tid;
-        const long long jy = j / mx, jx = j - jy * mx;
-        t = sp.mux[jx] + sp.muy[jy];
-      }
-      tmus[tid] = t;
-    }
-    // 1. first operand from the values loaded ahead (the previous tile's second transform is
-    // running)
-    build_b_vals(smem, L, L.bop1, L.colinv1, n, pa, pb, tid);
-    fence_async_smem();
-    __syncthreads();
-    fence_after();
-    if (tid == 0) issue_mmas(smem, L, L.bop1, h, dcol1, mbar1);
-    out1 = true;
-    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
-    // 2. while the first transform runs: finish the previous tile
-    if (pend) finish_second(pj0, pje);
-    // 3. first epilogue: unscale, spectral scaling, energy; scaled Y into the parity-split tile
-    {
-      const bool w = __syncthreads_and(mbar_wait(mbar1, ph1) ? 1 : 0) != 0;
-      ok = ok && w;
-      if (!w) break;  // uniform; the commit stays outstanding for the release below
-    }
-    out1 = false;
-    ph1 ^= 1u;
-    fence_after();
-    {
-      float v[16];
-      tmem_ld16(dcol1 + lanes + cview, v);
-      if (r < h) {
-        float rs = 0.f;
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float y = v[c] * colinv1[c0 + c];
-          const float yi = y * inv_sym(sp, sr, tmus[c0 + c]);
-          if (c0 + c < je) rs = fmaf(y, yi, rs);
-          yrow[c0 + c] = yi;
-        }
-        const float term = rs - ecomp;  // compensated running sum over rows and tiles
-        const float t = esum + term;
-        ecomp = (t - esum) - term;
-        esum = t;
-      }
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // 4. second operand from the scaled tile (row t = k - 1 lives in parity t & 1); start it
-    build_b(smem, L, L.bop2, L.colinv2, n, [&](int t, int c) -> float { return ycell(t, c); },
-            tid);
-    fence_async_smem();
-    __syncthreads();
-    fence_after();
-    if (tid == 0 && ok) issue_mmas(smem, L, L.bop2, h, dcol2, mbar2);
-    pend = ok;
-    out2 = out2 || ok;
-    pj0 = j0;
-    pje = je;
-  }
-  if (pend && ok) finish_second(pj0, pje);
-  tc_release_cols<128>(ok, out1, mbar1, ph1, out2, mbar2, ph2, tmem, S);
-  if (tmode != TM_NONE) {
-    const double e = (double)esum - (double)ecomp;
-    double tot;
-    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
-                               &tot) &&
-        tid == 0) {
-      if (tmode == TM_INIT || tmode == TM_RESTART)
-        minres_init_scalars_dev(S, tot);
-      else
-        minres_givens_dev(S, tot);
-    }
-  }
 }
 
 // ------------------------------------------------------------------ two tile pipelines per block
@@ -603,7 +258,7 @@ __device__ __forceinline__ bool group_sync_and(bool v, int id, int nthreads) {
 
 // Per-group shared-memory layout, offsets from the group's base (the base is 1024-aligned).
 struct TcGroupSmem {
-  uint32_t bop1, bop2, ytile, colscale, colinv1, colinv2, colmax, tmu, mbar1, mbar2, total;
+  uint32_t bop1, bop2, ytile, colinv1, colinv2, colmax, tmu, mbar1, mbar2, total;
 };
 
 __host__ __device__ inline TcGroupSmem tcg_layout(int n) {
@@ -617,14 +272,12 @@ __host__ __device__ inline TcGroupSmem tcg_layout(int n) {
   o += bop;
   L.ytile = o;
   o += (uint32_t)n * kYS * 4u;
-  L.colscale = o;
-  o += kTN * 4u;
   L.colinv1 = o;
   o += kTN * 4u;
   L.colinv2 = o;
   o += kTN * 4u;
-  L.colmax = o;
-  o += kTN * 4u;
+  L.colmax = o;  // 8 warps x 32 per-column partial maxima
+  o += 8u * kTN * 4u;
   L.tmu = o;
   o += kTN * 4u;
   L.mbar1 = o;
@@ -638,8 +291,12 @@ __host__ __device__ inline TcGroupSmem tcg_layout(int n) {
 // whole block: group 0, group 1, then the tensor-memory address slot
 __host__ __device__ inline uint32_t tcg_block_bytes(int n) { return kGroups * tcg_layout(n).total + 16u; }
 
-// Fold, scale and split of one tile for a group of 256 threads: thread (column c, t-block tb) with
-// tb = gt / 32 and tb + 8 (h/8 <= 16 t-blocks).  Same arithmetic as build_b_vals.
+// Fold, scale and split of one tile for a group of 256 threads: thread (column c = gt % 32,
+// t-blocks tb = gt / 32 and gt / 32 + 8 of 8 rows; h/8 <= 16 t-blocks).  A warp reads or writes
+// whole rows of 32 columns, so the global and staged loads are coalesced and the 16-byte operand
+// stores of a quarter-warp cover eight distinct rows.  The column maximum is reduced in one step:
+// each warp leaves its 32 per-column partial maxima in `part` (8 x 32 floats), the group passes
+// one barrier, and every thread combines the eight partials of its own column.
 __device__ __forceinline__ void load_b_g(int n, int gt, const float *data, long long m,
                                          long long j0, int je, float (&a)[2][8],
                                          float (&b)[2][8]) {
@@ -675,22 +332,20 @@ __device__ __forceinline__ void load_b_g_src(int n, int gt, Src src, float (&a)[
   }
 }
 
-template <class Lay>
-__device__ __forceinline__ void build_b_g(unsigned char *gs, const Lay &L,
-                                          uint32_t bop_off, uint32_t colinv_off, int n,
+// Fold (u = a + b, d = a - b), scale each column by a power of two so that its largest folded
+// value lies in [2^13, 2^14), and write the fp16 (hi, lo) pieces of both parities in canonical
+// layout at `bop`, with 1/(scale * 8) in `colinv` (written by warp 0; read after the caller's next
+// barrier).  `part` is the group's 8 x 32 partial-maximum array; one group barrier inside.
+__device__ __forceinline__ void build_b_g(unsigned char *bop, float *colinv, float *part, int n,
                                           const float (&a)[2][8], const float (&b)[2][8], int gt,
                                           int bar) {
   const int h = (n + 1) >> 1, hb = h >> 3;
-  unsigned int *colmax = reinterpret_cast<unsigned int *>(gs + L.colmax);
-  float *colscale = reinterpret_cast<float *>(gs + L.colscale);
-  float *colinv = reinterpret_cast<float *>(gs + colinv_off);
-  const int c = gt & (kTN - 1);
-  if (gt < kTN) colmax[gt] = 0u;
+  const int c = gt & (kTN - 1), w = gt >> 5;
   float u[2][8], d[2][8];
   float mx = 0.f;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int tb = (gt >> 5) + 8 * it;
+    const int tb = w + 8 * it;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       u[it][q] = a[it][q] + b[it][q];
@@ -698,27 +353,21 @@ __device__ __forceinline__ void build_b_g(unsigned char *gs, const Lay &L,
       if (tb < hb) mx = fmaxf(mx, fmaxf(fabsf(u[it][q]), fabsf(d[it][q])));
     }
   }
+  part[w * kTN + c] = mx;
   group_sync(bar, kGT);
-  atomicMax(&colmax[c], __float_as_uint(mx));
-  group_sync(bar, kGT);
-  if (gt < kTN) {
-    const float mm = __uint_as_float(colmax[gt]);
-    float sc = 1.0f;
-    if (mm > 0.f && isfinite(mm)) {
-      int e;
-      frexpf(mm, &e);
-      sc = ldexpf(1.0f, 14 - e);
-    }
-    colscale[gt] = sc;
-    colinv[gt] = 1.0f / (sc * kSScale);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) mx = fmaxf(mx, part[k * kTN + c]);
+  float sc = 1.0f;
+  if (mx > 0.f && isfinite(mx)) {
+    int e;
+    frexpf(mx, &e);
+    sc = ldexpf(1.0f, 14 - e);
   }
-  group_sync(bar, kGT);
-  const float sc = colscale[c];
-  unsigned char *bop = gs + bop_off;
+  if (w == 0) colinv[c] = 1.0f / (sc * kSScale);
   const uint32_t piece = (uint32_t)kTN * h * 2u;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int tb = (gt >> 5) + 8 * it;
+    const int tb = w + 8 * it;
     if (tb < hb) {
       uint32_t uh[4], ul[4], dh[4], dl[4];
 #pragma unroll
@@ -868,7 +517,8 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       tmus[gt] = t;
     }
-    build_b_g(gs, L, L.bop1, L.colinv1, n, pa, pb, gt, bar);
+    build_b_g(gs + L.bop1, reinterpret_cast<float *>(gs + L.colinv1),
+              reinterpret_cast<float *>(gs + L.colmax), n, pa, pb, gt, bar);
     fence_async_smem();
     group_sync(bar, kGT);
     fence_after();
@@ -912,7 +562,8 @@ __global__ void __launch_bounds__(kNT, 1)
     {
       float a2[2][8], b2[2][8];
       load_b_g_src(n, gt, [&](int t, int c) -> float { return ycell(t, c); }, a2, b2);
-      build_b_g(gs, L, L.bop2, L.colinv2, n, a2, b2, gt, bar);
+      build_b_g(gs + L.bop2, reinterpret_cast<float *>(gs + L.colinv2),
+                reinterpret_cast<float *>(gs + L.colmax), n, a2, b2, gt, bar);
     }
     fence_async_smem();
     group_sync(bar, kGT);
@@ -939,121 +590,11 @@ __global__ void __launch_bounds__(kNT, 1)
   }
 }
 
-// Spatial DST-I along y on the tensor cores (float32 transforms of the mixed-precision
-// preconditioner, Sec. 3.1.1 steps 1 and 3 along y), in place: the lines of one time level at
-// fixed x are len = my values mx apart, and a tile is 32 adjacent lines (x0..x0+31) of one time
-// level.  Same folded two-parity product as the time kernel, with S_len: one transform, no
-// scaling.  The next tile's input is staged by cp.async while the current one is transformed.
-__global__ void __launch_bounds__(kNT, 1)
-    k_dst_tc_y(const float *data, float *out, int len, int mx, long long m, long long nplanes,
-               const __half *sop_g, State *S, int gk) {
-  if (gate_closed(S, gk)) return;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int h = (len + 1) >> 1;
-  const TcSmem L = dst_layout(len);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
-  const float *colinv = reinterpret_cast<const float *>(smem + L.colinv1);
-  float *stage = reinterpret_cast<float *>(smem + L.stage);
-  float *ytile = reinterpret_cast<float *>(smem + L.ytile);
-  const uint32_t mbar = smem_u32(smem + L.mbar1);
-  const int tpp = (mx + kTN - 1) / kTN;  // tiles per time level
-  const long long ntiles = nplanes * tpp;
-  auto tile_at = [&](long long tile, long long &base, int &je) {
-    const long long t = tile / tpp;
-    const int x0 = (int)(tile - t * tpp) * kTN;
-    base = t * m + x0;
-    je = min(kTN, mx - x0);
-  };
-  auto prefetch = [&](long long tile) {
-    long long base;
-    int je;
-    tile_at(tile, base, je);
-    const uint32_t sbase = smem_u32(stage);
-    for (int idx = tid; idx < len * kTN; idx += kNT) {
-      const int e = idx >> 5, c = idx & (kTN - 1);
-      if (c < je)
-        cp_async4(sbase + 4u * (uint32_t)idx, data + base + (long long)e * mx + c);
-      else
-        stage[idx] = 0.f;
-    }
-    cp_async_commit();
-  };
-  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x);
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(sop_g);
-    uint4 *dst = reinterpret_cast<uint4 *>(smem + L.sop);
-    const int cnt = (int)((2u * 2u * kM * h * 2u) / 16u);
-    for (int i = tid; i < cnt; i += kNT) dst[i] = src[i];
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
-                     smem_u32(tmem_slot))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-  uint32_t phase = 0;
-  bool ok = true;
-  bool outstanding = false;  // a commit to mbar whose completion has not been seen
-  // accumulator view of this warp: TMEM lanes 32q..32q+31 (rows r), parity P, columns 16ch..
-  const int q = warp & 3, P = (warp >> 2) & 1, ch = warp >> 3;
-  const int r = (q << 5) + lane;
-  const int c0 = ch * 16;
-  const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN + c0);
-  const bool row_ok = r < h && (P == 0 ? 2 * r + 1 : 2 * r + 2) <= len;
-  float *yrow = ytile + (P * h + r) * kYS;
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    long long base;
-    int je;
-    tile_at(tile, base, je);
-    cp_async_wait_all();
-    __syncthreads();
-    build_b(smem, L, L.bop1, L.colinv1, len,
-            [&](int t, int c) -> float { return stage[t * kTN + c]; }, tid);
-    fence_async_smem();
-    __syncthreads();
-    fence_after();
-    if (tid == 0) issue_mmas(smem, L, L.bop1, h, tmem, mbar);
-    outstanding = true;
-    // the stage buffer is free: load the next tile while the tensor cores work
-    if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
-    ok = __syncthreads_and(mbar_wait(mbar, phase) ? 1 : 0) != 0;
-    if (!ok) break;  // uniform; the commit stays outstanding for the release below
-    outstanding = false;
-    phase ^= 1u;
-    fence_after();
-    float v[16];
-    tmem_ld16(tl, v);
-    if (row_ok) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) yrow[c0 + c] = v[c] * colinv[c0 + c];
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    // coalesced write-back: output row e holds coefficient k = e + 1 (parity e & 1)
-    for (int idx = tid; idx < len * kTN; idx += kNT) {
-      const int e = idx >> 5, c = idx & (kTN - 1);
-      if (c < je) out[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
-    }
-  }
-  cp_async_wait_all();
-  tc_release_cols<64>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
-}
-
 // Two-pipeline form of k_dst_tc_y: S_len (both parities, hi and lo) in tensor memory as the A
 // operand, two groups of 8 warps, each with its own staged input tile, B operand, Y tile,
 // accumulator (64 columns) and named barrier.  Same arithmetic and output.
 struct TcYSmem {
-  uint32_t bop, ytile, stage, colscale, colinv, colmax, mbar, total;
+  uint32_t bop, ytile, stage, colinv, colmax, mbar, total;
 };
 
 __host__ __device__ inline TcYSmem tcy_layout(int len) {
@@ -1066,12 +607,10 @@ __host__ __device__ inline TcYSmem tcy_layout(int len) {
   o += 2u * h * kYS * 4u;
   L.stage = o;
   o += (uint32_t)len * kTN * 4u;
-  L.colscale = o;
-  o += kTN * 4u;
   L.colinv = o;
   o += kTN * 4u;
-  L.colmax = o;
-  o += kTN * 4u;
+  L.colmax = o;  // 8 warps x 32 per-column partial maxima
+  o += 8u * kTN * 4u;
   L.mbar = o;
   o += 8;
   L.total = (o + 1023u) & ~1023u;
@@ -1173,7 +712,8 @@ __global__ void __launch_bounds__(kNT, 1)
     {
       float a[2][8], b[2][8];
       load_b_g_src(len, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, b);
-      build_b_g(gs, L, L.bop, L.colinv, len, a, b, gt, bar);
+      build_b_g(gs + L.bop, reinterpret_cast<float *>(gs + L.colinv),
+                reinterpret_cast<float *>(gs + L.colmax), len, a, b, gt, bar);
     }
     fence_async_smem();
     group_sync(bar, kGT);
@@ -1555,8 +1095,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
 // within the 227 KB a block may opt into
 bool time_tc_supported(int n) {
-  return n >= 32 && n <= 256 && (n % 32) == 0 && tc_layout(n).total + 1024u <= 227u * 1024u &&
-         tcg_block_bytes(n) + 1024u <= 227u * 1024u;
+  return n >= 32 && n <= 256 && (n % 32) == 0 && tcg_block_bytes(n) + 1024u <= 227u * 1024u;
 }
 
 size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * ((n + 1) / 2); }
@@ -1591,7 +1130,6 @@ void time_tc_build_sop(int len, unsigned short *out) {
 bool dst_tc_supported(int len) {
   const int L1 = len + 1;
   return (L1 == 32 || L1 == 64 || L1 == 128 || L1 == 256) &&
-         dst_layout(len).total + 1024u <= 227u * 1024u &&
          tcy_block_bytes(len) + 1024u <= 227u * 1024u;
 }
 
@@ -1606,41 +1144,22 @@ int time_tc_grid() {
   return sms;
 }
 
+// two tile pipelines per block, S_n in tensor memory
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st) {
-  static const bool v1 = [] {
-    const char *e = std::getenv("ST_TIME_TC_V1");
-    return e && e[0] == '1';
-  }();
-  if (!v1) {
-    // two tile pipelines per block, S_n in tensor memory
-    const uint32_t smem_bytes = tcg_block_bytes(g.n);
-    cudaError_t e = cudaFuncSetAttribute(k_time_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    const long long ntiles = (g.m + kTN - 1) / kTN;
-    const long long need = (ntiles + kGroups - 1) / kGroups;
-    int grid = time_tc_grid();
-    if (need < grid) grid = (int)need;
-    prof_begin(KC_TIME, st);
-    k_time_tc2<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
-                                              reinterpret_cast<const __half *>(sop), S, tmode,
-                                              partials, gk);
-    prof_end(st);
-    return cudaGetLastError();
-  }
-  const uint32_t smem_bytes = tc_layout(g.n).total;
-  cudaError_t e = cudaFuncSetAttribute(k_time_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const uint32_t smem_bytes = tcg_block_bytes(g.n);
+  cudaError_t e = cudaFuncSetAttribute(k_time_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = (g.m + kTN - 1) / kTN;
+  const long long need = (ntiles + kGroups - 1) / kGroups;
   int grid = time_tc_grid();
-  if (ntiles < grid) grid = (int)ntiles;
+  if (need < grid) grid = (int)need;
   prof_begin(KC_TIME, st);
-  k_time_tc<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
-                                        reinterpret_cast<const __half *>(sop), S, tmode, partials,
-                                        gk);
+  k_time_tc2<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
+                                            reinterpret_cast<const __half *>(sop), S, tmode,
+                                            partials, gk);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -1650,45 +1169,26 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
 bool dst_tc_len_supported(int len) {
   if (dst_tc_supported(len)) return true;
   return len >= 32 && len <= 256 && (len % 32) == 0 &&
-         dst_layout(len).total + 1024u <= 227u * 1024u &&
          tcy_block_bytes(len) + 1024u <= 227u * 1024u;
 }
 
 // One DST-I of length len along lines `stride` apart, nplanes planes `plane` apart, 32 adjacent
-// lines per tile (k_dst_tc_y), from `in` to `out` (the same array, or one that does not overlap).
+// lines per tile (k_dst_tc_y2, two tile pipelines per block, S_len in tensor memory), from `in`
+// to `out` (the same array, or one that does not overlap).
 cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride, long long plane,
                                 long long nplanes, const unsigned short *sop, State *S, int gk,
                                 int kc, cudaStream_t st) {
-  static const bool v1 = [] {
-    const char *e = std::getenv("ST_TIME_TC_V1");
-    return e && e[0] == '1';
-  }();
-  if (!v1) {
-    // two tile pipelines per block, S_len in tensor memory
-    const uint32_t smem_bytes = tcy_block_bytes(len);
-    cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
-    const long long need = (ntiles + kGroups - 1) / kGroups;
-    int grid = time_tc_grid();
-    if (need < grid) grid = (int)need;
-    prof_begin(kc, st);
-    k_dst_tc_y2<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
-                                               reinterpret_cast<const __half *>(sop), S, gk);
-    prof_end(st);
-    return cudaGetLastError();
-  }
-  const uint32_t smem_bytes = dst_layout(len).total;
-  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const uint32_t smem_bytes = tcy_block_bytes(len);
+  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
+  const long long need = (ntiles + kGroups - 1) / kGroups;
   int grid = time_tc_grid();
-  if (ntiles < grid) grid = (int)ntiles;
+  if (need < grid) grid = (int)need;
   prof_begin(kc, st);
-  k_dst_tc_y<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
-                                            reinterpret_cast<const __half *>(sop), S, gk);
+  k_dst_tc_y2<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
+                                             reinterpret_cast<const __half *>(sop), S, gk);
   prof_end(st);
   return cudaGetLastError();
 }
