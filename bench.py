@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import platform
 import statistics
@@ -51,22 +52,25 @@ ITER_BYTES = {"fp64": 96, "mixed": 84}
 OUTER_BYTES = 24
 # Bytes per unknown each launch of a kernel class moves (its own reads and writes of length-N
 # vectors; the implementation's launches, not the algorithm's floor), mixed / float64.
+# The mixed single solve's update applies G iterations per launch (grouped update): its bytes
+# are counted per step by update_bytes_per_step instead.
 CLASS_BYTES = {
     "mixed": {"stencil": 12, "lanczos_dst_x": 36, "dst_x": 8, "dst_y": 8, "time_dst_scale": 8,
-              "update": 44, "residual": 24},
+              "residual": 24},
     "fp64": {"stencil": 16, "lanczos_dst_x": 40, "dst_x": 16, "dst_y": 16, "time_dst_scale": 16,
              "update": 48, "residual": 24},
 }
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of every
 # launch of one mixed 2D Crank-Nicolson solve at 255^2 x 256), per kernel class, for the kernels
 # whose code is unchanged since: profiles/dram_traffic_mixed_cn2d_255x255_n256.md
-NCU_TRAFFIC = {("mixed", "stencil"): 136.3e6, ("mixed", "lanczos_dst_x"): 540.0e6,
-               ("mixed", "dst_x"): 70.3e6, ("mixed", "dst_y"): 72.6e6,
-               ("mixed", "time_dst_scale"): 72.9e6, ("mixed", "update"): 661.7e6,
-               ("mixed", "residual"): 373.2e6}
-# the same capture summed over one MINRES iteration (stencil, fused Lanczos x pass, y, time, y,
-# x, update), per unknown
-NCU_ITER_TRAFFIC = {"mixed": 97.7}
+NCU_TRAFFIC = {("mixed", "stencil"): 136.0e6, ("mixed", "lanczos_dst_x"): 539.6e6,
+               ("mixed", "dst_x"): 70.3e6, ("mixed", "dst_y"): 72.9e6,
+               ("mixed", "time_dst_scale"): 72.9e6, ("mixed", "residual"): 373.3e6}
+# the grouped update's DRAM bytes per solve (its six launches in the same capture)
+NCU_TRAFFIC_STEP = {("mixed", "update"): 6 * 1212.5e6}
+# the same capture summed over the solve's iteration kernels (stencil, fused Lanczos x pass, y,
+# time, y, x, grouped update), per unknown and iteration
+NCU_ITER_TRAFFIC = {"mixed": 71.5}
 # steps of the per-kernel-class profile, run after each timed region
 PROF_STEPS = 3
 
@@ -341,9 +345,19 @@ def _timed(stream, fn, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
-def kernel_table(prof, precision, unknowns, steps, peak):
+def update_bytes_per_step(unknowns, iterations, group):
+    """Bytes the grouped update moves in one solve of `iterations` MINRES iterations: each launch
+    reads its pending z_j (4 B each) and, once, the two latest directions and x (24 B), and
+    writes the directions and x (24 B).  ceil(iterations / group) launches is the fewest that
+    apply every update; a solve with several refinement steps may take one more per step, so the
+    GB/s derived from this count is a lower bound."""
+    return (4 * iterations + 48 * math.ceil(iterations / group)) * unknowns
+
+
+def kernel_table(prof, precision, unknowns, steps, peak, iterations=None, group=None):
     """Per kernel class: time and launches per step, and for the classes with a fixed byte count
-    per launch, that count, the achieved GB/s over the average launch and its fraction of HBM."""
+    per launch, that count, the achieved GB/s over the average launch and its fraction of HBM.
+    The mixed path's grouped update gets bytes and GB/s per step (iterations and group given)."""
     total_ms = sum(v["ms"] for v in prof.values())
     out = {}
     for k, v in prof.items():
@@ -356,6 +370,13 @@ def kernel_table(prof, precision, unknowns, steps, peak):
             row.update({"avg_launch_us": avg_ms * 1e3, "bytes_per_launch": b * unknowns,
                         "achieved_gbs": gbs, "frac_hbm": gbs / peak["hbm_gbs"],
                         "traffic": NCU_TRAFFIC.get((precision, k))})
+        elif (precision, k) == ("mixed", "update") and iterations and v["ms"] > 0:
+            bstep = update_bytes_per_step(unknowns, iterations, group)
+            gbs = bstep / (v["ms"] / steps * 1e-3) / 1e9
+            row.update({"avg_launch_us": v["ms"] / max(v["timed"], 1) * 1e3,
+                        "iterations_per_launch": group, "bytes_per_step": bstep,
+                        "achieved_gbs": gbs, "frac_hbm": gbs / peak["hbm_gbs"],
+                        "traffic_per_step": NCU_TRAFFIC_STEP.get((precision, k))})
         out[k] = row
     return out
 
@@ -454,9 +475,11 @@ def run_ours(args, world, rank, local):
     roof["scope"] = ("whole solve: every kernel of every MINRES iteration plus the refinement "
                      "residuals, algorithmic bytes of Sec. 8(d)")
     # DRAM bytes of one iteration's launches from ncu, per iteration like alg_bytes_per_iteration
-    roof["traffic"] = NCU_ITER_TRAFFIC["mixed"] * N if (w.mx, w.n) == (255, 256) else None
+    it_traffic = NCU_ITER_TRAFFIC["mixed"]
+    roof["traffic"] = it_traffic * N if it_traffic and (w.mx, w.n) == (255, 256) else None
     roof["traffic_unit"] = "bytes per MINRES iteration"
-    kern = kernel_table(mixed["prof"], "mixed", N, PROF_STEPS, peaks)
+    kern = kernel_table(mixed["prof"], "mixed", N, PROF_STEPS, peaks, iterations=iters,
+                        group=P.update_group())
     # kernels launched per step (the same solve every step), counted by the profiled steps
     launches = sum(v["launches"] for v in mixed["prof"].values()) / PROF_STEPS
     fp = results["fp64"]
@@ -479,7 +502,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": dict(CONFIG, precision="mixed",
                        parallelism=("replicas" if world > 1 else "single"),
-                       l2="no flush: every vector (133 MB) and the ~1.1 GB working set exceed L2"),
+                       l2="no flush: every vector (133 MB) and the ~1.6 GB working set exceed L2"),
         "iterations": iters,
         "outer_steps": outer,
         "true_rel_res": mixed["stats"]["true_rel_res"],

@@ -109,9 +109,12 @@ typedef struct st_stats {
 
 typedef struct st_handle st_handle;
 
-/* Validate *prob, allocate the device workspace (about 9 space-time vectors of float64, fewer
- * in ST_MIXED) and precompute face coefficients, spectral tables and twiddles.  a_nodal is read
- * during the call only.  Synchronous.  Returns ST_ERR_ARG for unsupported sizes. */
+/* Validate *prob, allocate the device workspace (about 9 space-time vectors of float64; in
+ * ST_MIXED about 12.5, of which 7 float32 vectors hold the preconditioned vectors of the MINRES
+ * iterations whose direction/solution update is still pending: st_solve applies those updates 8
+ * iterations at a time, ST_UPDATE_GROUP=1..8 sets the group and with it the vectors kept) and
+ * precompute face coefficients, spectral tables and twiddles.  a_nodal is read during the call
+ * only.  Synchronous.  Returns ST_ERR_ARG for unsupported sizes. */
 int st_setup(const st_problem *prob, st_handle **out);
 
 /* Free the workspace (synchronises the handle's stream first).  NULL is ignored. */

@@ -33,6 +33,18 @@ EXPORTS = (
 )
 KERNEL_CLASSES = ("stencil", "lanczos_dst_x", "dst_x", "dst_y", "time_dst_scale", "update", "residual",
                   "aux")
+# Most MINRES iterations one grouped direction/solution update applies (the library's ring).
+UPDATE_GROUP_MAX = 8
+
+
+def update_group() -> int:
+    """Iterations per grouped update of a mixed single solve, as st_setup reads it: the
+    ST_UPDATE_GROUP environment variable when it holds 1..8, else 8."""
+    try:
+        g = int(os.environ.get("ST_UPDATE_GROUP", "0"))
+    except ValueError:
+        g = 0
+    return g if 1 <= g <= UPDATE_GROUP_MAX else UPDATE_GROUP_MAX
 
 
 class StProblem(ctypes.Structure):

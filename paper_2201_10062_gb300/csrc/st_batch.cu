@@ -96,7 +96,7 @@ cudaError_t iteration(st_handle *h, int c, cudaStream_t st) {
   if ((e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials,
                                                  st)) != cudaSuccess)
     return e;
-  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, 0, st);
+  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
 }
 
 // refinement block: x (float64) <- x (df); r <- Y f_H - Y T x with decision; restart if asked
@@ -261,7 +261,7 @@ int st_setup_batch(const st_problem *probs, int count, void *stream, st_batch **
     // caller's stream; the batch solve passes its internal streams explicitly
     st_problem p = probs[i];
     p.stream = stream;
-    int r = st_setup(&p, &b->h[i]);
+    int r = setup_handle(&p, &b->h[i], 1);
     if (r) return fail(r);
     // launch shapes per (size, precision), cached across instances of the same shape
     r = st_autotune(b->h[i], 5);

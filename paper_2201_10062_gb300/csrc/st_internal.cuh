@@ -90,6 +90,9 @@ struct Spec {
 
 // Device-resident MINRES scalars.  Written only by the last block of a kernel (the
 // "last block" reduction pattern) or by the host between solves.
+// Most iterations whose direction/solution updates one grouped update pass applies.
+constexpr int kUpdRing = 8;
+
 struct State {
   double alpha, beta, beta_prev, beta1, eta;
   double c1, s1, c2, s2;               // rotations k-1 and k-2
@@ -109,10 +112,13 @@ struct State {
   double inner_floor;                  // lowest target of an inner run (device-side restarts)
   double rho;                          // last true relative residual
   int done, restart, total, outer, maxit_total;
-  int pad2;
+  int upd;                             // grouped update: iterations whose d/x update is applied
   // double-float copies of the per-iteration scalars, refreshed by whoever sets the float64
   // values, so that the double-float vector kernels read them without float64 instructions
   df dfs[8];
+  // grouped update (mixed single solves): the direction/solution scalars of iteration j, in
+  // slot (j - 1) % kUpdRing as {dz, d1, d2, xc}, kept until the pass that applies them
+  df ucoef[kUpdRing][4];
   // Set (never cleared on the device) by a tensor-core kernel whose bounded waits ran out twice,
   // so that it exited without releasing its tensor memory (an MMA might still have been writing
   // it).  It is the last member: the host pushes the state up to it (kStatePushBytes) and so
@@ -135,7 +141,7 @@ __host__ __device__ inline void refresh_df(State *S) {
   S->dfs[DFS_XC] = df_of_double(S->xc);
 }
 
-enum { CNT_STENCIL = 0, CNT_TIME = 1, CNT_RESID = 2, CNT_NORM = 3 };
+enum { CNT_STENCIL = 0, CNT_TIME = 1, CNT_RESID = 2, CNT_NORM = 3, CNT_UPD = 4 };
 
 // Last-block completion: every block writes its partial, the last block to arrive sums all
 // partials in a fixed order (deterministic) and returns the total to thread 0.
@@ -260,6 +266,11 @@ __device__ inline void minres_givens_dev(State *S, double E) {
   S->est = fabs(S->eta) / S->beta1;
   if (S->est <= S->target || bnext == 0.0 || k >= S->maxit) S->finish = 1;
   refresh_df(S);
+  df *uc = S->ucoef[(k - 1) % kUpdRing];
+  uc[0] = S->dfs[DFS_DZ];
+  uc[1] = S->dfs[DFS_D1];
+  uc[2] = S->dfs[DFS_D2];
+  uc[3] = S->dfs[DFS_XC];
 }
 
 
@@ -348,6 +359,14 @@ struct PrecPlan {
 // overrides it, for measurements).
 double inner_floor();
 
+// Iterations per grouped direction/solution update of a mixed single solve: kUpdRing unless
+// ST_UPDATE_GROUP (1..kUpdRing) sets it, for measurements.
+int update_group();
+
+// st_setup with an explicit update group (the batched solve's instance handles take 1: their
+// captured loop updates every iteration and keeps no extra z vectors)
+int setup_handle(const st_problem *prob, st_handle **out, int ugroup);
+
 // A device on which a tensor-core kernel kept its tensor memory after a timeout is closed: every
 // later call there returns ST_ERR_TIMEOUT (the host learns it from State::tmem_held).
 void close_device(int dev);
@@ -420,10 +439,9 @@ cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const dou
 // done; r = Y f_H - Y T x into r_out and, in the last block, the done/restart decision
 cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const double *fH,
                                State *S, double *partials, cudaStream_t st);
-// kidx > 0: run only if the Givens step of iteration kidx happened (S->k >= kidx); kidx = 0:
-// run while the MINRES run is active
+// one iteration's direction/solution update (batched solves), while the MINRES run is active
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, int kidx, cudaStream_t st);
+                             State *S, cudaStream_t st);
 cudaError_t launch_flip_to_df(const Geom &g, const double *src, df *dst, cudaStream_t st);
 cudaError_t launch_df_to_double(long long N, const df *src, double *dst, cudaStream_t st);
 
@@ -561,11 +579,11 @@ struct st_handle {
   st::State *hS;         // pinned host mirror of S
   int partials_len;
   st::Prof prof;         // kernel-class timing (off unless st_profile_begin was called)
-  // ST_MIXED with ST_OVERLAP_UPDATE=1: the solution/direction update of iteration k runs on this
-  // side stream, concurrently with the inverse transforms of iteration k and the stencil of
-  // iteration k + 1 (null: serial order on the caller's stream)
-  cudaStream_t ustream;
-  cudaEvent_t ev_givens[2], ev_update[2];  // indexed by the parity of k
+  // ST_MIXED single solves: iterations per grouped direction/solution update (1..kUpdRing), and
+  // the z vectors beyond Z[0], Z[1] that keep the pending iterations' z_j (ugroup - 1 of them):
+  // z_j lives in slot (j - 1) % (ugroup + 1) of Z[0], Z[1], Zx[0], ...
+  int ugroup;
+  float *Zx[st::kUpdRing - 1];
 };
 
 

@@ -8,7 +8,8 @@
 //                fused into the load of the first spatial DST, then z_{k+1} = P^-1 vhat_{k+1},
 //                beta_{k+1}^2 = <vhat_{k+1}, z_{k+1}> and the Givens step (st_prec.cu,
 //                st_time_tc.cu)
-//   3. update:   d_k = (z_k/beta_k - delta d_{k-1} - eps d_{k-2})/rho,  x += c eta d_k
+//   3. update:   d_k = (z_k/beta_k - delta d_{k-1} - eps d_{k-2})/rho,  x += c eta d_k; the
+//                mixed single solve applies it for G iterations at once (k_update_group_df)
 // Scalars never leave the device inside the loop; the host reads the state after each chunk of
 // iterations to learn whether the device-side stopping test has fired, and sizes the next chunk
 // from the observed convergence rate.  Kernels launched after that point return at entry.
@@ -95,11 +96,8 @@ namespace {
 // the per-element arithmetic runs on the float32 pipes (see st_df.cuh).
 __global__ void __launch_bounds__(kNT)
     k_update_df(long long N, const float *__restrict__ z, const df *__restrict__ d1,
-                df *__restrict__ d2, df *__restrict__ x, const State *S, int kidx) {
-  // kidx > 0: the update of iteration kidx, launched on a side stream after its Givens step;
-  // it runs iff that step happened (the concurrent stencil of the next iteration may already
-  // have cleared `active`)
-  if (kidx > 0 ? S->k < kidx : !S->active) return;
+                df *__restrict__ d2, df *__restrict__ x, const State *S) {
+  if (!S->active) return;
   const df cz = S->dfs[DFS_DZ], c1 = S->dfs[DFS_D1], c2 = S->dfs[DFS_D2], cx = S->dfs[DFS_XC];
   for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
        i += (long long)gridDim.x * kNT) {
@@ -119,6 +117,96 @@ __global__ void __launch_bounds__(kNT)
     float xs = xo.hi, xt = xo.lo;
     dacc_prod(xs, xt, cx, d);
     x[i] = df_from_sum(xs, xt);
+  }
+}
+
+// Grouped direction and solution update (mixed single solves).  The direction recurrence
+// d_j = dz_j z_j + d1_j d_{j-1} + d2_j d_{j-2} and the solution update x += xc_j d_j consume the
+// preconditioned vectors z_j but feed nothing back into the Lanczos recurrence, so the updates
+// of up to kUpdRing iterations are applied in one pass: each element reads its pending z_j (one
+// float32 vector per iteration), the two latest directions and x once, runs the recurrence in
+// registers with every iteration's scalars (State::ucoef) and writes back the two latest
+// directions and x.  With G iterations per pass the update moves 4 + 48/G bytes per unknown and
+// iteration instead of 44, and every element goes through the same float32 operations in the
+// same order, whatever G (the per-iteration kernel k_update_df adds its first product to a zero
+// sum; here the sum starts as that product, which differs at most in the sign of a zero).
+//
+// The pending iterations are upd + 1 .. k of the device state: the pass reads both counters at
+// entry and its last block to finish sets upd = k, so a pass with nothing pending returns at once
+// and a pass never applies an iteration twice.  da holds d_upd and db d_{upd-1} on entry, d_k and
+// d_{k-1} on exit; z_j is in zr.p[(j - 1) % zr.len].
+struct ZRing {
+  const float *p[kUpdRing + 1];
+  int len;
+};
+
+// a shared-memory load the compiler may not hoist out of the element loop: holding every
+// iteration's coefficients in registers (64 of them) would halve the resident warps
+__device__ __forceinline__ float4 lds_f4(const float4 *p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+
+__global__ void __launch_bounds__(kNT, 4)
+    k_update_group_df(long long N, ZRing zr, df *__restrict__ da, df *__restrict__ db,
+                      df *__restrict__ x, State *S) {
+  // per pending iteration: {dz.hi, dz.lo, d1.hi, d1.lo}, {d2.hi, d2.lo, xc.hi, xc.lo}
+  __shared__ float4 sc[kUpdRing][2];
+  __shared__ const float *sz[kUpdRing];
+  const int kd = S->k, u = S->upd;
+  const int np = kd - u;
+  if (np <= 0 || np > kUpdRing) return;  // nothing pending (more than a ring never happens)
+  if (threadIdx.x < 2 * np) {
+    const int j = threadIdx.x >> 1, h = threadIdx.x & 1;
+    const df *c = S->ucoef[(u + j) % kUpdRing] + 2 * h;
+    sc[j][h] = make_float4(c[0].hi, c[0].lo, c[1].hi, c[1].lo);
+  }
+  if (threadIdx.x < np) sz[threadIdx.x] = zr.p[(u + threadIdx.x) % zr.len];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kNT) {
+    float zv[kUpdRing];
+#pragma unroll
+    for (int j = 0; j < kUpdRing; ++j)
+      if (j < np) zv[j] = sz[j][i];
+    df d1 = da[i], d2 = db[i];
+    const df xo = x[i];
+    float xs = xo.hi, xt = xo.lo;
+#pragma unroll
+    for (int j = 0; j < kUpdRing; ++j) {
+      if (j < np) {
+        const float4 a = lds_f4(&sc[j][0]), b = lds_f4(&sc[j][1]);
+        const df cz{a.x, a.y}, c1{a.z, a.w}, c2{b.x, b.y}, cx{b.z, b.w};
+        // the sum starts as the exact product cz.hi z plus its low-order terms
+        float s, t;
+        two_prod(cz.hi, zv[j], s, t);
+        t = fmaf(cz.lo, zv[j], t);
+        dacc_prod(s, t, c1, d1);
+        dacc_prod(s, t, c2, d2);
+        const df d = df_from_sum(s, t);
+        dacc_prod(xs, xt, cx, d);
+        const df xn = df_from_sum(xs, xt);
+        xs = xn.hi;
+        xt = xn.lo;
+        d2 = d1;
+        d1 = d;
+      }
+    }
+    da[i] = d1;
+    db[i] = d2;
+    x[i] = df{xs, xt};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&S->counter[CNT_UPD], 1u);
+    if (prev == gridDim.x - 1) {
+      S->upd = kd;
+      S->counter[CNT_UPD] = 0;
+    }
   }
 }
 
@@ -162,6 +250,12 @@ double inner_floor() {
     return (x > 0.0 && x < 1.0) ? x : 1e-7;
   }();
   return f;
+}
+
+int update_group() {
+  const char *v = std::getenv("ST_UPDATE_GROUP");
+  const int x = v ? std::atoi(v) : 0;
+  return (x >= 1 && x <= kUpdRing) ? x : kUpdRing;
 }
 
 thread_local Prof *t_prof = nullptr;
@@ -209,9 +303,24 @@ cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
 }
 
 cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, int kidx, cudaStream_t st) {
+                             State *S, cudaStream_t st) {
   prof_begin(KC_UPDATE, st);
-  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S, kidx);
+  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+float *zslot(st_handle *h, int s) { return s < 2 ? (float *)h->Z[s] : h->Zx[s - 2]; }
+
+// applies every pending direction/solution update of the mixed single solve (see
+// k_update_group_df); the device state decides how many
+cudaError_t launch_update_group(st_handle *h, cudaStream_t st) {
+  ZRing zr{};
+  zr.len = h->ugroup + 1;
+  for (int s = 0; s < zr.len; ++s) zr.p[s] = zslot(h, s);
+  prof_begin(KC_UPDATE, st);
+  k_update_group_df<<<kStreamBlocks, kNT, 0, st>>>(h->g.N, zr, (df *)h->D[0], (df *)h->D[1],
+                                                   h->Xdf, h->S);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -407,9 +516,10 @@ size_t cheb_coef_bytes(const Geom &g, int deg) {
   return ((size_t)deg * g.n * 2 * (sizeof(double) + sizeof(float)) + 255) / 256 * 256;
 }
 
-size_t workspace_bytes(const Geom &g, bool mixed, int cheb) {
+size_t workspace_bytes(const Geom &g, bool mixed, int cheb, int ugroup) {
   const size_t N = (size_t)g.N;
   size_t b = 0;
+  if (mixed) b += (size_t)(ugroup - 1) * N * sizeof(float);  // grouped update: pending z_j
   if (cheb) b += cheb_coef_bytes(g, cheb) + 5 * N * sizeof(double);
   b += 2 * N * sizeof(double);                             // V
   b += 2 * N * (mixed ? sizeof(float) : sizeof(double));   // Z
@@ -818,11 +928,7 @@ void free_handle(st_handle *h) {
   cudaFree(h->gfy);
   cudaFree(h->cheb);
   if (h->hS) cudaFreeHost(h->hS);
-  for (int i = 0; i < 2; ++i) {
-    if (h->ev_givens[i]) cudaEventDestroy(h->ev_givens[i]);
-    if (h->ev_update[i]) cudaEventDestroy(h->ev_update[i]);
-  }
-  if (h->ustream) cudaStreamDestroy(h->ustream);
+  for (int i = 0; i < kUpdRing - 1; ++i) cudaFree(h->Zx[i]);
   prof_free(h->prof);
   delete h;
 }
@@ -845,36 +951,26 @@ cudaError_t launch_iteration(st_handle *h, int k, double *x) {
   return launch_update<Tz>(g.N, zc, h->D[c], h->D[o], x, h->S, st);
 }
 
-// Mixed path iteration k: df vectors in V, D, q; float32 z.
+// Mixed path iteration k: df vectors in V, D, q; float32 z_k in ring slot (k - 1) % (G + 1).
+// The direction/solution update runs after every G-th iteration (G = ugroup) and applies the
+// updates of the G iterations since the previous one; solve_mixed flushes the rest at the end
+// of each inner run.
 cudaError_t launch_iteration_mixed(st_handle *h, int k) {
   const int c = (k - 1) & 1, o = k & 1;
+  const int R = h->ugroup + 1;
   const Geom &g = h->g;
   cudaStream_t st = h->stream;
-  const float *zc = (const float *)h->Z[c];
-  float *zn = (float *)h->Z[o];
+  const float *zc = zslot(h, (k - 1) % R);
+  float *zn = zslot(h, k % R);
   df *V0 = (df *)h->V[c], *V1 = (df *)h->V[o];
-  df *D0 = (df *)h->D[c], *D1 = (df *)h->D[o];
   df *q = (df *)h->q;
   cudaError_t e;
   e = launch_stencil_df(g, zc, q, h->S, h->partials, st);
   if (e != cudaSuccess) return e;
-  if (!h->ustream) {  // serial order: the update follows the preconditioner pass on one stream
-    e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st);
-    if (e != cudaSuccess) return e;
-    return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, 0, st);
-  }
-  // the preconditioner pass writes z_{k+1} over z_{k-1}, which the update of iteration k-1 (side
-  // stream) reads
-  if (k > 1 && (e = cudaStreamWaitEvent(st, h->ev_update[c], 0)) != cudaSuccess) return e;
-  e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st,
-                                            h->ev_givens[o]);
+  e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials, st);
   if (e != cudaSuccess) return e;
-  // d_k, x: after the Givens step of this iteration, concurrently with the inverse transforms
-  // and the next stencil
-  if ((e = cudaStreamWaitEvent(h->ustream, h->ev_givens[o], 0)) != cudaSuccess) return e;
-  if ((e = launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, k, h->ustream)) != cudaSuccess)
-    return e;
-  return cudaEventRecord(h->ev_update[o], h->ustream);
+  if (k % h->ugroup == 0) return launch_update_group(h, st);
+  return cudaSuccess;
 }
 
 int sync_state(st_handle *h) {
@@ -1052,7 +1148,6 @@ int mixed_iterate(st_handle *h) {
     const int k0 = h->hS->k;
     const double est0 = known ? h->hS->est : 0.0;
     for (int i = 1; i <= chunk; ++i) ST_TRY(launch_iteration_mixed(h, k0 + i));
-    if (h->ustream) ST_TRY(cudaStreamWaitEvent(h->stream, h->ev_update[(k0 + chunk) & 1], 0));
     int r = sync_state(h);
     if (r) return r;
     const State &s = *h->hS;
@@ -1094,6 +1189,7 @@ int solve_mixed(st_handle *h, const double *fH, double *x, double tol, int maxit
     total += s.k;
     last_est = s.est;
     status = s.status;
+    ST_TRY(launch_update_group(h, st));  // the inner run's pending updates
     ST_TRY(launch_df_to_double(g.N, h->Xdf, x, st));
     // r = Y f_H - Y T x (float64), stored as the next step's double-float right-hand side
     ST_TRY(launch_resid_df(g, x, (df *)h->V[0], fH, h->S, h->partials, st));
@@ -1126,6 +1222,67 @@ double now_s() {
 }  // namespace
 
 // ------------------------------------------------------------------------------------ C ABI
+int st::setup_handle(const st_problem *prob, st_handle **out, int ugroup) {
+  if (!out) return ST_ERR_ARG;
+  *out = nullptr;
+  int r = check_problem(prob);
+  if (r) return r;
+  if (ugroup < 1 || ugroup > kUpdRing) return ST_ERR_ARG;
+  st_handle *h = new (std::nothrow) st_handle();
+  if (!h) return ST_ERR_OOM;
+  std::memset(h, 0, sizeof(st_handle));
+  h->prob = *prob;
+  h->stream = (cudaStream_t)prob->stream;
+  h->mixed = (prob->precision == ST_MIXED);
+  h->g = geom_of(prob);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return ST_ERR_CUDA;
+  }
+  if (device_closed(h->device)) {
+    delete h;
+    return ST_ERR_TIMEOUT;
+  }
+  const Geom g = h->g;
+  const size_t N = (size_t)g.N;
+  auto fail = [&](int code) {
+    h->prob.a_nodal = nullptr;
+    free_handle(h);
+    return code;
+  };
+  r = build_tables(h);
+  if (r) return fail(r);
+  const size_t zsz = h->mixed ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&h->V[i], N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->Z[i], N * zsz);
+    if (e == cudaSuccess) e = cudaMalloc(&h->D[i], N * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->q, N * sizeof(double));
+  if (e == cudaSuccess && h->mixed) e = cudaMalloc(&h->Xdf, N * sizeof(df));
+  h->partials_len = partials_needed(g);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->partials_len * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->S, sizeof(State));
+  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_in, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_out, N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->gfx, (size_t)g.my * (g.mx + 1) * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&h->gfy, ((size_t)g.my + 1) * g.mx * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hS, sizeof(State));
+  // z vectors of the iterations a grouped update keeps pending (mixed single solves)
+  h->ugroup = h->mixed ? ugroup : 1;
+  for (int i = 0; i < h->ugroup - 1 && e == cudaSuccess; ++i)
+    e = cudaMalloc(&h->Zx[i], N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(h->S, 0, sizeof(State));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(map_cuda(e));
+  std::memset(h->hS, 0, sizeof(State));
+  h->prob.a_nodal = nullptr;
+  *out = h;
+  return ST_OK;
+}
+
 extern "C" {
 
 int st_version(void) { return 1; }
@@ -1393,76 +1550,12 @@ int st_workspace_bytes(const st_problem *prob, size_t *bytes) {
   int r = check_problem(prob);
   if (r) return r;
   Geom g = geom_of(prob);
-  *bytes = workspace_bytes(g, prob->precision == ST_MIXED, cheb_degree(prob));
+  *bytes = workspace_bytes(g, prob->precision == ST_MIXED, cheb_degree(prob), update_group());
   return ST_OK;
 }
 
 int st_setup(const st_problem *prob, st_handle **out) {
-  if (!out) return ST_ERR_ARG;
-  *out = nullptr;
-  int r = check_problem(prob);
-  if (r) return r;
-  st_handle *h = new (std::nothrow) st_handle();
-  if (!h) return ST_ERR_OOM;
-  std::memset(h, 0, sizeof(st_handle));
-  h->prob = *prob;
-  h->stream = (cudaStream_t)prob->stream;
-  h->mixed = (prob->precision == ST_MIXED);
-  h->g = geom_of(prob);
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
-    delete h;
-    return ST_ERR_CUDA;
-  }
-  if (device_closed(h->device)) {
-    delete h;
-    return ST_ERR_TIMEOUT;
-  }
-  const Geom g = h->g;
-  const size_t N = (size_t)g.N;
-  auto fail = [&](int code) {
-    h->prob.a_nodal = nullptr;
-    free_handle(h);
-    return code;
-  };
-  r = build_tables(h);
-  if (r) return fail(r);
-  const size_t zsz = h->mixed ? sizeof(float) : sizeof(double);
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaMalloc(&h->V[i], N * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->Z[i], N * zsz);
-    if (e == cudaSuccess) e = cudaMalloc(&h->D[i], N * sizeof(double));
-  }
-  if (e == cudaSuccess) e = cudaMalloc(&h->q, N * sizeof(double));
-  if (e == cudaSuccess && h->mixed) e = cudaMalloc(&h->Xdf, N * sizeof(df));
-  h->partials_len = partials_needed(g);
-  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->partials_len * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->S, sizeof(State));
-  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_in, N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->hbuf_out, N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->gfx, (size_t)g.my * (g.mx + 1) * sizeof(double));
-  if (e == cudaSuccess)
-    e = cudaMalloc(&h->gfy, ((size_t)g.my + 1) * g.mx * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&h->hS, sizeof(State));
-  // ST_OVERLAP_UPDATE=1 runs the update of iteration k on a side stream, concurrently with the
-  // inverse transforms of k and the stencil of k + 1 (about 1% faster on a 255^2 x 256 solve, but
-  // the per-kernel timings then include the overlap); by default it follows the preconditioner
-  // pass on the caller's stream
-  const char *overlap = std::getenv("ST_OVERLAP_UPDATE");
-  if (e == cudaSuccess && h->mixed && overlap && overlap[0] == '1') {
-    e = cudaStreamCreateWithFlags(&h->ustream, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-      e = cudaEventCreateWithFlags(&h->ev_givens[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_update[i], cudaEventDisableTiming);
-    }
-  }
-  if (e == cudaSuccess) e = cudaMemset(h->S, 0, sizeof(State));
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return fail(map_cuda(e));
-  std::memset(h->hS, 0, sizeof(State));
-  h->prob.a_nodal = nullptr;
-  *out = h;
-  return ST_OK;
+  return setup_handle(prob, out, update_group());
 }
 
 void st_destroy(st_handle *h) {

@@ -245,6 +245,13 @@ struct acc_df {
     t += err + e;
   }
   __device__ __forceinline__ void add(df a) { add(a.hi, a.lo); }
+  // add a float (no low-order part)
+  __device__ __forceinline__ void add1(float p) {
+    float ss, err;
+    two_sum(s, p, ss, err);
+    s = ss;
+    t += err;
+  }
   __device__ __forceinline__ void add_prod(df a, df b) {
     float p, e;
     two_prod(a.hi, b.hi, p, e);
@@ -325,8 +332,8 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
         float pp, e;
         two_prod(1.5f, c, pp, e);
         A.add(pp, e);
-        A.add(-2.0f * c1, 0.f);
-        A.add(0.5f * c2, 0.f);
+        A.add1(-2.0f * c1);
+        A.add1(0.5f * c2);
         A.add(Kc);
       }
       return A.get();
@@ -353,16 +360,16 @@ __global__ void __launch_bounds__(kNT, D3 ? 3 : 4) k_stencil_df(Geom g, const fl
       if (UNI) {
         // c_uni (f z_c - z_w - z_e - ...): f z_c is exact (f = 2, 4, or 4 + 2 in 3D)
         acc_df A{(dim >= 2) ? 4.f * c : 2.f * c, 0.f};
-        if (D3) A.add(2.f * c, 0.f);
-        A.add(-q.w, 0.f);
-        A.add(-q.e, 0.f);
+        if (D3) A.add1(2.f * c);
+        A.add1(-q.w);
+        A.add1(-q.e);
         if (dim >= 2) {
-          A.add(-q.s, 0.f);
-          A.add(-q.n, 0.f);
+          A.add1(-q.s);
+          A.add1(-q.n);
         }
         if (D3) {
-          A.add(-q.d, 0.f);
-          A.add(-q.u, 0.f);
+          A.add1(-q.d);
+          A.add1(-q.u);
         }
         return df_mul(g.c_uni, A.get());
       }

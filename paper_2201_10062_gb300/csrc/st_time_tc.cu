@@ -10,8 +10,9 @@
 // power of two so that fp16 keeps its range; S is scaled by 8.
 //
 // S (both parities, both pieces: 128 KB for n = 256) lives in tensor memory as the A operand of
-// tcgen05.mma; one block of 16 warps per SM runs two independent tile pipelines of 8 warps
-// (k_time_tc2, k_dst_tc_y2), each walking column tiles of 32 as a two-stage software pipeline.
+// tcgen05.mma; one block per SM runs independent tile pipelines of 8 warps, each walking column
+// tiles of 32: three in the time kernel (k_time_tc3), two, each a two-stage software pipeline,
+// in the spatial one (k_dst_tc_y2).
 // One thread per pipeline issues tcgen05.mma (M = 128, N = 32, K = 16; B from a shared-memory
 // descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the
 // pipeline's mbarrier, and its warps read the accumulators with tcgen05.ld.  For 256 < n <= 512
@@ -210,14 +211,14 @@ __device__ __forceinline__ float inv_sym(const Spec<float> &sp, const SymRow &r,
   return rsqrtf(re * re + im * im);
 }
 
-// ------------------------------------------------------------------ two tile pipelines per block
-// The same transform, scaling and energy as k_time_tc, organised for more overlap: S_n (both
-// parities, hi and lo) lives in tensor memory as the A operand of tcgen05.mma (256 of the 512
-// columns), which leaves shared memory for two independent tile pipelines of 8 warps each.  Each
-// group has its own B operands, Y tile, accumulators (64 + 64 columns), mbarriers and named
-// barrier, so one group's fold/split/scale phases run while the other waits on its barriers or
-// its MMAs; the MMAs read only B from shared memory.  Group g of block b takes the tiles
-// 2b + g, 2b + g + 2 gridDim.x, ...
+// ------------------------------------------------------------------ tile pipelines per block
+// S (both parities, hi and lo) lives in tensor memory as the A operand of tcgen05.mma (256 of
+// the 512 columns), which leaves shared memory for independent tile pipelines of 8 warps each.
+// Each group has its own B operands, tiles, accumulators, mbarriers and named barrier, so one
+// group's fold/split/scale phases run while the others wait on their barriers or their MMAs; the
+// MMAs read only B from shared memory.  Group g of block b takes the tiles G b + g,
+// G b + g + G gridDim.x, ... (G groups per block: 2 for the spatial kernel, 3 for the time
+// kernel).
 constexpr int kGroups = 2;
 constexpr int kGT = 256;  // threads per group
 
@@ -256,40 +257,6 @@ __device__ __forceinline__ bool group_sync_and(bool v, int id, int nthreads) {
   return out != 0;
 }
 
-// Per-group shared-memory layout, offsets from the group's base (the base is 1024-aligned).
-struct TcGroupSmem {
-  uint32_t bop1, bop2, ytile, colinv1, colinv2, colmax, tmu, mbar1, mbar2, total;
-};
-
-__host__ __device__ inline TcGroupSmem tcg_layout(int n) {
-  const int h = n / 2;
-  const uint32_t bop = 2u * 2u * kTN * h * 2u;  // [parity][piece][32][h] fp16
-  TcGroupSmem L{};
-  uint32_t o = 0;
-  L.bop1 = o;
-  o += bop;
-  L.bop2 = o;
-  o += bop;
-  L.ytile = o;
-  o += (uint32_t)n * kYS * 4u;
-  L.colinv1 = o;
-  o += kTN * 4u;
-  L.colinv2 = o;
-  o += kTN * 4u;
-  L.colmax = o;  // 8 warps x 32 per-column partial maxima
-  o += 8u * kTN * 4u;
-  L.tmu = o;
-  o += kTN * 4u;
-  L.mbar1 = o;
-  o += 8;
-  L.mbar2 = o;
-  o += 8;
-  L.total = (o + 1023u) & ~1023u;
-  return L;
-}
-
-// whole block: group 0, group 1, then the tensor-memory address slot
-__host__ __device__ inline uint32_t tcg_block_bytes(int n) { return kGroups * tcg_layout(n).total + 16u; }
 
 // Fold, scale and split of one tile for a group of 256 threads: thread (column c = gt % 32,
 // t-blocks tb = gt / 32 and gt / 32 + 8 of 8 rows; h/8 <= 16 t-blocks).  A warp reads or writes
@@ -404,195 +371,9 @@ __device__ __forceinline__ void issue_mmas_ta(uint32_t a_base, uint32_t bbase, i
   mma_commit(mbar);
 }
 
-__global__ void __launch_bounds__(kNT, 1)
-    k_time_tc2(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
-               State *S, int tmode, double *__restrict__ partials, int gk) {
-  __shared__ double red[32];
-  if (gate_closed(S, gk)) return;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int h = n >> 1;
-  const TcGroupSmem L = tcg_layout(n);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int grp = warp >> 3, gt = tid & (kGT - 1), w8 = warp & 7;
-  const int bar = 1 + grp;  // named barrier of this group (0 is __syncthreads)
-  unsigned char *gs = smem + (uint32_t)grp * L.total;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kGroups * L.total);
-  const float *colinv1 = reinterpret_cast<const float *>(gs + L.colinv1);
-  const float *colinv2 = reinterpret_cast<const float *>(gs + L.colinv2);
-  float *ytile = reinterpret_cast<float *>(gs + L.ytile);
-  float *tmus = reinterpret_cast<float *>(gs + L.tmu);
-  const uint32_t mbar1 = smem_u32(gs + L.mbar1), mbar2 = smem_u32(gs + L.mbar2);
-  const long long ntiles = (m + kTN - 1) / kTN;
-  if (gt == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar2) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_u32(tmem_slot))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t a_base = tmem;  // columns 0..255: S_n pieces
-  const uint32_t dcol1 = tmem + 256u + (uint32_t)grp * 128u, dcol2 = dcol1 + 64u;
-  // A into tensor memory: warp w writes piece w / 4 for the lanes of its quadrant w % 4; row r's
-  // 16-byte chunks of 8 K values sit at canon_off(r, 8j, h) in the shared-memory image
-  {
-    const int q = warp & 3, piece = warp >> 2;
-    const int r = q * 32 + lane;
-    const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
-                               (size_t)piece * kM * h * 2u;
-    const uint32_t lanes = (uint32_t)(q * 32) << 16;
-    for (int ks = 0; ks < h / 16; ++ks) {
-      uint32_t w[8];
-      const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
-      const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
-      w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
-      w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
-      tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
-    }
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  uint32_t ph1 = 0, ph2 = 0;
-  bool ok = true;
-  bool out1 = false, out2 = false;
-  float esum = 0.f, ecomp = 0.f;
-  // accumulator view of this warp: TMEM lanes 32q.. (rows r), parity P, all 32 columns
-  const int q = warp & 3, P = w8 >> 2;
-  const int r = (q << 5) + lane;
-  const uint32_t lanes = (uint32_t)(q * 32) << 16, cview = (uint32_t)(P * kTN);
-  const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
-  float *yrow = ytile + (P * h + r) * kYS;
-  auto ycell = [&](int t, int c) -> float & { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
-  const long long tstride = (long long)kGroups * gridDim.x;
-  auto finish_second = [&](long long pj0, int pje) {
-    const bool w = group_sync_and(mbar_wait(mbar2, ph2), bar, kGT);
-    ok = ok && w;
-    if (!w) return;
-    out2 = false;
-    ph2 ^= 1u;
-    fence_after();
-    float v[32];
-    tmem_ld16(dcol2 + lanes + cview, v);
-    tmem_ld16(dcol2 + lanes + cview + 16u, v + 16);
-    if (r < h) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) yrow[c] = v[c] * colinv2[c];
-    }
-    fence_before();
-    group_sync(bar, kGT);
-    fence_after();
-    for (int idx = gt; idx < n * kTN; idx += kGT) {
-      const int t = idx >> 5, c = idx & (kTN - 1);
-      if (c < pje) data[(long long)t * m + pj0 + c] = ycell(t, c);
-    }
-    group_sync(bar, kGT);
-  };
-  bool pend = false;
-  long long pj0 = 0;
-  int pje = 0;
-  float pa[2][8], pb[2][8];
-  const long long first = (long long)blockIdx.x * kGroups + grp;
-  if (first < ntiles) {
-    const long long jt = first * kTN;
-    load_b_g(n, gt, data, m, jt, (int)min((long long)kTN, m - jt), pa, pb);
-  }
-  for (long long tile = first; tile < ntiles && ok; tile += tstride) {
-    const long long j0 = tile * kTN;
-    const int je = (int)min((long long)kTN, m - j0);
-    if (gt < kTN) {
-      float t = 0.f;
-      if (gt < je) {
-        const long long j = j0 + gt;
-        const long long jy = j / mx, jx = j - jy * mx;
-        t = sp.mux[jx] + sp.muy[jy];
-      }
-      tmus[gt] = t;
-    }
-    build_b_g(gs + L.bop1, reinterpret_cast<float *>(gs + L.colinv1),
-              reinterpret_cast<float *>(gs + L.colmax), n, pa, pb, gt, bar);
-    fence_async_smem();
-    group_sync(bar, kGT);
-    fence_after();
-    if (gt == 0) issue_mmas_ta(a_base, smem_u32(gs + L.bop1), h, dcol1, mbar1);
-    out1 = true;
-    if (tile + tstride < ntiles) {
-      const long long jt = (tile + tstride) * kTN;
-      load_b_g(n, gt, data, m, jt, (int)min((long long)kTN, m - jt), pa, pb);
-    }
-    if (pend) finish_second(pj0, pje);
-    {
-      const bool w = group_sync_and(mbar_wait(mbar1, ph1), bar, kGT);
-      ok = ok && w;
-      if (!w) break;
-    }
-    out1 = false;
-    ph1 ^= 1u;
-    fence_after();
-    {
-      float v[32];
-      tmem_ld16(dcol1 + lanes + cview, v);
-      tmem_ld16(dcol1 + lanes + cview + 16u, v + 16);
-      if (r < h) {
-        float rs = 0.f;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float y = v[c] * colinv1[c];
-          const float yi = y * inv_sym(sp, sr, tmus[c]);
-          if (c < je) rs = fmaf(y, yi, rs);
-          yrow[c] = yi;
-        }
-        const float term = rs - ecomp;
-        const float t = esum + term;
-        ecomp = (t - esum) - term;
-        esum = t;
-      }
-    }
-    fence_before();
-    group_sync(bar, kGT);
-    fence_after();
-    {
-      float a2[2][8], b2[2][8];
-      load_b_g_src(n, gt, [&](int t, int c) -> float { return ycell(t, c); }, a2, b2);
-      build_b_g(gs + L.bop2, reinterpret_cast<float *>(gs + L.colinv2),
-                reinterpret_cast<float *>(gs + L.colmax), n, a2, b2, gt, bar);
-    }
-    fence_async_smem();
-    group_sync(bar, kGT);
-    fence_after();
-    if (gt == 0 && ok) issue_mmas_ta(a_base, smem_u32(gs + L.bop2), h, dcol2, mbar2);
-    pend = ok;
-    out2 = out2 || ok;
-    pj0 = j0;
-    pje = je;
-  }
-  if (pend && ok) finish_second(pj0, pje);
-  tc_release_cols<512>(ok, out1, mbar1, ph1, out2, mbar2, ph2, tmem, S);
-  if (tmode != TM_NONE) {
-    const double e = (double)esum - (double)ecomp;
-    double tot;
-    if (last_block_reduce<kNT>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
-                               &tot) &&
-        tid == 0) {
-      if (tmode == TM_INIT || tmode == TM_RESTART)
-        minres_init_scalars_dev(S, tot);
-      else
-        minres_givens_dev(S, tot);
-    }
-  }
-}
-
-// Two-pipeline form of k_dst_tc_y: S_len (both parities, hi and lo) in tensor memory as the A
-// operand, two groups of 8 warps, each with its own staged input tile, B operand, Y tile,
-// accumulator (64 columns) and named barrier.  Same arithmetic and output.
+// One DST-I of length len along lines (y, z, or a single time transform): S_len (both
+// parities, hi and lo) in tensor memory as the A operand, two groups of 8 warps, each with its
+// own staged input tile, B operand, Y tile, accumulator (64 columns) and named barrier.
 struct TcYSmem {
   uint32_t bop, ytile, stage, colinv, colmax, mbar, total;
 };
@@ -744,6 +525,216 @@ __global__ void __launch_bounds__(kNT, 1)
   }
   cp_async_wait_all();
   tc_release_cols<512>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
+}
+
+// ------------------------------------------------------------------ time kernel: three pipelines
+// Time DST, 1/p scaling, <v, P^-1 v> and time DST of 32-column tiles.  Two pipelines (16 warps
+// per SM, 4 per scheduler) cannot hide the latency of the ALU phases between the MMAs; three
+// 8-warp pipelines (24 warps) with one B buffer and one 64-column accumulator each run both
+// transforms of a tile in sequence while the other two pipelines fill the gaps (103 against
+// 110 us per 255^2 x 256 launch).  Registers are capped at 80 per thread (768 threads); tensor
+// memory holds S in 256 columns and the three accumulators in 192.  The same organisation for
+// the spatial kernel was slower (79 against 54 us): its transformed rows, written from the
+// accumulator registers without a staged Y tile, left the stores uncoalesced.
+constexpr int kGroups3 = 3;
+constexpr int kNT3 = kGroups3 * kGT;  // 768 threads
+
+struct Tc3Smem {
+  uint32_t bop, ytile, colinv1, colinv2, colmax, tmu, mbar, total;
+};
+
+__host__ __device__ inline Tc3Smem tc3_layout(int n) {
+  const int h = n / 2;
+  Tc3Smem L{};
+  uint32_t o = 0;
+  L.bop = o;
+  o += 2u * 2u * kTN * h * 2u;
+  L.ytile = o;
+  o += (uint32_t)n * kYS * 4u;
+  L.colinv1 = o;
+  o += kTN * 4u;
+  L.colinv2 = o;
+  o += kTN * 4u;
+  L.colmax = o;
+  o += 8u * kTN * 4u;
+  L.tmu = o;
+  o += kTN * 4u;
+  L.mbar = o;
+  o += 8;
+  L.total = (o + 1023u) & ~1023u;
+  return L;
+}
+
+__host__ __device__ inline uint32_t tc3_block_bytes(int n) { return kGroups3 * tc3_layout(n).total + 16u; }
+
+// S pieces into tensor memory: 24 warps, warp w writes piece (w / 4) % 4 for quadrant w % 4 (the
+// first 16 warps cover the four pieces once; the others skip)
+__device__ __forceinline__ void load_a_tmem(const __half *sop_g, int h, uint32_t a_base, int warp,
+                                            int lane) {
+  if (warp >= 16) return;
+  const int q = warp & 3, piece = warp >> 2;
+  const int r = q * 32 + lane;
+  const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
+                             (size_t)piece * kM * h * 2u;
+  const uint32_t lanes = (uint32_t)(q * 32) << 16;
+  for (int ks = 0; ks < h / 16; ++ks) {
+    uint32_t w[8];
+    const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
+    const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
+    w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+    w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
+    tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kNT3, 1)
+    k_time_tc3(float *data, int n, long long m, int mx, Spec<float> sp, const __half *sop_g,
+               State *S, int tmode, double *__restrict__ partials, int gk) {
+  __shared__ double red[32];
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = n >> 1;
+  const Tc3Smem L = tc3_layout(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = warp >> 3, gt = tid & (kGT - 1), w8 = warp & 7;
+  const int bar = 1 + grp;
+  unsigned char *gs = smem + (uint32_t)grp * L.total;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kGroups3 * L.total);
+  float *colinv1 = reinterpret_cast<float *>(gs + L.colinv1);
+  float *colinv2 = reinterpret_cast<float *>(gs + L.colinv2);
+  float *part = reinterpret_cast<float *>(gs + L.colmax);
+  float *ytile = reinterpret_cast<float *>(gs + L.ytile);
+  float *tmus = reinterpret_cast<float *>(gs + L.tmu);
+  const uint32_t mbar = smem_u32(gs + L.mbar);
+  const long long ntiles = (m + kTN - 1) / kTN;
+  if (gt == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_base = tmem;
+  const uint32_t dcol = tmem + 256u + (uint32_t)grp * 64u;
+  load_a_tmem(sop_g, h, a_base, warp, lane);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  uint32_t phase = 0;
+  bool ok = true, outstanding = false;
+  float esum = 0.f, ecomp = 0.f;
+  const int q = warp & 3, P = w8 >> 2;
+  const int r = (q << 5) + lane;
+  const uint32_t tl = dcol + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN);
+  const SymRow sr = sym_row(sp, r < h ? (P == 0 ? 2 * r + 1 : 2 * r + 2) : 1);
+  float *yrow = ytile + (P * h + r) * kYS;
+  auto ycell = [&](int t, int c) -> float & { return ytile[((t & 1) * h + (t >> 1)) * kYS + c]; };
+  // one transform: MMAs from the operand just built, then the bounded wait (uniform in the group)
+  auto run_mmas = [&]() -> bool {
+    fence_async_smem();
+    group_sync(bar, kGT);
+    fence_after();
+    if (gt == 0) issue_mmas_ta(a_base, smem_u32(gs + L.bop), h, dcol, mbar);
+    outstanding = true;
+    const bool w = group_sync_and(mbar_wait(mbar, phase), bar, kGT);
+    if (!w) return false;
+    outstanding = false;
+    phase ^= 1u;
+    fence_after();
+    return true;
+  };
+  const long long tstride = (long long)kGroups3 * gridDim.x;
+  for (long long tile = (long long)blockIdx.x * kGroups3 + grp; tile < ntiles; tile += tstride) {
+    const long long j0 = tile * kTN;
+    const int je = (int)min((long long)kTN, m - j0);
+    if (gt < kTN) {
+      float t = 0.f;
+      if (gt < je) {
+        const long long j = j0 + gt;
+        const long long jy = j / mx, jx = j - jy * mx;
+        t = sp.mux[jx] + sp.muy[jy];
+      }
+      tmus[gt] = t;
+    }
+    {
+      float a[2][8], b[2][8];
+      load_b_g(n, gt, data, m, j0, je, a, b);
+      build_b_g(gs + L.bop, colinv1, part, n, a, b, gt, bar);
+    }
+    if (!(ok = run_mmas())) break;
+    // first epilogue: unscale, spectral scaling, energy; scaled Y into the parity-split tile
+    {
+      float v[16];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        tmem_ld16(tl + 16u * half, v);
+        if (r < h) {
+          float rs = 0.f;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int cc = 16 * half + c;
+            const float y = v[c] * colinv1[cc];
+            const float yi = y * inv_sym(sp, sr, tmus[cc]);
+            if (cc < je) rs = fmaf(y, yi, rs);
+            yrow[cc] = yi;
+          }
+          const float term = rs - ecomp;
+          const float t = esum + term;
+          ecomp = (t - esum) - term;
+          esum = t;
+        }
+      }
+    }
+    fence_before();
+    group_sync(bar, kGT);
+    fence_after();
+    {
+      float a[2][8], b[2][8];
+      load_b_g_src(n, gt, [&](int t, int c) -> float { return ycell(t, c); }, a, b);
+      build_b_g(gs + L.bop, colinv2, part, n, a, b, gt, bar);
+    }
+    if (!(ok = run_mmas())) break;
+    {
+      float v[16];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        tmem_ld16(tl + 16u * half, v);
+        if (r < h) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) yrow[16 * half + c] = v[c] * colinv2[16 * half + c];
+        }
+      }
+    }
+    fence_before();
+    group_sync(bar, kGT);
+    fence_after();
+    for (int idx = gt; idx < n * kTN; idx += kGT) {
+      const int t = idx >> 5, c = idx & (kTN - 1);
+      if (c < je) data[(long long)t * m + j0 + c] = ycell(t, c);
+    }
+    group_sync(bar, kGT);
+  }
+  tc_release_cols<512>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
+  if (tmode != TM_NONE) {
+    const double e = (double)esum - (double)ecomp;
+    double tot;
+    if (last_block_reduce<kNT3>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                                &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT || tmode == TM_RESTART)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ long time axes (n > 256)
@@ -1095,7 +1086,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // n a multiple of 32 up to 256, and the whole tile layout (plus 1 KB of static shared memory)
 // within the 227 KB a block may opt into
 bool time_tc_supported(int n) {
-  return n >= 32 && n <= 256 && (n % 32) == 0 && tcg_block_bytes(n) + 1024u <= 227u * 1024u;
+  return n >= 32 && n <= 256 && (n % 32) == 0 && tc3_block_bytes(n) + 1024u <= 227u * 1024u;
 }
 
 size_t time_tc_sop_halves(int n) { return (size_t)2 * 2 * kM * ((n + 1) / 2); }
@@ -1144,22 +1135,22 @@ int time_tc_grid() {
   return sms;
 }
 
-// two tile pipelines per block, S_n in tensor memory
+// three tile pipelines per block, S_n in tensor memory
 cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st) {
-  const uint32_t smem_bytes = tcg_block_bytes(g.n);
-  cudaError_t e = cudaFuncSetAttribute(k_time_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const uint32_t smem_bytes = tc3_block_bytes(g.n);
+  cudaError_t e = cudaFuncSetAttribute(k_time_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = (g.m + kTN - 1) / kTN;
-  const long long need = (ntiles + kGroups - 1) / kGroups;
+  const long long need = (ntiles + kGroups3 - 1) / kGroups3;
   int grid = time_tc_grid();
   if (need < grid) grid = (int)need;
   prof_begin(KC_TIME, st);
-  k_time_tc2<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
-                                            reinterpret_cast<const __half *>(sop), S, tmode,
-                                            partials, gk);
+  k_time_tc3<<<grid, kNT3, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
+                                             reinterpret_cast<const __half *>(sop), S, tmode,
+                                             partials, gk);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -1,4 +1,4 @@
-"""Run solves of one synthetic workload from the command line (also the driver for profiling).
+"""Run solves of one synthetic workload from the command line (also the command the ncu profiles run).
 
   python -m paper_2201_10062_gb300.run_case --workload cn2d --mx 255 --n 256 --precision mixed \
       --repeat 3

@@ -103,8 +103,25 @@ def test_workspace_bytes(lib):
     b32 = st_workspace_bytes(_spec(mx=255, my=255, n=256, precision="mixed"))
     N = 255 * 255 * 256
     assert 9 * 8 * N <= b64 <= 9 * 8 * N + (64 << 20)
-    # float32 z vectors, plus a double-float x accumulator and the tensor-core S_n image
-    assert b32 <= b64 + (1 << 20)
+    # float32 z vectors, plus a double-float x accumulator, the tensor-core S_n image and the
+    # seven float32 z vectors a grouped update of 8 iterations keeps pending
+    assert b32 <= b64 + 7 * 4 * N + (1 << 20)
+
+
+def test_workspace_bytes_follow_the_update_group(lib, monkeypatch):
+    """Each iteration of the update group beyond the first keeps one more float32 z vector
+    (mixed precision only)."""
+    from paper_2201_10062_gb300 import st_workspace_bytes
+
+    N = 255 * 255 * 256
+    got = {}
+    for G in (1, 4, 8):
+        monkeypatch.setenv("ST_UPDATE_GROUP", str(G))
+        got[G] = (st_workspace_bytes(_spec(mx=255, my=255, n=256, precision="mixed")),
+                  st_workspace_bytes(_spec(mx=255, my=255, n=256)))
+    assert got[4][0] - got[1][0] == 3 * 4 * N
+    assert got[8][0] - got[1][0] == 7 * 4 * N
+    assert got[1][1] == got[4][1] == got[8][1]
 
 
 def test_workspace_bytes_chebyshev_ptheta(lib):

@@ -551,24 +551,62 @@ def test_fp64_engines_match_oracle(pkg, case, monkeypatch):
     assert not np.array_equal(outs["dd"], outs["dfma"])
 
 
-# ------------------------------------------------------------------ update on a side stream
-def test_overlapped_update_matches_serial(pkg, monkeypatch):
-    """ST_OVERLAP_UPDATE=1 moves the mixed solve's update to a side stream (event-ordered): same
-    iterations and the same solution as the serial order, and the oracle's residual."""
+# ------------------------------------------------------------------ grouped update
+@pytest.mark.parametrize("maxit", [600, 13])
+def test_grouped_update_matches_per_iteration(pkg, monkeypatch, maxit):
+    """The mixed single solve applies the MINRES direction/solution updates G iterations at a time
+    (default 8; ST_UPDATE_GROUP sets G).  The Lanczos recurrence does not read d or x, so every G
+    gives the same iterations, and each element goes through the same float32 operations in the
+    same order: the solutions are bitwise equal to the per-iteration ones (G = 1), whether the
+    solve stops at a multiple of G or in between (maxit = 13 stops mid-group and exercises the
+    flush at the end of each inner run), and the converged one meets the oracle's residual."""
     w = W.small_case(2, 63, 63, 40, scheme="theta", theta=0.5, varcoef=True, seed=90)
     p = H.Problem.from_workload(w)
     spec = _spec(pkg, w, precision="mixed")
-    s0 = pkg.Solver(spec)
-    fH = s0.st_assemble_rhs(_d(w.f), _d(w.u0))
-    u0, st0 = s0.st_solve(fH, tol=1e-9, maxit=600)
-    u0 = u0.clone()
-    s0.close()
-    monkeypatch.setenv("ST_OVERLAP_UPDATE", "1")
-    s1 = pkg.Solver(spec)
-    u1, st1 = s1.st_solve(fH, tol=1e-9, maxit=600)
-    assert st1["iterations"] == st0["iterations"] and st1["outer_steps"] == st0["outer_steps"]
-    assert torch.equal(u1, u0)
-    fH_or = H.rhs(p, w.f, w.u0)
-    r = H.flip(fH_or, p.n) - H.apply_op(p, _h(u1).reshape(p.n, p.m))
-    assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-9 * (1 + 1e-6)
-    s1.close()
+    res = {}
+    fH = None
+    for G in (1, 3, 8):
+        monkeypatch.setenv("ST_UPDATE_GROUP", str(G))
+        s = pkg.Solver(spec)
+        if fH is None:
+            fH = s.st_assemble_rhs(_d(w.f), _d(w.u0))
+        u, st = s.st_solve(fH, tol=1e-9, maxit=maxit, allow_not_converged=True)
+        res[G] = (u.clone(), st["iterations"], st["outer_steps"], st["status"])
+        s.close()
+    for G in (3, 8):
+        assert res[G][1:] == res[1][1:], G
+        assert torch.equal(res[G][0], res[1][0]), G
+    if maxit == 600:
+        assert res[8][3] == 0
+        fH_or = H.rhs(p, w.f, w.u0)
+        r = H.flip(fH_or, p.n) - H.apply_op(p, _h(res[8][0]).reshape(p.n, p.m))
+        assert np.linalg.norm(r) / np.linalg.norm(fH_or) <= 1e-9 * (1 + 1e-6)
+    else:
+        assert res[8][1] == 13
+
+
+@pytest.mark.parametrize("dim,mx,n,theta", [(2, 63, 40, 0.5), (1, 127, 33, 1.0), (2, 31, 24, 0.7)])
+def test_uniform_and_general_double_float_stencil(pkg, dim, mx, n, theta, monkeypatch):
+    """A constant coefficient on a grid with equal spacing gives one face coefficient everywhere,
+    and the double-float stencil then takes its uniform form (one exact neighbour sum and one
+    product per node).  The mixed solve with it and with the general form (ST_STENCIL_GENERAL=1)
+    both reach the oracle's converged solution to 1e-8 in the same number of iterations (within
+    one)."""
+    my = mx if dim == 2 else 1
+    w = W.small_case(dim, mx, my, n, scheme="theta", theta=theta, varcoef=False, seed=41)
+    p = H.Problem.from_workload(w)
+    fH = H.rhs(p, w.f, w.u0)
+    x_ref, _ = H.solve(p, fH, tol=1e-13, maxit=500)
+    its = {}
+    for form in ("uniform", "general"):
+        if form == "general":
+            monkeypatch.setenv("ST_STENCIL_GENERAL", "1")
+        else:
+            monkeypatch.delenv("ST_STENCIL_GENERAL", raising=False)
+        s = pkg.Solver(_spec(pkg, w, precision="mixed"))
+        u, st = s.st_solve(_d(fH), tol=1e-10, maxit=500)
+        assert st["true_rel_res"] <= 1e-10
+        assert _rel2(_h(u).reshape(p.n, p.m), x_ref) <= 1e-8, form
+        its[form] = st["iterations"]
+        s.close()
+    assert abs(its["uniform"] - its["general"]) <= 1, its

@@ -115,3 +115,26 @@ def test_partition_edge_cases():
     assert shard.partition([3.0, 1.0, 2.0], 1) == [[0, 1, 2]]
     with pytest.raises(ValueError):
         shard.partition([1.0], 0)
+
+
+def test_bench_roofline_and_update_accounting():
+    """Host arithmetic of the bench's roofline: Sec. 8(d)'s bytes (84 per unknown and iteration
+    in mixed precision plus 24 per refinement step) over the solve time, and the grouped
+    update's bytes per solve (4 per pending z_j and iteration, 48 per launch)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    peak = {"hbm_gbs": 1000.0, "src": "test"}
+    r = bench.roofline_iter("mixed", 10**6, 10, 2, 1e-3, peak)
+    assert r["achieved"] == pytest.approx((84 * 10 + 24 * 2) * 10**6 / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    # 39 iterations in groups of 8: 5 launches; in groups of 1: 39 launches of 4 + 48 B each
+    assert bench.update_bytes_per_step(100, 39, 8) == (4 * 39 + 48 * 5) * 100
+    assert bench.update_bytes_per_step(100, 39, 1) == 52 * 39 * 100
+    prof = {"update": {"launches": 15, "timed": 15, "ms": 3.0},
+            "stencil": {"launches": 117, "timed": 117, "ms": 9.0}}
+    t = bench.kernel_table(prof, "mixed", 100, 3, peak, iterations=39, group=8)
+    assert t["update"]["bytes_per_step"] == (4 * 39 + 48 * 5) * 100
+    assert t["update"]["achieved_gbs"] == pytest.approx(t["update"]["bytes_per_step"] / 1e-3 / 1e9)
+    assert t["stencil"]["bytes_per_launch"] == 12 * 100
+    assert t["update"]["share"] == pytest.approx(0.25)
