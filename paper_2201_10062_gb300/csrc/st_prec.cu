@@ -19,6 +19,7 @@
 
 #include "st_fft.cuh"
 #include "st_internal.cuh"
+#include "st_symbol.cuh"
 
 namespace st {
 
@@ -26,9 +27,6 @@ namespace {
 
 constexpr int kNT = 256;
 
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ dd rsq(dd x) { return rsqrt_dd(x); }
 
 // Inside a MINRES iteration only the first kernel (the stencil) looks at `finish`; it clears
 // `active` so that the rest of that iteration is skipped.  The preconditioner kernels check
@@ -269,28 +267,6 @@ __device__ void time_dst_tile(Tc *X, Tc *Y, const Tc *sintab, int n, int J) {
   __syncthreads();
 }
 
-// 1/p for the eigenvalue of the preconditioner at time frequency k (1-based) and tau*mu.
-template <class T>
-__device__ __forceinline__ T inv_symbol(const Spec<T> &sp, int k, T tmu) {
-  const T hk = sp.hk[k - 1], ck = sp.ck[k - 1], sk = sp.sk[k - 1];
-  if (sp.prec == ST_PREC_PTHETA) {
-    // lam_H = sqrt(2 - 2cos x) = 2 sin(x/2), lam_Htheta = sqrt(th^2 + (1-th)^2 + 2 th(1-th) cos x)
-    return T(1) / (sp.lh[k - 1] + sp.lht[k - 1] * tmu);
-  }
-  T re, im;
-  if (sp.scheme == ST_THETA) {
-    // |a0 + a1 e^{ix}|, a0 = 1 + th tmu, a1 = -1 + (1-th) tmu;  a0 + a1 cos x = (1 - cos x) +
-    // tmu (th + (1-th) cos x)
-    re = hk + tmu * (sp.theta + (T(1) - sp.theta) * ck);
-    im = (T(-1) + (T(1) - sp.theta) * tmu) * sk;
-  } else {
-    // |a0 + a1 e^{ix} + a2 e^{2ix}|, a0 = 3/2 + tmu, a1 = -2, a2 = 1/2:
-    // re = (1 - cos x)^2 + tmu, im = -sin x (2 - cos x)
-    re = hk * hk + tmu;
-    im = -sk * (T(1) + hk);
-  }
-  return rsq(re * re + im * im);
-}
 
 template <class Tc, int KT, int JT>
 __global__ void __launch_bounds__(kNT)
