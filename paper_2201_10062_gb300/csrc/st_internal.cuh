@@ -334,6 +334,12 @@ struct PrecPlan {
   const unsigned short *sop_z;  // fp16 S_mz image for the tensor-core z-DST (3D mixed), or null
   const unsigned short *sop_long;  // streamed S_n chunks for the tensor-core time kernel when
                                    // 256 < n <= 512 (mixed), or null
+  const unsigned char *sdig;  // integer-digit image of S_n for the float64-accurate tensor-core
+                              // time kernel (float64 path, double-float engine), or null
+  int sdig_e;                 // its scale: the digits are those of S_n 2^sdig_e
+  dd *tscratch;               // N double-floats the tensor-core time stage writes between its
+                              // two transforms (the handle's stencil-output vector, free
+                              // during a preconditioner pass)
   int pcr;                    // P_theta with varying a in 1D: tridiagonal solves per frequency
   const unsigned short *sop_t1;  // fp16 S_n image for unscaled single time transforms on the
                                  // tensor cores (mixed P_theta with varying a), or null
@@ -379,6 +385,15 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
                            const unsigned short *sop, State *S, int tmode, double *partials,
                            int gk, cudaStream_t st);
 bool dst_tc_supported(int len);
+// float64-accurate time stage on the tensor cores (integer digits of S_n and of the double-float
+// data, exact float32 accumulation per digit group; k_time_tcd)
+bool time_tcd_supported(int n);
+size_t time_tcd_bytes(int n);
+int time_tcd_build(int n, unsigned char *out);  // returns the scale exponent of the digits
+// scratch: an N-vector of double-floats that overlaps neither data nor anything the stage reads
+cudaError_t launch_time_tcd(dd *data, dd *scratch, const Geom &g, const Spec<dd> &sp,
+                            const unsigned char *img, int eS, State *S, int tmode,
+                            double *partials, int gk, cudaStream_t st);
 bool time_tc_long_supported(int n);
 size_t time_tc_long_bytes(int n);
 void time_tc_long_build(int n, unsigned short *out);
@@ -418,6 +433,8 @@ cudaError_t launch_prec(const Geom &g, const PrecPlan &pp, const Tin *v, Tout *z
                         int tmode, double *partials, cudaStream_t st);
 int time_blocks_for(const Geom &g, const PrecPlan &pp, bool fp32);
 int time_J_default(int n, bool fp32);
+// the spatial DST passes alone, ungated: float32 (fp32), else the float64 path's engine
+// (double-float when pp.fp64_dd, float64 otherwise)
 cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
                           cudaStream_t st);
 cudaError_t tune_run_time(const Geom &g, const PrecPlan &pp, bool fp32, void *data,
@@ -575,6 +592,7 @@ struct st_handle {
   // the tensor-core operand images the handle was built with (the autotuner may switch a stage
   // to its CUDA-core kernel by clearing the plan's pointer; these keep the originals)
   const unsigned short *tc_time_img, *tc_y_img, *tc_z_img;
+  const unsigned char *tc_dig_img;  // the float64 path's digit image of S_n (see PrecPlan::sdig)
   int fp64_dd_ok;        // the float64 preconditioner may take the double-float engine
   st::State *hS;         // pinned host mirror of S
   int partials_len;

@@ -538,6 +538,7 @@ size_t workspace_bytes(const Geom &g, bool mixed, int cheb, int ugroup) {
     b += time_tc_long_bytes(g.n) + 256;
   if (mixed && g.dim >= 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
   if (mixed && g.dim == 3 && dst_tc_supported(g.mz)) b += time_tc_sop_halves(g.mz) * 2 + 256;
+  if (!mixed && time_tcd_supported(g.n)) b += time_tcd_bytes(g.n) + 256;  // digits of S_n
   b += 256;  // alignment of the z image
   return b;
 }
@@ -797,7 +798,16 @@ int build_tables(st_handle *h) {
   std::vector<dd> hdd(nd - o_mux);
   for (size_t i = o_mux; i < nd; ++i) hdd[i - o_mux] = dd(hd[i]);
   const size_t o_dd = (o_sopz + sopz.size() * sizeof(unsigned short) + 255) / 256 * 256;
-  const size_t bytes = o_dd + hdd.size() * sizeof(dd);
+  // integer-digit image of S_n for the float64 path's tensor-core time stage (double-float
+  // engine, P_H / P-hat and constant-coefficient P_theta)
+  std::vector<unsigned char> sdig;
+  int sdig_e = 0;
+  if (p.precision == ST_FP64 && time_tcd_supported(n) && !(no_tc && no_tc[0] == '1')) {
+    sdig.resize(time_tcd_bytes(n));
+    sdig_e = time_tcd_build(n, sdig.data());
+  }
+  const size_t o_dig = (o_dd + hdd.size() * sizeof(dd) + 255) / 256 * 256;
+  const size_t bytes = o_dig + sdig.size();
   ST_TRY(cudaMalloc(&h->tables, bytes));
   ST_TRY(cudaMemcpy(h->tables, hd.data(), bytes_d, cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + bytes_d, hf.data(), bytes_f, cudaMemcpyHostToDevice));
@@ -814,6 +824,9 @@ int build_tables(st_handle *h) {
                       sopz.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + o_dd, hdd.data(), hdd.size() * sizeof(dd),
                     cudaMemcpyHostToDevice));
+  if (!sdig.empty())
+    ST_TRY(cudaMemcpy((char *)h->tables + o_dig, sdig.data(), sdig.size(),
+                      cudaMemcpyHostToDevice));
   const double *D = (const double *)h->tables;
   const float *F = (const float *)((const char *)h->tables + bytes_d) - o_mux;
   h->g.cx = D + o_cx;
@@ -899,6 +912,9 @@ int build_tables(st_handle *h) {
   pp.twx_dd = DD + o_twx;
   pp.twy_dd = DD + o_twy;
   pp.twz_dd = DD + o_twz;
+  pp.sdig = sdig.empty() ? nullptr : (const unsigned char *)h->tables + o_dig;
+  pp.sdig_e = sdig_e;
+  h->tc_dig_img = pp.sdig;
   // the float64 P_H / P-hat preconditioner runs its transforms in double-float unless
   // ST_FP64_ENGINE=dfma asks for float64 arithmetic; st_autotune times both and keeps the faster
   const char *eng = std::getenv("ST_FP64_ENGINE");
@@ -1260,6 +1276,7 @@ int st::setup_handle(const st_problem *prob, st_handle **out, int ugroup) {
     if (e == cudaSuccess) e = cudaMalloc(&h->D[i], N * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->q, N * sizeof(double));
+  h->pp.tscratch = reinterpret_cast<dd *>(h->q);  // free during a preconditioner pass
   if (e == cudaSuccess && h->mixed) e = cudaMalloc(&h->Xdf, N * sizeof(df));
   h->partials_len = partials_needed(g);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->partials_len * sizeof(double));
@@ -1344,6 +1361,7 @@ struct Knobs {
   int st_target, dst_shift, jd, jf;
   int tc_time, tc_y, tc_z;  // 1: the stage runs on the tensor cores (when the handle has them)
   int fp64_dd, jdd;         // float64 preconditioner: double-float engine, its time-kernel tile
+  int tc_dd;                // 1: the double-float engine's time stage runs on the tensor cores
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int, int>, Knobs> g_tune_cache;
@@ -1356,13 +1374,14 @@ int st_autotune(st_handle *h, int reps) {
   const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.mz, h->g.n, (int)fp32,
                                    (h->tc_time_img ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
                                        (h->pp.cheb ? 4 : 0) + (h->tc_y_img ? 8 : 0) +
-                                       (h->tc_z_img ? 16 : 0));
+                                       (h->tc_z_img ? 16 : 0) + (h->tc_dig_img ? 32 : 0));
   auto apply_engines = [&](const Knobs &k) {
     h->pp.sop = k.tc_time ? h->tc_time_img : nullptr;
     h->pp.sop_y = k.tc_y ? h->tc_y_img : nullptr;
     h->pp.sop_z = k.tc_z ? h->tc_z_img : nullptr;
     h->pp.fp64_dd = h->fp64_dd_ok ? k.fp64_dd : 0;
     h->pp.time_J_dd = k.jdd;
+    h->pp.sdig = k.tc_dd ? h->tc_dig_img : nullptr;
   };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1377,7 +1396,7 @@ int st_autotune(st_handle *h, int reps) {
     }
   }
   // tune from the tensor-core configuration the handle was built with
-  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1, 1, 0});
+  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1, 1, 0, 1});
   cudaStream_t st = h->stream;
   const Geom &g = h->g;
   cudaEvent_t e0, e1;
@@ -1484,9 +1503,10 @@ int st_autotune(st_handle *h, int reps) {
       *use[axis - 1] = (ms_tc <= ms_fft) ? 1 : 0;
     }
   }
-  // 5. float64 preconditioner: double-float engine (its own time-kernel tile first) against the
-  // float64 one, the whole P_H pass each
-  int fp64_dd = 0, jdd = 0;
+  // 5. float64 preconditioner: double-float engine (the tile of its CUDA-core time kernel first,
+  // then that kernel against the tensor-core digit kernel) against the float64 one, the whole
+  // P_H pass each
+  int fp64_dd = 0, jdd = 0, tc_dd = 0;
   if (!fp32 && h->fp64_dd_ok) {
     const int cand[] = {16, 32, 48, 64};
     float best = 1e30f;
@@ -1501,6 +1521,14 @@ int st_autotune(st_handle *h, int reps) {
       }
     }
     h->pp.time_J_dd = jdd;
+    if (h->tc_dig_img) {
+      const float ms_tc = timed([&]() {
+        return launch_time_tcd((dd *)h->Z[0], (dd *)h->q, h->g, h->pp.spec_dd, h->tc_dig_img,
+                               h->pp.sdig_e, h->S, TM_NONE, h->partials, GK_NONE, st);
+      });
+      tc_dd = (ms_tc <= best) ? 1 : 0;
+    }
+    h->pp.sdig = tc_dd ? h->tc_dig_img : nullptr;
     const float ms_dd = timed([&]() {
       return launch_prec<double, double, double>(h->g, h->pp, h->V[0], (double *)h->Z[0], h->S,
                                                  TM_NONE, h->partials, st);
@@ -1513,7 +1541,7 @@ int st_autotune(st_handle *h, int reps) {
     fp64_dd = (ms_dd <= ms_d) ? 1 : 0;
   }
   const Knobs chosen{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f, tc_time,
-                     tc_y, tc_z, fp64_dd, jdd};
+                     tc_y, tc_z, fp64_dd, jdd, tc_dd};
   apply_engines(chosen);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -893,7 +893,11 @@ cudaError_t prec_stages_dd(const Geom &g, const PrecPlan &pp, Src src, double *z
   if (e != cudaSuccess) return e;
   if (g.dim >= 2 && (e = dst_y_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
   if (g.dim == 3 && (e = dst_z_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
-  e = launch_time<dd>(zd, g, pp.spec_dd, S, tmode, 0, partials, gk, pp.time_J_dd, st);
+  if (pp.sdig && pp.tscratch)
+    e = launch_time_tcd(zd, pp.tscratch, g, pp.spec_dd, pp.sdig, pp.sdig_e, S, tmode, partials,
+                        gk, st);
+  else
+    e = launch_time<dd>(zd, g, pp.spec_dd, S, tmode, 0, partials, gk, pp.time_J_dd, st);
   if (e != cudaSuccess) return e;
   if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
   if (g.dim == 3 && (e = dst_z_pass<dd>(Inner{zd}, zd, g, pp, S, gk, st)) != cudaSuccess) return e;
@@ -1003,6 +1007,18 @@ cudaError_t tune_run_dsts(const Geom &g, const PrecPlan &pp, bool fp32, void *da
     if (e == cudaSuccess && g.dim == 3)
       e = launch_dst<float, A, float, false>(A{z}, z, g.mz, pp.Lz, nz, g.mx * g.my, g.m,
                                              pp.twz_f, nullptr, GK_NONE, pp.dst_shift, st);
+  } else if (pp.fp64_dd) {
+    // the float64 path's double-float engine: its own FFT kernels (double-float data in place)
+    dd *z = (dd *)data;
+    using A = SrcArray<dd, dd>;
+    e = launch_dst<dd, A, dd, true>(A{z}, z, g.mx, pp.Lx, nx, g.mx, g.m, pp.twx_dd, nullptr,
+                                    GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim >= 2)
+      e = launch_dst<dd, A, dd, false>(A{z}, z, g.my, pp.Ly, ny, g.mx, (long long)g.mx * g.my,
+                                       pp.twy_dd, nullptr, GK_NONE, pp.dst_shift, st);
+    if (e == cudaSuccess && g.dim == 3)
+      e = launch_dst<dd, A, dd, false>(A{z}, z, g.mz, pp.Lz, nz, g.mx * g.my, g.m, pp.twz_dd,
+                                       nullptr, GK_NONE, pp.dst_shift, st);
   } else {
     double *z = (double *)data;
     using A = SrcArray<double, double>;

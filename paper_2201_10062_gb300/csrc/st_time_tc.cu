@@ -29,6 +29,7 @@
 #include <cstdlib>
 
 #include "st_internal.cuh"
+#include "st_symbol.cuh"
 
 namespace st {
 namespace {
@@ -1258,6 +1259,445 @@ cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &s
   k_time_tc_long<<<grid, kNT, smem_bytes, st>>>(data, g.n, g.m, g.mx, sp,
                                                 reinterpret_cast<const unsigned char *>(A), S,
                                                 tmode, partials, gk);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ float64-accurate time DST
+// The time stage of the float64 preconditioner (Sec. 3.1.1, steps 1-3 along time) on the tensor
+// cores, for double-float data.  An fp16 MMA with float32 accumulation is exact on integers as
+// long as every partial sum stays below 2^24, so both operands are cut into integer digits:
+//   S^ = S 2^eS = sum_i S_i 2^-7i,   X^ = X 2^ec = sum_j B_j 2^-7j,   i, j = 0..6,
+// with |S_i|, |B_j| <= 2^7 (one scale for S, one per column c of X and parity).  S's digits are
+// rounded ones taken in float64 on the host; X's are the 7-bit fields of the folded double-float
+// value as a 64-bit fixed-point integer (2^42 X^, rounded), the top one signed.  One product
+// S_i B_j over K = h <= 128 folded rows is at most 2^21 in magnitude, and the at most seven
+// products of a digit group g = i + j sum below 2^24, so each group accumulates exactly in
+// float32.  The groups g <= 6 are kept (28 products per parity); the dropped ones and the
+// digits' remainders are below 2^-41 of the column's largest entry.  The groups are summed in
+// double-float (sum_g acc_g 2^-7g, TwoSum) and unscaled by 2^-(eS + ec).
+//
+// With S's digits read from shared memory each MMA (M = 128, N = 32) costs about ten times one
+// that reads A from tensor memory, so the seven digits of one parity (448 tensor-memory columns)
+// stay resident for a whole phase: a block takes its tiles of 32 spatial columns once for each
+// parity.  Per tile and parity:
+//   1. fold the tile's rows for that parity (x_t + x_{n+1-t}, or x_t - x_{n+1-t}), choose each
+//      column's scale from its largest folded entry, write the seven digits as fp16 B operands
+//      (canonical K-major, [digit][32][h]);
+//   2. one thread issues the digit groups in order, g = 0..6, alternating between two 32-column
+//      accumulators: group g + 1 runs on the tensor cores while the block drains group g with
+//      tcgen05.ld and adds it into double-float sums (one row, 8 columns per thread);
+//   3. the rows of that parity are unscaled (and, in the first launch, multiplied by 1/p with
+//      <v, P^-1 v> accumulated), staged in shared memory and written out row by row.
+// A row of output depends on every input row, so the transform cannot run in place: the first
+// launch reads the data and writes the scaled transform into a scratch vector, the second
+// transforms the scratch vector back into the data.
+namespace {
+
+constexpr int kDg = 7;      // digits per operand
+constexpr int kDgW = 7;     // bits per digit
+constexpr int kNTG = 512;   // threads per block
+
+struct TcdSmem {
+  uint32_t bdig, ytile, part, cdown, tmu, mbar, tmem, total;
+};
+
+__host__ __device__ inline TcdSmem tcd_layout(int n) {
+  const int h = n / 2;
+  TcdSmem L{};
+  uint32_t o = 0;
+  L.bdig = o;  // [digit][32][h] fp16, one parity
+  o += (uint32_t)kDg * kTN * (uint32_t)h * 2u;
+  o = (o + 127u) & ~127u;
+  L.ytile = o;  // one parity's rows: hi floats then lo floats, [h][kYS]
+  o += 2u * (uint32_t)h * kYS * 4u;
+  L.part = o;  // 16 warps x 32 per-column partial maxima
+  o += 16u * kTN * 4u;
+  L.cdown = o;  // per column: 2^-(eS + e_c), the factor that undoes both scales
+  o += kTN * 4u;
+  L.tmu = o;  // tau mu_j and the symbol's column factor w_j, double-float
+  o += 2u * kTN * 8u;
+  L.mbar = o;  // one per accumulator
+  o += 2u * 8u;
+  L.tmem = o;
+  o += 8u;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ dd ld_dd(const dd *p) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  return dd(v.x, v.y);
+}
+__device__ __forceinline__ void st_dd(dd *p, dd v) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+}
+
+// 2^e as a float (exact; e outside the normal range through ldexpf)
+__device__ __forceinline__ float pow2f(int e) {
+  return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 1/p in double-float with the per-row parts hoisted (the double-float form of inv_symbol):
+// theta and BDF2 take 1/sqrt((a + tmu b)^2 + (w c)^2) with a, b, c per time frequency and
+// w per column (w = -1 + (1 - theta) tmu for theta, 1 for BDF2); P_theta takes 1/(a + b tmu).
+struct SymRowDD {
+  dd a, b, c;
+};
+__device__ __forceinline__ SymRowDD sym_row_dd(const Spec<dd> &sp, int k) {
+  SymRowDD r;
+  const dd hk = sp.hk[k - 1], ck = sp.ck[k - 1], sk = sp.sk[k - 1];
+  if (sp.prec == ST_PREC_PTHETA) {
+    r.a = sp.lh[k - 1];
+    r.b = sp.lht[k - 1];
+    r.c = dd(0.f, 0.f);
+  } else if (sp.scheme == ST_THETA) {
+    r.a = hk;
+    r.b = sp.theta + (dd(1) - sp.theta) * ck;
+    r.c = sk;
+  } else {
+    r.a = hk * hk;
+    r.b = dd(1);
+    r.c = -(sk * (dd(1) + hk));
+  }
+  return r;
+}
+__device__ __forceinline__ dd sym_col_w(const Spec<dd> &sp, dd tmu) {
+  if (sp.prec != ST_PREC_PTHETA && sp.scheme == ST_THETA)
+    return dd(-1) + (dd(1) - sp.theta) * tmu;
+  return dd(1);
+}
+__device__ __forceinline__ dd inv_sym_dd(const Spec<dd> &sp, const SymRowDD &r, dd tmu, dd w) {
+  if (sp.prec == ST_PREC_PTHETA) return dd(1) / (r.a + r.b * tmu);
+  const dd re = dd_fma(tmu, r.b, r.a), im = w * r.c;
+  return rsqrt_dd(dd_fma(re, re, im * im));
+}
+
+// scaled: out = (S_n x)/p per column with <in, P^-1 in> into the MINRES state (tmode);
+// otherwise out = S_n x.  in and out do not overlap.
+__global__ void __launch_bounds__(kNTG, 1)
+    k_time_tcd(const dd *__restrict__ in, dd *__restrict__ out, int n, long long m, int mx,
+               Spec<dd> sp, const unsigned char *A_g, int eS, int scaled, State *S, int tmode,
+               double *__restrict__ partials, int gk) {
+  __shared__ double red[32];
+  if (gate_closed(S, gk)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int h = n >> 1, hb = h >> 3;
+  const TcdSmem L = tcd_layout(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+  float *yhi = reinterpret_cast<float *>(smem + L.ytile);
+  float *ylo = yhi + (size_t)h * kYS;
+  float *part = reinterpret_cast<float *>(smem + L.part);
+  float *cdown = reinterpret_cast<float *>(smem + L.cdown);
+  dd *tmus = reinterpret_cast<dd *>(smem + L.tmu);  // tau mu_j, then w_j
+  const uint32_t mbar0 = smem_u32(smem + L.mbar);
+  const long long ntiles = (m + kTN - 1) / kTN;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8u * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t acol = (uint32_t)(h / 2);          // tensor-memory columns of one S digit
+  const uint32_t dcol = tmem + (uint32_t)kDg * acol;  // the two accumulators follow S
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+  bool pend[2] = {false, false};  // a commit whose completion has not been seen
+  MacAcc<dd> en;                  // this thread's part of <v, P^-1 v>
+  en.zero();
+  // build view: column bc, t-block bw (rows 8 bw.. and their mirrors)
+  const int bc = tid & (kTN - 1), bw = warp;
+  // drain view: lanes 32 q4.., columns 8 cc..
+  const int q4 = warp & 3, cc = warp >> 2;
+  const int r = (q4 << 5) + lane;
+  const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+  const uint32_t bop = (uint32_t)kTN * h * 2u;  // one digit's B operand
+
+  // issue digit group g into accumulator g & 1 and commit it (thread 0)
+  auto issue_group = [&](int g) {
+    const uint32_t d = dcol + (uint32_t)(kTN * (g & 1));
+    const uint32_t bbase = smem_u32(smem + L.bdig);
+    bool first = true;
+    for (int i = (g > kDg - 1 ? g - (kDg - 1) : 0); i <= g && i < kDg; ++i) {
+      const int j = g - i;
+      for (int ks = 0; ks < h / 16; ++ks) {
+        mma_f16_ta(d, tmem + (uint32_t)i * acol + (uint32_t)ks * 8u,
+                   make_desc(bbase + (uint32_t)j * bop + (uint32_t)ks * 256u, h), first ? 0u : 1u);
+        first = false;
+      }
+    }
+    mma_commit(mbar0 + 8u * (g & 1));
+  };
+
+  for (int P = 0; P < 2 && ok; ++P) {
+    // this parity's seven S digits into tensor memory (lane = row r, 16 K values per 8 columns)
+    {
+      const uint32_t tl = (uint32_t)(q4 * 32) << 16;
+      for (int pc = warp >> 2; pc < kDg; pc += 4) {
+        const unsigned char *img = A_g + (size_t)(P * kDg + pc) * kM * h * 2u;
+        for (int ks = 0; ks < h / 16; ++ks) {
+          uint32_t w[8];
+          const uint4 a0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
+          const uint4 a1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
+          w[0] = a0.x; w[1] = a0.y; w[2] = a0.z; w[3] = a0.w;
+          w[4] = a1.x; w[5] = a1.y; w[6] = a1.z; w[7] = a1.w;
+          tmem_st8(tmem + tl + (uint32_t)pc * acol + (uint32_t)ks * 8u, w);
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    const int krow = (P == 0) ? 2 * r + 1 : 2 * r + 2;  // time frequency of drain row r
+    const bool row_ok = r < h && krow <= n;
+    const SymRowDD srow = sym_row_dd(sp, row_ok ? krow : 1);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const long long j0 = tile * kTN;
+      const int je = (int)min((long long)kTN, m - j0);
+      if (scaled && tid < kTN) {
+        dd tv(0.f, 0.f);
+        if (tid < je) {
+          const long long jj = j0 + tid;
+          const long long jy = jj / mx, jx = jj - jy * mx;
+          tv = sp.mux[jx] + sp.muy[jy];
+        }
+        tmus[tid] = tv;
+        tmus[kTN + tid] = sym_col_w(sp, tv);
+      }
+      // 1. fold, scale and digits of this parity
+      {
+        dd f[8];
+        float mxv = 0.f;
+        if (bw < hb) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int t = bw * 8 + q;
+            dd a(0.f, 0.f), b(0.f, 0.f);
+            if (bc < je) {
+              a = ld_dd(in + (long long)t * m + j0 + bc);
+              b = ld_dd(in + (long long)(n - 1 - t) * m + j0 + bc);
+            }
+            f[q] = P == 0 ? a + b : a - b;
+            mxv = fmaxf(mxv, fabsf(f[q].hi));
+          }
+        }
+        part[bw * kTN + bc] = mxv;
+        fence_before();
+        __syncthreads();  // also: the previous tile's drains and write-out are done
+        fence_after();
+        float cm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) cm = fmaxf(cm, part[k * kTN + bc]);
+        int e = 0;
+        if (cm > 0.f && isfinite(cm)) {
+          int E;
+          frexpf(cm, &E);
+          e = 7 - E;  // cm 2^e in [2^6, 2^7)
+        }
+        if (bw == 0) cdown[bc] = pow2f(-(eS + e));
+        if (bw < hb) {
+          const float up = pow2f(e + 42);  // scale and fixed point in one exact factor
+          const uint32_t off = canon_off(bc, bw * 8, h);
+          long long V[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) V[q] = __float2ll_rn(f[q].hi * up) + __float2ll_rn(f[q].lo * up);
+#pragma unroll
+          for (int dg = 0; dg < kDg; ++dg) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) {
+              int d2[2];
+#pragma unroll
+              for (int h2 = 0; h2 < 2; ++h2) {
+                const long long Vq = V[2 * q2 + h2];
+                d2[h2] = dg == 0 ? (int)(Vq >> 42) : (int)((Vq >> (42 - kDgW * dg)) & 127);
+              }
+              const __half2 hv = __floats2half2_rn((float)d2[0], (float)d2[1]);
+              pk[q2] = *reinterpret_cast<const uint32_t *>(&hv);
+            }
+            *reinterpret_cast<uint4 *>(smem + L.bdig + (uint32_t)dg * bop + off) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          }
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      // 2. digit groups through two accumulators; the block drains group g while g + 1 runs
+      if (tid == 0) {
+        issue_group(0);
+        issue_group(1);
+      }
+      pend[0] = pend[1] = true;
+      float s[8], t[8];
+      for (int g = 0; g < kDg; ++g) {
+        const int b = g & 1;
+        const bool w = __syncthreads_and(mbar_wait(mbar0 + 8u * b, ph[b]) ? 1 : 0) != 0;
+        if (!w) {
+          ok = false;
+          break;
+        }
+        pend[b] = false;
+        ph[b] ^= 1u;
+        fence_after();
+        float v[8];
+        tmem_ld8(dcol + lanes + (uint32_t)(kTN * b + 8 * cc), v);
+        const float sc = pow2f(-kDgW * g);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float x = v[c] * sc;
+          if (g == 0) {
+            s[c] = x;
+            t[c] = 0.f;
+          } else {
+            float ss, er;
+            two_sum(s[c], x, ss, er);
+            s[c] = ss;
+            t[c] += er;
+          }
+        }
+        fence_before();
+        __syncthreads();  // accumulator b is drained
+        fence_after();
+        if (g + 2 < kDg) {
+          if (tid == 0) issue_group(g + 2);
+          pend[b] = true;
+        }
+      }
+      if (!ok) break;  // uniform
+      // 3. unscale (and scale by 1/p), stage this parity's rows, write them out
+      if (row_ok) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int col = 8 * cc + c;
+          const dd v = dd_norm(s[c], t[c]);
+          const float fdn = cdown[col];
+          dd y(v.hi * fdn, v.lo * fdn);
+          if (scaled) {
+            const dd yi = y * inv_sym_dd(sp, srow, tmus[col], tmus[kTN + col]);
+            if (col < je) en.add(y, yi);
+            y = yi;
+          }
+          yhi[r * kYS + col] = y.hi;
+          ylo[r * kYS + col] = y.lo;
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < h * kTN; idx += kNTG) {
+        const int rr = idx >> 5, c = idx & (kTN - 1);
+        const int k = (P == 0) ? 2 * rr + 1 : 2 * rr + 2;
+        if (c < je && k <= n)
+          st_dd(out + (long long)(k - 1) * m + j0 + c, dd(yhi[rr * kYS + c], ylo[rr * kYS + c]));
+      }
+    }
+    fence_before();
+    __syncthreads();  // this parity's digits leave tensor memory: every MMA is drained
+    fence_after();
+  }
+  // a timed-out wait leaves its commit outstanding: tc_release_cols waits for it (bounded)
+  tc_release_cols<512>(ok, pend[0], mbar0, ph[0], pend[1], mbar0 + 8u, ph[1], tmem, S, true);
+  if (scaled && tmode != TM_NONE) {
+    const double e = (double)en.get();
+    double tot;
+    if (last_block_reduce<kNTG>(e, partials, &S->counter[CNT_TIME], gridDim.x, blockIdx.x, red,
+                                &tot) &&
+        tid == 0) {
+      if (tmode == TM_INIT || tmode == TM_RESTART)
+        minres_init_scalars_dev(S, tot);
+      else
+        minres_givens_dev(S, tot);
+    }
+  }
+}
+
+}  // namespace
+
+// n a multiple of 32 up to 256 (h = n/2 folded rows, a multiple of the MMA K step; seven S
+// digits of h/2 columns plus two 32-column accumulators within the 512 tensor-memory columns),
+// and the layout within the 227 KB a block may opt into (with 1 KB of static shared memory)
+bool time_tcd_supported(int n) {
+  if (n < 32 || n > 256 || (n % 32) != 0) return false;
+  if (kDg * (n / 4) + 2 * kTN > 512) return false;
+  return tcd_layout(n).total + 1024u <= 227u * 1024u;
+}
+
+size_t time_tcd_bytes(int n) { return (size_t)2 * kDg * kM * (size_t)(n / 2) * 2; }
+
+// Host: the digit image of S_n for k_time_tcd: piece (parity P, digit i) at index P * 7 + i, the
+// rows r of parity P (k = 2r+1 or 2r+2) by K = h folded columns, canonical K-major fp16; the
+// digits of S 2^eS (integers, |.| <= 2^7) are taken in float64, where they are exact.
+// Returns eS.
+int time_tcd_build(int n, unsigned char *out) {
+  const int h = n / 2;
+  const double PI = 3.14159265358979323846;
+  const double sn = std::sqrt(2.0 / (n + 1));
+  double smax = 0.0;
+  for (int k = 1; k <= n; ++k)
+    for (int t = 1; t <= h; ++t)
+      smax = std::fmax(smax, std::fabs(sn * std::sin(PI * (double)k * t / (n + 1))));
+  int E = 0;
+  std::frexp(smax, &E);
+  const int eS = 7 - E;  // smax 2^eS in [2^6, 2^7)
+  unsigned short *o = reinterpret_cast<unsigned short *>(out);
+  const size_t piece = (size_t)kM * h;  // halves
+  for (size_t i = 0; i < time_tcd_bytes(n) / 2; ++i) o[i] = 0;
+  for (int P = 0; P < 2; ++P)
+    for (int r = 0; r < h; ++r) {
+      const int k = (P == 0) ? 2 * r + 1 : 2 * r + 2;
+      if (k > n) continue;
+      for (int t = 0; t < h; ++t) {
+        double v = std::ldexp(sn * std::sin(PI * (double)k * (t + 1) / (n + 1)), eS);
+        for (int dg = 0; dg < kDg; ++dg) {
+          const double q = std::nearbyint(v);
+          v = (v - q) * 128.0;
+          const __half hq = __float2half_rn((float)q);
+          __half_raw raw = hq;
+          o[(size_t)(P * kDg + dg) * piece + canon_off(r, t, h) / 2] = raw.x;
+        }
+      }
+    }
+  return eS;
+}
+
+// scaled: scratch = (S_n data)/p with <v, P^-1 v> and the MINRES step; then data = S_n scratch
+cudaError_t launch_time_tcd(dd *data, dd *scratch, const Geom &g, const Spec<dd> &sp,
+                            const unsigned char *img, int eS, State *S, int tmode,
+                            double *partials, int gk, cudaStream_t st) {
+  // at least 116 KB of shared memory, so that one block runs per SM: each allocates all 512
+  // tensor-memory columns
+  uint32_t smem_bytes = tcd_layout(g.n).total;
+  if (smem_bytes < 116u * 1024u) smem_bytes = 116u * 1024u;
+  cudaError_t e = cudaFuncSetAttribute(k_time_tcd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (g.m + kTN - 1) / kTN;
+  int grid = time_tc_grid();
+  if (ntiles < grid) grid = (int)ntiles;
+  prof_begin(KC_TIME, st);
+  k_time_tcd<<<grid, kNTG, smem_bytes, st>>>(data, scratch, g.n, g.m, g.mx, sp, img, eS, 1, S,
+                                             tmode, partials, gk);
+  k_time_tcd<<<grid, kNTG, smem_bytes, st>>>(scratch, data, g.n, g.m, g.mx, sp, img, eS, 0, S,
+                                             TM_NONE, partials, gk);
   prof_end(st);
   return cudaGetLastError();
 }

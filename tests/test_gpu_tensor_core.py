@@ -97,3 +97,56 @@ def test_tc_single_time_transform_ptheta(pkg, dim, mx, my, n, theta, deg):
     assert _rel2(z_tc, z_ff) <= max(2e-5, 2 * e_ff)
     s_tc.close()
     s_ff.close()
+
+
+def _prec_tol64(p):
+    """float64 path with double-float transforms: 1e-11 (48-bit significands), widened for a
+    varying coefficient by the spread of the averaged-K eigenvalues (the lowest modes cancel)."""
+    if p.a_nodal is None:
+        return 1e-11
+    mu = H.averaged_stiffness_eigs(p)
+    return max(1e-11, 16 * 2.220446049250313e-16 * mu.max() / mu.min())
+
+
+# n supported by the float64 tensor-core time stage (multiples of 32 with n/2 <= 64, and 256),
+# ragged 32-column tiles, theta, BDF2 and the constant-coefficient P_theta
+@pytest.mark.parametrize("dim,mx,my,n,scheme,theta,var,prec", [
+    (1, 63, 1, 32, "theta", 1.0, False, "PH"),
+    (2, 15, 31, 64, "theta", 0.5, True, "PH"),
+    (2, 31, 31, 96, "bdf2", 1.0, True, "PH"),
+    (1, 127, 1, 128, "theta", 0.5, False, "PH"),
+    (2, 63, 63, 256, "theta", 0.5, True, "PH"),
+    (2, 31, 15, 64, "theta", 0.5, False, "Ptheta"),
+])
+def test_fp64_time_digits_match_oracle(pkg, dim, mx, my, n, scheme, theta, var, prec):
+    """The float64 path's time stage on the tensor cores (S_n and the double-float data cut into
+    seven 7-bit integer digits, each digit group accumulated exactly in float32): P^-1 v within
+    the float64 path's oracle tolerance, within 1e-12 of the CUDA-core double-float kernel
+    (ST_DISABLE_TENSOR_CORES=1) but not bitwise equal to it (a different kernel ran), and the same
+    MINRES iterates as the oracle at equal iteration count (1e-10)."""
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=var, seed=3 * n + mx)
+    p = H.Problem.from_workload(w, prec=prec)
+    v = np.random.default_rng(8).standard_normal((n, p.m))
+    ref = H.apply_prec(p, v)
+    spec = pkg.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, prec, "fp64")
+    s_tc = pkg.Solver(spec)
+    z_tc = s_tc.st_apply_prec(torch.tensor(v, device="cuda")).cpu().numpy()
+    os.environ["ST_DISABLE_TENSOR_CORES"] = "1"
+    try:
+        s_cc = pkg.Solver(spec)
+    finally:
+        del os.environ["ST_DISABLE_TENSOR_CORES"]
+    z_cc = s_cc.st_apply_prec(torch.tensor(v, device="cuda")).cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(z_tc - ref).max() / scale <= _prec_tol64(p)
+    assert np.abs(z_tc - z_cc).max() / scale <= max(1e-12, _prec_tol64(p) / 10)
+    assert not np.array_equal(z_tc, z_cc)
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    K = 5
+    x_or, _ = H.solve(p, fH, tol=0.0, maxit=K, rule="est")
+    u, st = s_tc.st_solve(torch.tensor(fH, device="cuda").reshape(-1), tol=0.0, maxit=K,
+                          allow_not_converged=True)
+    assert st["iterations"] == K
+    assert _rel2(u.cpu().numpy().reshape(n, p.m), x_or) <= 1e-10
+    s_tc.close()
+    s_cc.close()
