@@ -1280,23 +1280,28 @@ cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &s
 // With S's digits read from shared memory each MMA (M = 128, N = 32) costs about ten times one
 // that reads A from tensor memory, so the seven digits of one parity (448 tensor-memory columns)
 // stay resident for a whole phase: a block takes its tiles of 32 spatial columns once for each
-// parity.  Per tile and parity:
-//   1. fold the tile's rows for that parity (x_t + x_{n+1-t}, or x_t - x_{n+1-t}), choose each
-//      column's scale from its largest folded entry, write the seven digits as fp16 B operands
-//      (canonical K-major, [digit][32][h]);
-//   2. one thread issues the digit groups in order, g = 0..6, alternating between two 32-column
-//      accumulators: group g + 1 runs on the tensor cores while the block drains group g with
-//      tcgen05.ld and adds it into double-float sums (one row, 8 columns per thread);
-//   3. the rows of that parity are unscaled (and, in the first launch, multiplied by 1/p with
-//      <v, P^-1 v> accumulated), staged in shared memory and written out row by row.
+// parity.  Within a phase three roles work on different tiles at once, handing off through
+// mbarriers (every wait bounded):
+//   - eight build warps fold a tile's rows for the parity (x_t + x_{n+1-t}, or the difference),
+//     choose each column's scale from its largest folded entry and write the seven digits as fp16
+//     B operands (canonical K-major, [digit][32][h]) into one of two buffers;
+//   - one thread issues the digit groups g = 0..6 of a tile in order, alternating between two
+//     32-column accumulators, and frees the B buffer after the tile's last group;
+//   - eight drain warps take each group out of tensor memory (tcgen05.ld; one row, 16 columns
+//     per thread), add it into double-float sums, release the accumulator, and after group 6
+//     unscale the tile's rows (and in the first launch multiply by 1/p and accumulate
+//     <v, P^-1 v>), stage them in shared memory and write them out row by row.
 // A row of output depends on every input row, so the transform cannot run in place: the first
 // launch reads the data and writes the scaled transform into a scratch vector, the second
 // transforms the scratch vector back into the data.
 namespace {
 
-constexpr int kDg = 7;      // digits per operand
-constexpr int kDgW = 7;     // bits per digit
-constexpr int kNTG = 512;   // threads per block
+constexpr int kDg = 7;                                   // digits per operand
+constexpr int kDgW = 7;                                  // bits per digit
+constexpr int kDrainW = 8;                               // warps 0..7: drain and epilogue
+constexpr int kBuildW = 8;                               // warps 8..15: digits of the next tile
+constexpr int kNTG = (kDrainW + kBuildW + 1) * 32;       // and warp 16: the MMA thread
+constexpr int kBarD = 1, kBarB = 2;                      // named barriers of the two groups
 
 struct TcdSmem {
   uint32_t bdig, ytile, part, cdown, tmu, mbar, tmem, total;
@@ -1306,19 +1311,18 @@ __host__ __device__ inline TcdSmem tcd_layout(int n) {
   const int h = n / 2;
   TcdSmem L{};
   uint32_t o = 0;
-  L.bdig = o;  // [digit][32][h] fp16, one parity
-  o += (uint32_t)kDg * kTN * (uint32_t)h * 2u;
-  o = (o + 127u) & ~127u;
-  L.ytile = o;  // one parity's rows: hi floats then lo floats, [h][kYS]
+  L.bdig = o;  // two buffers of [digit][32][h] fp16
+  o += 2u * kDg * kTN * (uint32_t)h * 2u;
+  L.ytile = o;  // the drain warps' staged rows: hi floats then lo floats, [h][kYS]
   o += 2u * (uint32_t)h * kYS * 4u;
-  L.part = o;  // 16 warps x 32 per-column partial maxima
-  o += 16u * kTN * 4u;
-  L.cdown = o;  // per column: 2^-(eS + e_c), the factor that undoes both scales
-  o += kTN * 4u;
-  L.tmu = o;  // tau mu_j and the symbol's column factor w_j, double-float
+  L.part = o;  // 8 build warps x 32 per-column partial maxima
+  o += (uint32_t)kBuildW * kTN * 4u;
+  L.cdown = o;  // per buffer and column: 2^-(eS + e_c), the factor that undoes both scales
+  o += 2u * kTN * 4u;
+  L.tmu = o;  // per column: tau mu_j and the symbol's column factor w_j, double-float
   o += 2u * kTN * 8u;
-  L.mbar = o;  // one per accumulator
-  o += 2u * 8u;
+  L.mbar = o;  // bfull[2], bempty[2], afull[2], aempty[2], done
+  o += 9u * 8u;
   L.tmem = o;
   o += 8u;
   L.total = o;
@@ -1338,15 +1342,8 @@ __device__ __forceinline__ float pow2f(int e) {
   return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // 1/p in double-float with the per-row parts hoisted (the double-float form of inv_symbol):
@@ -1384,6 +1381,26 @@ __device__ __forceinline__ dd inv_sym_dd(const Spec<dd> &sp, const SymRowDD &r, 
   return rsqrt_dd(dd_fma(re, re, im * im));
 }
 
+// The seven 7-bit digits of x 2^e (|x 2^e| < 2^7, double-float): X = 2^42 x 2^e rounded to an
+// integer, held as H 2^21 + Lo with 0 <= Lo < 2^21 (32-bit parts: no float64 conversion), is
+// d_0 2^42 + sum_k d_k 2^(42-7k) with d_0 = H >> 21 (signed) and d_k the 7-bit fields below.
+__device__ __forceinline__ void digits7(dd x, float up21, int (&d)[kDg]) {
+  const float xh = x.hi * up21, xl = x.lo * up21;  // exact: powers of two
+  int H = __float2int_rn(xh);                      // |H| <= 2^28; exact when |xh| >= 2^24
+  const float r = xh - (float)H;                   // exact, |r| <= 1/2
+  int Lo = __float2int_rn((r + xl) * 2097152.0f);  // (r + xl) 2^21; the rounding is below 1
+  const int carry = Lo >> 21;                      // floor(Lo / 2^21)
+  Lo -= carry * 2097152;
+  H += carry;
+  d[0] = H >> 21;
+  d[1] = (H >> 14) & 127;
+  d[2] = (H >> 7) & 127;
+  d[3] = H & 127;
+  d[4] = (Lo >> 14) & 127;
+  d[5] = (Lo >> 7) & 127;
+  d[6] = Lo & 127;
+}
+
 // scaled: out = (S_n x)/p per column with <in, P^-1 in> into the MINRES state (tmode);
 // otherwise out = S_n x.  in and out do not overlap.
 __global__ void __launch_bounds__(kNTG, 1)
@@ -1396,17 +1413,24 @@ __global__ void __launch_bounds__(kNTG, 1)
   const int h = n >> 1, hb = h >> 3;
   const TcdSmem L = tcd_layout(n);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bop = (uint32_t)kTN * h * 2u;   // one digit's B operand
+  const uint32_t bbytes = (uint32_t)kDg * bop;   // one B buffer
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
   float *yhi = reinterpret_cast<float *>(smem + L.ytile);
   float *ylo = yhi + (size_t)h * kYS;
   float *part = reinterpret_cast<float *>(smem + L.part);
   float *cdown = reinterpret_cast<float *>(smem + L.cdown);
-  dd *tmus = reinterpret_cast<dd *>(smem + L.tmu);  // tau mu_j, then w_j
-  const uint32_t mbar0 = smem_u32(smem + L.mbar);
+  dd *tmus = reinterpret_cast<dd *>(smem + L.tmu);
+  const uint32_t mb = smem_u32(smem + L.mbar);
+  const uint32_t bfull = mb, bempty = mb + 16u, afull = mb + 32u, aempty = mb + 48u,
+                 done = mb + 64u;
   const long long ntiles = (m + kTN - 1) / kTN;
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8u * i) : "memory");
+    for (int i = 0; i < 9; ++i) {
+      const uint32_t cnt = (i == 6 || i == 7) ? (uint32_t)kDrainW : 1u;  // aempty: every drain warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb + 8u * i), "r"(cnt)
+                   : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -1418,43 +1442,32 @@ __global__ void __launch_bounds__(kNTG, 1)
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t acol = (uint32_t)(h / 2);          // tensor-memory columns of one S digit
-  const uint32_t dcol = tmem + (uint32_t)kDg * acol;  // the two accumulators follow S
-  uint32_t ph[2] = {0u, 0u};
-  bool ok = true;
-  bool pend[2] = {false, false};  // a commit whose completion has not been seen
-  MacAcc<dd> en;                  // this thread's part of <v, P^-1 v>
-  en.zero();
-  // build view: column bc, t-block bw (rows 8 bw.. and their mirrors)
-  const int bc = tid & (kTN - 1), bw = warp;
-  // drain view: lanes 32 q4.., columns 8 cc..
-  const int q4 = warp & 3, cc = warp >> 2;
-  const int r = (q4 << 5) + lane;
-  const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
-  const uint32_t bop = (uint32_t)kTN * h * 2u;  // one digit's B operand
-
-  // issue digit group g into accumulator g & 1 and commit it (thread 0)
-  auto issue_group = [&](int g) {
-    const uint32_t d = dcol + (uint32_t)(kTN * (g & 1));
-    const uint32_t bbase = smem_u32(smem + L.bdig);
-    bool first = true;
-    for (int i = (g > kDg - 1 ? g - (kDg - 1) : 0); i <= g && i < kDg; ++i) {
-      const int j = g - i;
-      for (int ks = 0; ks < h / 16; ++ks) {
-        mma_f16_ta(d, tmem + (uint32_t)i * acol + (uint32_t)ks * 8u,
-                   make_desc(bbase + (uint32_t)j * bop + (uint32_t)ks * 256u, h), first ? 0u : 1u);
-        first = false;
-      }
+  if (tid == 0) {  // both B buffers and both accumulators start free
+    mbar_arrive(bempty);
+    mbar_arrive(bempty + 8u);
+    for (int k = 0; k < kDrainW; ++k) {
+      mbar_arrive(aempty);
+      mbar_arrive(aempty + 8u);
     }
-    mma_commit(mbar0 + 8u * (g & 1));
-  };
+  }
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t acol = (uint32_t)(h / 2);            // tensor-memory columns of one S digit
+  const uint32_t dcol = tmem + (uint32_t)kDg * acol;  // the two accumulators follow S
+  bool ok = true;
+  // phases of bfull, bempty, afull and aempty as this thread's role waits on them
+  uint32_t pbf[2] = {0u, 0u}, pbe[2] = {0u, 0u}, paf[2] = {0u, 0u}, pae[2] = {0u, 0u};
+  uint32_t G = 0;  // digit groups this thread's role has handled (accumulator G & 1)
+  MacAcc<dd> en;   // drain threads: their part of <v, P^-1 v>
+  en.zero();
+  __syncthreads();
 
   for (int P = 0; P < 2 && ok; ++P) {
-    // this parity's seven S digits into tensor memory (lane = row r, 16 K values per 8 columns)
+    // this parity's seven S digits into tensor memory: warp w writes lanes 32 (w % 4).., pieces
+    // split among the warps of that quadrant
     {
-      const uint32_t tl = (uint32_t)(q4 * 32) << 16;
-      for (int pc = warp >> 2; pc < kDg; pc += 4) {
+      const int q = warp & 3, nq = (kNTG / 32 - q + 3) / 4, r = (q << 5) + lane;
+      const uint32_t tl = (uint32_t)(q * 32) << 16;
+      for (int pc = warp >> 2; pc < kDg; pc += nq) {
         const unsigned char *img = A_g + (size_t)(P * kDg + pc) * kM * h * 2u;
         for (int ks = 0; ks < h / 16; ++ks) {
           uint32_t w[8];
@@ -1467,155 +1480,204 @@ __global__ void __launch_bounds__(kNTG, 1)
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    const int krow = (P == 0) ? 2 * r + 1 : 2 * r + 2;  // time frequency of drain row r
-    const bool row_ok = r < h && krow <= n;
-    const SymRowDD srow = sym_row_dd(sp, row_ok ? krow : 1);
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const long long j0 = tile * kTN;
-      const int je = (int)min((long long)kTN, m - j0);
-      if (scaled && tid < kTN) {
-        dd tv(0.f, 0.f);
-        if (tid < je) {
-          const long long jj = j0 + tid;
-          const long long jy = jj / mx, jx = jj - jy * mx;
-          tv = sp.mux[jx] + sp.muy[jy];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == kDrainW + kBuildW) {
+      // ---------------------------------------------------------------- MMA thread
+      if (lane == 0) {
+        int u = 0;
+        for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++u) {
+          const int b = u & 1;
+          if (!mbar_wait(bfull + 8u * b, pbf[b])) {
+            ok = false;
+            break;
+          }
+          pbf[b] ^= 1u;
+          const uint32_t bbase = smem_u32(smem + L.bdig) + (uint32_t)b * bbytes;
+          for (int g = 0; g < kDg; ++g) {
+            const int a = (int)(G & 1u);
+            if (!mbar_wait(aempty + 8u * a, pae[a])) {
+              ok = false;
+              break;
+            }
+            pae[a] ^= 1u;
+            fence_after();
+            const uint32_t d = dcol + (uint32_t)(kTN * a);
+            bool first = true;
+            for (int i = 0; i <= g; ++i) {
+              const int j = g - i;
+              for (int ks = 0; ks < h / 16; ++ks) {
+                mma_f16_ta(d, tmem + (uint32_t)i * acol + (uint32_t)ks * 8u,
+                           make_desc(bbase + (uint32_t)j * bop + (uint32_t)ks * 256u, h),
+                           first ? 0u : 1u);
+                first = false;
+              }
+            }
+            mma_commit(afull + 8u * a);
+            ++G;
+          }
+          if (!ok) break;
+          mma_commit(bempty + 8u * b);  // the buffer is free once this tile's MMAs are done
         }
-        tmus[tid] = tv;
-        tmus[kTN + tid] = sym_col_w(sp, tv);
       }
-      // 1. fold, scale and digits of this parity
-      {
-        dd f[8];
+      __syncwarp();
+    } else if (warp >= kDrainW) {
+      // ---------------------------------------------------------------- build warps
+      const int bw = warp - kDrainW, bc = lane;
+      int u = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
+        const int b = u & 1;
+        const long long j0 = tile * kTN;
+        const int je = (int)min((long long)kTN, m - j0);
+        ok = group_sync_and(mbar_wait(bempty + 8u * b, pbe[b]), kBarB, kBuildW * 32);
+        if (!ok) break;
+        pbe[b] ^= 1u;
+        dd f[2][8];
         float mxv = 0.f;
-        if (bw < hb) {
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+          const int tb = bw + kBuildW * it;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const int t = bw * 8 + q;
-            dd a(0.f, 0.f), b(0.f, 0.f);
-            if (bc < je) {
-              a = ld_dd(in + (long long)t * m + j0 + bc);
-              b = ld_dd(in + (long long)(n - 1 - t) * m + j0 + bc);
+            f[it][q] = dd(0.f, 0.f);
+            if (tb < hb && bc < je) {
+              const int t = tb * 8 + q;
+              const dd x1 = ld_dd(in + (long long)t * m + j0 + bc);
+              const dd x2 = ld_dd(in + (long long)(n - 1 - t) * m + j0 + bc);
+              f[it][q] = P == 0 ? x1 + x2 : x1 - x2;
+              mxv = fmaxf(mxv, fabsf(f[it][q].hi));
             }
-            f[q] = P == 0 ? a + b : a - b;
-            mxv = fmaxf(mxv, fabsf(f[q].hi));
           }
         }
         part[bw * kTN + bc] = mxv;
-        fence_before();
-        __syncthreads();  // also: the previous tile's drains and write-out are done
-        fence_after();
+        group_sync(kBarB, kBuildW * 32);
         float cm = 0.f;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) cm = fmaxf(cm, part[k * kTN + bc]);
+        for (int k = 0; k < kBuildW; ++k) cm = fmaxf(cm, part[k * kTN + bc]);
         int e = 0;
         if (cm > 0.f && isfinite(cm)) {
           int E;
           frexpf(cm, &E);
           e = 7 - E;  // cm 2^e in [2^6, 2^7)
         }
-        if (bw == 0) cdown[bc] = pow2f(-(eS + e));
-        if (bw < hb) {
-          const float up = pow2f(e + 42);  // scale and fixed point in one exact factor
-          const uint32_t off = canon_off(bc, bw * 8, h);
-          long long V[8];
+        if (bw == 0) cdown[b * kTN + bc] = pow2f(-(eS + e));
+        const float up21 = pow2f(e + 21);
+        unsigned char *bb = smem + L.bdig + (uint32_t)b * bbytes;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) V[q] = __float2ll_rn(f[q].hi * up) + __float2ll_rn(f[q].lo * up);
+        for (int it = 0; it < 2; ++it) {
+          const int tb = bw + kBuildW * it;
+          if (tb >= hb) continue;
+          int dq[8][kDg];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) digits7(f[it][q], up21, dq[q]);
+          const uint32_t off = canon_off(bc, tb * 8, h);
 #pragma unroll
           for (int dg = 0; dg < kDg; ++dg) {
             uint32_t pk[4];
 #pragma unroll
             for (int q2 = 0; q2 < 4; ++q2) {
-              int d2[2];
-#pragma unroll
-              for (int h2 = 0; h2 < 2; ++h2) {
-                const long long Vq = V[2 * q2 + h2];
-                d2[h2] = dg == 0 ? (int)(Vq >> 42) : (int)((Vq >> (42 - kDgW * dg)) & 127);
-              }
-              const __half2 hv = __floats2half2_rn((float)d2[0], (float)d2[1]);
+              const __half2 hv = __floats2half2_rn((float)dq[2 * q2][dg], (float)dq[2 * q2 + 1][dg]);
               pk[q2] = *reinterpret_cast<const uint32_t *>(&hv);
             }
-            *reinterpret_cast<uint4 *>(smem + L.bdig + (uint32_t)dg * bop + off) =
+            *reinterpret_cast<uint4 *>(bb + (uint32_t)dg * bop + off) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
           }
         }
+        fence_async_smem();
+        group_sync(kBarB, kBuildW * 32);  // the buffer is written (and `part` read)
+        if (bw == 0 && lane == 0) mbar_arrive(bfull + 8u * b);
       }
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
-      fence_after();
-      // 2. digit groups through two accumulators; the block drains group g while g + 1 runs
-      if (tid == 0) {
-        issue_group(0);
-        issue_group(1);
-      }
-      pend[0] = pend[1] = true;
-      float s[8], t[8];
-      for (int g = 0; g < kDg; ++g) {
-        const int b = g & 1;
-        const bool w = __syncthreads_and(mbar_wait(mbar0 + 8u * b, ph[b]) ? 1 : 0) != 0;
-        if (!w) {
-          ok = false;
-          break;
-        }
-        pend[b] = false;
-        ph[b] ^= 1u;
-        fence_after();
-        float v[8];
-        tmem_ld8(dcol + lanes + (uint32_t)(kTN * b + 8 * cc), v);
-        const float sc = pow2f(-kDgW * g);
+    } else {
+      // ---------------------------------------------------------------- drain warps
+      const int q4 = warp & 3, c0 = (warp >> 2) * 16;
+      const int r = (q4 << 5) + lane;
+      const int krow = (P == 0) ? 2 * r + 1 : 2 * r + 2;  // time frequency of row r (1-based)
+      const bool row_ok = r < h && krow <= n;
+      const SymRowDD srow = sym_row_dd(sp, row_ok ? krow : 1);
+      const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+      int u = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
+        const int b = u & 1;
+        const long long j0 = tile * kTN;
+        const int je = (int)min((long long)kTN, m - j0);
+        ok = group_sync_and(mbar_wait(bfull + 8u * b, pbf[b]), kBarD, kDrainW * 32);
+        if (!ok) break;
+        pbf[b] ^= 1u;
+        float cd[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float x = v[c] * sc;
-          if (g == 0) {
-            s[c] = x;
-            t[c] = 0.f;
-          } else {
-            float ss, er;
-            two_sum(s[c], x, ss, er);
-            s[c] = ss;
-            t[c] += er;
+        for (int c = 0; c < 16; ++c) cd[c] = cdown[b * kTN + c0 + c];
+        if (scaled && warp == 0) {
+          dd tv(0.f, 0.f);
+          if (lane < je) {
+            const long long jj = j0 + lane;
+            const long long jy = jj / mx, jx = jj - jy * mx;
+            tv = sp.mux[jx] + sp.muy[jy];
+          }
+          tmus[lane] = tv;
+          tmus[kTN + lane] = sym_col_w(sp, tv);
+        }
+        float s[16], t[16];
+        for (int g = 0; g < kDg; ++g) {
+          const int a = (int)(G & 1u);
+          ok = group_sync_and(mbar_wait(afull + 8u * a, paf[a]), kBarD, kDrainW * 32);
+          if (!ok) break;
+          paf[a] ^= 1u;
+          fence_after();
+          float v[16];
+          tmem_ld16(dcol + lanes + (uint32_t)(kTN * a + c0), v);
+          const float sc = pow2f(-kDgW * g);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float x = v[c] * sc;
+            if (g == 0) {
+              s[c] = x;
+              t[c] = 0.f;
+            } else {
+              float ss, er;
+              two_sum(s[c], x, ss, er);
+              s[c] = ss;
+              t[c] += er;
+            }
+          }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(aempty + 8u * a);
+          ++G;
+        }
+        if (!ok) break;
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int col = c0 + c;
+            const dd v = dd_norm(s[c], t[c]);
+            dd y(v.hi * cd[c], v.lo * cd[c]);
+            if (scaled) {
+              const dd yi = y * inv_sym_dd(sp, srow, tmus[col], tmus[kTN + col]);
+              if (col < je) en.add(y, yi);
+              y = yi;
+            }
+            yhi[r * kYS + col] = y.hi;
+            ylo[r * kYS + col] = y.lo;
           }
         }
-        fence_before();
-        __syncthreads();  // accumulator b is drained
-        fence_after();
-        if (g + 2 < kDg) {
-          if (tid == 0) issue_group(g + 2);
-          pend[b] = true;
+        group_sync(kBarD, kDrainW * 32);
+        for (int idx = tid; idx < h * kTN; idx += kDrainW * 32) {
+          const int rr = idx >> 5, c = idx & (kTN - 1);
+          const int k = (P == 0) ? 2 * rr + 1 : 2 * rr + 2;
+          if (c < je && k <= n)
+            st_dd(out + (long long)(k - 1) * m + j0 + c, dd(yhi[rr * kYS + c], ylo[rr * kYS + c]));
         }
-      }
-      if (!ok) break;  // uniform
-      // 3. unscale (and scale by 1/p), stage this parity's rows, write them out
-      if (row_ok) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int col = 8 * cc + c;
-          const dd v = dd_norm(s[c], t[c]);
-          const float fdn = cdown[col];
-          dd y(v.hi * fdn, v.lo * fdn);
-          if (scaled) {
-            const dd yi = y * inv_sym_dd(sp, srow, tmus[col], tmus[kTN + col]);
-            if (col < je) en.add(y, yi);
-            y = yi;
-          }
-          yhi[r * kYS + col] = y.hi;
-          ylo[r * kYS + col] = y.lo;
-        }
-      }
-      __syncthreads();
-      for (int idx = tid; idx < h * kTN; idx += kNTG) {
-        const int rr = idx >> 5, c = idx & (kTN - 1);
-        const int k = (P == 0) ? 2 * rr + 1 : 2 * rr + 2;
-        if (c < je && k <= n)
-          st_dd(out + (long long)(k - 1) * m + j0 + c, dd(yhi[rr * kYS + c], ylo[rr * kYS + c]));
+        group_sync(kBarD, kDrainW * 32);  // the staged rows and tmus are free again
       }
     }
     fence_before();
-    __syncthreads();  // this parity's digits leave tensor memory: every MMA is drained
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;  // every role done: all MMAs of the phase drained
     fence_after();
   }
-  // a timed-out wait leaves its commit outstanding: tc_release_cols waits for it (bounded)
-  tc_release_cols<512>(ok, pend[0], mbar0, ph[0], pend[1], mbar0 + 8u, ph[1], tmem, S, true);
+  if (warp == kDrainW + kBuildW && lane == 0) mma_commit(done);
+  // after a timeout `done` tracks every MMA issued: tc_release_cols waits for it (bounded)
+  tc_release_cols<512>(ok, true, done, 0u, false, 0u, 0u, tmem, S, true);
   if (scaled && tmode != TM_NONE) {
     const double e = (double)en.get();
     double tot;
