@@ -1494,7 +1494,10 @@ __global__ void __launch_bounds__(kNTG, 1)
             break;
           }
           pbf[b] ^= 1u;
-          const uint32_t bbase = smem_u32(smem + L.bdig) + (uint32_t)b * bbytes;
+          // descriptors differ only in their start-address field (address / 16), so each MMA
+          // takes one add on a descriptor built once per tile
+          const uint64_t bdesc = make_desc(smem_u32(smem + L.bdig) + (uint32_t)b * bbytes, h);
+          const int ksteps = h / 16;
           for (int g = 0; g < kDg; ++g) {
             const int a = (int)(G & 1u);
             if (!mbar_wait(aempty + 8u * a, pae[a])) {
@@ -1504,14 +1507,14 @@ __global__ void __launch_bounds__(kNTG, 1)
             pae[a] ^= 1u;
             fence_after();
             const uint32_t d = dcol + (uint32_t)(kTN * a);
-            bool first = true;
+            uint32_t acc = 0u;
             for (int i = 0; i <= g; ++i) {
-              const int j = g - i;
-              for (int ks = 0; ks < h / 16; ++ks) {
-                mma_f16_ta(d, tmem + (uint32_t)i * acol + (uint32_t)ks * 8u,
-                           make_desc(bbase + (uint32_t)j * bop + (uint32_t)ks * 256u, h),
-                           first ? 0u : 1u);
-                first = false;
+              const uint32_t at = tmem + (uint32_t)i * acol;
+              const uint64_t bd = bdesc + (uint64_t)(((uint32_t)(g - i) * bop) >> 4);
+#pragma unroll 8
+              for (int ks = 0; ks < ksteps; ++ks) {
+                mma_f16_ta(d, at + (uint32_t)ks * 8u, bd + (uint64_t)(16 * ks), acc);
+                acc = 1u;
               }
             }
             mma_commit(afull + 8u * a);
