@@ -1604,9 +1604,12 @@ __global__ void __launch_bounds__(kNTG, 1)
         const int b = u & 1;
         const long long j0 = tile * kTN;
         const int je = (int)min((long long)kTN, m - j0);
-        ok = group_sync_and(mbar_wait(bfull + 8u * b, pbf[b]), kBarD, kDrainW * 32);
-        if (!ok) break;
-        pbf[b] ^= 1u;
+        // each warp waits on its own (warp-uniform result); the drain group combines the results
+        // once per tile, before its first named barrier, so that no warp leaves a barrier early
+        if (ok) {
+          ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, pbf[b]) ? 1 : 0) != 0;
+          if (ok) pbf[b] ^= 1u;
+        }
         float cd[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) cd[c] = cdown[b * kTN + c0 + c];
@@ -1623,12 +1626,18 @@ __global__ void __launch_bounds__(kNTG, 1)
         float s[16], t[16];
         for (int g = 0; g < kDg; ++g) {
           const int a = (int)(G & 1u);
-          ok = group_sync_and(mbar_wait(afull + 8u * a, paf[a]), kBarD, kDrainW * 32);
-          if (!ok) break;
+          ++G;
+          if (!ok) continue;
+          ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * a, paf[a]) ? 1 : 0) != 0;
+          if (!ok) continue;
           paf[a] ^= 1u;
           fence_after();
           float v[16];
           tmem_ld16(dcol + lanes + (uint32_t)(kTN * a + c0), v);
+          // the values are in registers: the accumulator is free for group g + 2
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(aempty + 8u * a);
           const float sc = pow2f(-kDgW * g);
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -1643,11 +1652,8 @@ __global__ void __launch_bounds__(kNTG, 1)
               t[c] += er;
             }
           }
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(aempty + 8u * a);
-          ++G;
         }
+        ok = group_sync_and(ok, kBarD, kDrainW * 32);
         if (!ok) break;
         if (row_ok) {
 #pragma unroll
