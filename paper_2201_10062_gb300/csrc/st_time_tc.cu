@@ -429,13 +429,16 @@ __global__ void __launch_bounds__(kNT, 1)
     long long base;
     int je;
     tile_at(tile, base, je);
-    const uint32_t sbase = smem_u32(stage);
-    for (int idx = gt; idx < len * kTN; idx += kGT) {
-      const int e = idx >> 5, c = idx & (kTN - 1);
+    // thread gt copies column c = gt % 32 of rows gt / 32, + 8, + 16, ... (running pointers)
+    const int c = gt & (kTN - 1), e0 = gt >> 5;
+    const float *gp = data + base + (long long)e0 * mx + c;
+    const long long gstep = (long long)(kGT / kTN) * mx;
+    uint32_t sa = smem_u32(stage) + 4u * (uint32_t)gt;
+    for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
       if (c < je)
-        cp_async4(sbase + 4u * (uint32_t)idx, data + base + (long long)e * mx + c);
+        cp_async4(sa, gp);
       else
-        stage[idx] = 0.f;
+        stage[e * kTN + c] = 0.f;
     }
     cp_async_commit();
   };
@@ -519,9 +522,16 @@ __global__ void __launch_bounds__(kNT, 1)
     fence_before();
     group_sync(bar, kGT);
     fence_after();
-    for (int idx = gt; idx < len * kTN; idx += kGT) {
-      const int e = idx >> 5, c = idx & (kTN - 1);
-      if (c < je) out[base + (long long)e * mx + c] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+    {
+      // column c of rows gt / 32, + 8, ...: rows of one parity, 4 rows apart in the Y tile
+      const int c = gt & (kTN - 1), e0 = gt >> 5;
+      if (c < je) {
+        float *op = out + base + (long long)e0 * mx + c;
+        const float *yp = ytile + ((e0 & 1) * h + (e0 >> 1)) * kYS + c;
+        const long long ostep = (long long)(kGT / kTN) * mx;
+        for (int e = e0; e < len; e += kGT / kTN, op += ostep, yp += (kGT / kTN / 2) * kYS)
+          *op = *yp;
+      }
     }
   }
   cp_async_wait_all();
