@@ -2,12 +2,13 @@
 // a(x)) run concurrently in one CUDA graph, launched once per solve.
 //
 // The graph holds one conditional WHILE node per instance; the nodes have no dependencies, so the
-// instances run side by side.  The body of instance i is two MINRES iterations (even and odd
-// buffer parity) followed by a refinement block: convert the double-float x to float64,
-// recompute the float64 residual, and let the residual kernel's last block decide (done, or
-// restart the inner run with the residual as right-hand side).  A restart zeroes the direction
-// buffers and re-initialises the inner run through a preconditioner pass gated on the state's
-// `restart` flag, so the next trip starts again at even parity.  The body ends with a one-thread
+// instances run side by side.  The body of instance i is four MINRES iterations (z in a ring of
+// four vectors, with a grouped direction/solution update after the second and the fourth)
+// followed by a refinement block: convert the double-float x to float64, recompute the float64
+// residual, and let the residual kernel's last block decide (done, or restart the inner run with
+// the residual as right-hand side).  A restart zeroes the direction buffers and re-initialises
+// the inner run through a preconditioner pass gated on the state's `restart` flag, so the next
+// trip starts again at the ring's first slot.  The body ends with a one-thread
 // kernel that sets the loop's condition from the device state: the loop of an instance ends as
 // soon as it is done, so a finished instance launches nothing more, and no host decision sits
 // anywhere inside the solve.  Each loop also stops after a fixed number of trips (maxit + 64),
@@ -81,14 +82,16 @@ __global__ void k_gather(State *const *states, int count, BatchInfo *out) {
   out[i] = b;
 }
 
-// one MINRES iteration with explicit buffer parity c (0: iterations 1, 3, ...; 1: 2, 4, ...)
-cudaError_t iteration(st_handle *h, int c, cudaStream_t st) {
-  const int o = c ^ 1;
+// MINRES iteration b (0..3) of a trip: iterations 4t + 1 .. 4t + 4 of an inner run, z_k in ring
+// slot (k - 1) % 4 (st_setup_batch gives the instance handles four z vectors), the Lanczos
+// vectors alternating with the parity of k; the direction/solution update runs after b = 1 and
+// b = 3 and applies the iterations pending since the previous one (k_update_group_df)
+cudaError_t iteration(st_handle *h, int b, cudaStream_t st) {
+  const int c = b & 1, o = c ^ 1;
   const Geom &g = h->g;
-  const float *zc = (const float *)h->Z[c];
-  float *zn = (float *)h->Z[o];
+  const float *zc = zslot(h, b);
+  float *zn = zslot(h, (b + 1) & 3);
   df *V0 = (df *)h->V[c], *V1 = (df *)h->V[o];
-  df *D0 = (df *)h->D[c], *D1 = (df *)h->D[o];
   df *q = (df *)h->q;
   cudaError_t e;
   if ((e = launch_stencil_df(g, zc, q, h->S, h->partials, st)) != cudaSuccess) return e;
@@ -96,7 +99,7 @@ cudaError_t iteration(st_handle *h, int c, cudaStream_t st) {
   if ((e = launch_prec_lanczos<float, df, float>(g, h->pp, q, V0, V1, zn, h->S, h->partials,
                                                  st)) != cudaSuccess)
     return e;
-  return launch_update_df(g.N, zc, D0, D1, h->Xdf, h->S, st);
+  return (b & 1) ? launch_update_group(h, st) : cudaSuccess;
 }
 
 // refinement block: x (float64) <- x (df); r <- Y f_H - Y T x with decision; restart if asked
@@ -192,8 +195,7 @@ int capture(st_batch *b, const double *const *fH, double *const *u, int maxit) {
     cudaStream_t s = b->streams[i];
     e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) break;
-    e = iteration(b->h[i], 0, s);
-    if (e == cudaSuccess) e = iteration(b->h[i], 1, s);
+    for (int it = 0; it < 4 && e == cudaSuccess; ++it) e = iteration(b->h[i], it, s);
     if (e == cudaSuccess) e = refine(b->h[i], fH[i], u[i], s);
     if (e == cudaSuccess) {
       k_loop_control<<<1, 32, 0, s>>>(cond, b->h[i]->S, b->d_trips + i, max_trips);
@@ -261,7 +263,9 @@ int st_setup_batch(const st_problem *probs, int count, void *stream, st_batch **
     // caller's stream; the batch solve passes its internal streams explicitly
     st_problem p = probs[i];
     p.stream = stream;
-    int r = setup_handle(&p, &b->h[i], 1);
+    // group of 3 (four z vectors): the captured trip uses the ring of four with an update pass
+    // after every second iteration
+    int r = setup_handle(&p, &b->h[i], 3);
     if (r) return fail(r);
     // launch shapes per (size, precision), cached across instances of the same shape
     r = st_autotune(b->h[i], 5);

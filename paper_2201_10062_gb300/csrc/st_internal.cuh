@@ -456,9 +456,10 @@ cudaError_t launch_resid_df(const Geom &g, const double *x, df *r_out, const dou
 // done; r = Y f_H - Y T x into r_out and, in the last block, the done/restart decision
 cudaError_t launch_resid_outer(const Geom &g, const double *x, df *r_out, const double *fH,
                                State *S, double *partials, cudaStream_t st);
-// one iteration's direction/solution update (batched solves), while the MINRES run is active
-cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, cudaStream_t st);
+// every pending direction/solution update of a mixed solve (k_update_group_df), and the ring
+// slot of a mixed handle's z vectors (slot s of Z[0], Z[1], Zx[0], ...)
+cudaError_t launch_update_group(st_handle *h, cudaStream_t st);
+float *zslot(st_handle *h, int s);
 cudaError_t launch_flip_to_df(const Geom &g, const double *src, df *dst, cudaStream_t st);
 cudaError_t launch_df_to_double(long long N, const df *src, double *dst, cudaStream_t st);
 

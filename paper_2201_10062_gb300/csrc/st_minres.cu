@@ -94,42 +94,16 @@ namespace {
 // ------------------------------------------------------------------ double-float vectors
 // Mixed path: vhat, d and x are double-floats (hi + lo float32 pairs, ~46 significant bits);
 // the per-element arithmetic runs on the float32 pipes (see st_df.cuh).
-__global__ void __launch_bounds__(kNT)
-    k_update_df(long long N, const float *__restrict__ z, const df *__restrict__ d1,
-                df *__restrict__ d2, df *__restrict__ x, const State *S) {
-  if (!S->active) return;
-  const df cz = S->dfs[DFS_DZ], c1 = S->dfs[DFS_D1], c2 = S->dfs[DFS_D2], cx = S->dfs[DFS_XC];
-  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
-       i += (long long)gridDim.x * kNT) {
-    float s = 0.f, t = 0.f;
-    {
-      const float zi = z[i];
-      float p, e;
-      two_prod(cz.hi, zi, p, e);
-      e = fmaf(cz.lo, zi, e);
-      dacc_add(s, t, p, e);
-    }
-    dacc_prod(s, t, c1, d1[i]);
-    dacc_prod(s, t, c2, d2[i]);
-    const df d = df_from_sum(s, t);
-    d2[i] = d;
-    const df xo = x[i];
-    float xs = xo.hi, xt = xo.lo;
-    dacc_prod(xs, xt, cx, d);
-    x[i] = df_from_sum(xs, xt);
-  }
-}
-
-// Grouped direction and solution update (mixed single solves).  The direction recurrence
-// d_j = dz_j z_j + d1_j d_{j-1} + d2_j d_{j-2} and the solution update x += xc_j d_j consume the
-// preconditioned vectors z_j but feed nothing back into the Lanczos recurrence, so the updates
-// of up to kUpdRing iterations are applied in one pass: each element reads its pending z_j (one
-// float32 vector per iteration), the two latest directions and x once, runs the recurrence in
-// registers with every iteration's scalars (State::ucoef) and writes back the two latest
-// directions and x.  With G iterations per pass the update moves 4 + 48/G bytes per unknown and
+//
+// Grouped direction and solution update (mixed solves, single and batched).  The direction
+// recurrence d_j = dz_j z_j + d1_j d_{j-1} + d2_j d_{j-2} and the solution update x += xc_j d_j
+// consume the preconditioned vectors z_j but feed nothing back into the Lanczos recurrence, so
+// the updates of up to kUpdRing iterations are applied in one pass: each element reads its
+// pending z_j (one float32 vector per iteration), the two latest directions and x once, runs the
+// recurrence in registers with every iteration's scalars (State::ucoef) and writes back the two
+// latest directions and x.  With G iterations per pass the update moves 4 + 48/G bytes per unknown and
 // iteration instead of 44, and every element goes through the same float32 operations in the
-// same order, whatever G (the per-iteration kernel k_update_df adds its first product to a zero
-// sum; here the sum starts as that product, which differs at most in the sign of a zero).
+// same order, whatever G.
 //
 // The pending iterations are upd + 1 .. k of the device state: the pass reads both counters at
 // entry and its last block to finish sets upd = k, so a pass with nothing pending returns at once
@@ -302,18 +276,10 @@ cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_df(long long N, const float *z, const df *d1, df *d2_out, df *x,
-                             State *S, cudaStream_t st) {
-  prof_begin(KC_UPDATE, st);
-  k_update_df<<<kStreamBlocks, kNT, 0, st>>>(N, z, d1, d2_out, x, S);
-  prof_end(st);
-  return cudaGetLastError();
-}
-
 float *zslot(st_handle *h, int s) { return s < 2 ? (float *)h->Z[s] : h->Zx[s - 2]; }
 
-// applies every pending direction/solution update of the mixed single solve (see
-// k_update_group_df); the device state decides how many
+// applies every pending direction/solution update of a mixed solve (see k_update_group_df); the
+// device state decides how many
 cudaError_t launch_update_group(st_handle *h, cudaStream_t st) {
   ZRing zr{};
   zr.len = h->ugroup + 1;

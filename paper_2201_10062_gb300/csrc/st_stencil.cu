@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kNT) k_stencil(Geom g, const Tz *__restrict__ 
             S->target = t > S->inner_floor ? t : S->inner_floor;
             S->maxit = S->maxit_total - S->total;
             S->k = 0;
+            S->upd = 0;  // the grouped update of the new inner run starts from iteration 1
             S->finish = 0;
             S->active = 0;
             S->restart = 1;

@@ -551,17 +551,23 @@ constexpr int kGroups3 = 3;
 constexpr int kNT3 = kGroups3 * kGT;  // 768 threads
 
 struct Tc3Smem {
-  uint32_t bop, ytile, colinv1, colinv2, colmax, tmu, mbar, total;
+  uint32_t bop, ytile, stage, colinv1, colinv2, colmax, tmu, mbar, total;
 };
 
+// The B operand and the Y tile are never live together (the second build reads the whole Y tile
+// into registers before its column-maximum barrier, and writes B after it), so they share one
+// region; the room this frees holds the staged next tile.
 __host__ __device__ inline Tc3Smem tc3_layout(int n) {
   const int h = n / 2;
   Tc3Smem L{};
+  const uint32_t bbytes = 2u * 2u * kTN * h * 2u, ybytes = (uint32_t)n * kYS * 4u;
   uint32_t o = 0;
   L.bop = o;
-  o += 2u * 2u * kTN * h * 2u;
   L.ytile = o;
-  o += (uint32_t)n * kYS * 4u;
+  o += bbytes > ybytes ? bbytes : ybytes;
+  o = (o + 15u) & ~15u;
+  L.stage = o;  // the next tile, [t][32] floats, loaded with cp.async
+  o += (uint32_t)n * kTN * 4u;
   L.colinv1 = o;
   o += kTN * 4u;
   L.colinv2 = o;
@@ -642,6 +648,23 @@ __global__ void __launch_bounds__(kNT3, 1)
   uint32_t phase = 0;
   bool ok = true, outstanding = false;
   float esum = 0.f, ecomp = 0.f;
+  float *stage = reinterpret_cast<float *>(gs + L.stage);
+  // copy the tile's n rows x 32 columns into the stage (zeros beyond the last column)
+  auto prefetch = [&](long long tile) {
+    const long long tj0 = tile * kTN;
+    const int tje = (int)min((long long)kTN, m - tj0);
+    const int c = gt & (kTN - 1), t0 = gt >> 5;
+    const float *gp = data + (long long)t0 * m + tj0 + c;
+    const long long gstep = (long long)(kGT / kTN) * m;
+    uint32_t sa = smem_u32(stage) + 4u * (uint32_t)gt;
+    for (int t = t0; t < n; t += kGT / kTN, gp += gstep, sa += 4u * kGT) {
+      if (c < tje)
+        cp_async4(sa, gp);
+      else
+        stage[t * kTN + c] = 0.f;
+    }
+    cp_async_commit();
+  };
   const int q = warp & 3, P = w8 >> 2;
   const int r = (q << 5) + lane;
   const uint32_t tl = dcol + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN);
@@ -663,7 +686,9 @@ __global__ void __launch_bounds__(kNT3, 1)
     return true;
   };
   const long long tstride = (long long)kGroups3 * gridDim.x;
-  for (long long tile = (long long)blockIdx.x * kGroups3 + grp; tile < ntiles; tile += tstride) {
+  const long long tfirst = (long long)blockIdx.x * kGroups3 + grp;
+  if (tfirst < ntiles) prefetch(tfirst);
+  for (long long tile = tfirst; tile < ntiles; tile += tstride) {
     const long long j0 = tile * kTN;
     const int je = (int)min((long long)kTN, m - j0);
     if (gt < kTN) {
@@ -675,11 +700,16 @@ __global__ void __launch_bounds__(kNT3, 1)
       }
       tmus[gt] = t;
     }
+    cp_async_wait_all();
+    group_sync(bar, kGT);  // this tile is staged
     {
       float a[2][8], b[2][8];
-      load_b_g(n, gt, data, m, j0, je, a, b);
+      load_b_g_src(n, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, b);
       build_b_g(gs + L.bop, colinv1, part, n, a, b, gt, bar);
     }
+    // every thread has read the stage (the column-maximum barrier inside the build): load the
+    // next tile while this one is transformed
+    if (tile + tstride < ntiles) prefetch(tile + tstride);
     if (!(ok = run_mmas())) break;
     // first epilogue: unscale, spectral scaling, energy; scaled Y into the parity-split tile
     {
@@ -733,6 +763,7 @@ __global__ void __launch_bounds__(kNT3, 1)
     }
     group_sync(bar, kGT);
   }
+  cp_async_wait_all();
   tc_release_cols<512>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
   if (tmode != TM_NONE) {
     const double e = (double)esum - (double)ecomp;
