@@ -64,8 +64,7 @@ CLASS_BYTES = {
 # launch of one mixed 2D Crank-Nicolson solve at 255^2 x 256), per kernel class, for the kernels
 # whose code is unchanged since: profiles/dram_traffic_mixed_cn2d_255x255_n256.md
 NCU_TRAFFIC = {("mixed", "stencil"): 136.0e6, ("mixed", "lanczos_dst_x"): 539.6e6,
-               ("mixed", "dst_x"): 70.3e6, ("mixed", "dst_y"): 72.9e6,
-               ("mixed", "time_dst_scale"): 72.9e6, ("mixed", "residual"): 373.3e6}
+               ("mixed", "dst_x"): 70.3e6, ("mixed", "residual"): 373.3e6}
 # the grouped update's DRAM bytes per solve (its six launches in the same capture)
 NCU_TRAFFIC_STEP = {("mixed", "update"): 6 * 1212.5e6}
 # the same capture summed over the solve's iteration kernels (stencil, fused Lanczos x pass, y,

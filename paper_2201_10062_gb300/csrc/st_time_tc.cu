@@ -1,5 +1,6 @@
-// Time-axis DST-I -> spectral scaling -> DST-I on the 5th-generation tensor cores (tcgen05),
-// float32-accurate, for the mixed-precision preconditioner (Sec. 3.1.1, steps 1-3 along time).
+// Time-axis DST-I -> spectral scaling -> DST-I on the 5th-generation tensor cores (tcgen05):
+// float32-accurate for the mixed-precision preconditioner (Sec. 3.1.1, steps 1-3 along time),
+// and, at the end of this file, float64-accurate with integer digits for the float64 path.
 //
 // The folded transform is two dense products per parity of the output index k:
 //   odd  k = 2r+1:  Y_k = sum_{t=1..h} S_{k,t} (x_t + x_{n+1-t})
@@ -10,9 +11,9 @@
 // power of two so that fp16 keeps its range; S is scaled by 8.
 //
 // S (both parities, both pieces: 128 KB for n = 256) lives in tensor memory as the A operand of
-// tcgen05.mma; one block per SM runs independent tile pipelines of 8 warps, each walking column
-// tiles of 32: three in the time kernel (k_time_tc3), two, each a two-stage software pipeline,
-// in the spatial one (k_dst_tc_y2).
+// tcgen05.mma; one block per SM walks tiles of 32 columns: the time kernel (k_time_tc3) runs three
+// independent 8-warp tile pipelines, the spatial one (k_dst_tc_yw) splits build, MMA issue and
+// epilogue over separate warps.
 // One thread per pipeline issues tcgen05.mma (M = 128, N = 32, K = 16; B from a shared-memory
 // descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the
 // pipeline's mbarrier, and its warps read the accumulators with tcgen05.ld.  For 256 < n <= 512
@@ -92,6 +93,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     if (done) return true;
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
@@ -217,10 +222,8 @@ __device__ __forceinline__ float inv_sym(const Spec<float> &sp, const SymRow &r,
 // the 512 columns), which leaves shared memory for independent tile pipelines of 8 warps each.
 // Each group has its own B operands, tiles, accumulators, mbarriers and named barrier, so one
 // group's fold/split/scale phases run while the others wait on their barriers or their MMAs; the
-// MMAs read only B from shared memory.  Group g of block b takes the tiles G b + g,
-// G b + g + G gridDim.x, ... (G groups per block: 2 for the spatial kernel, 3 for the time
-// kernel).
-constexpr int kGroups = 2;
+// MMAs read only B from shared memory.  The time kernel runs three such groups per block; group
+// g of block b takes the tiles 3 b + g, 3 b + g + 3 gridDim.x, ...
 constexpr int kGT = 256;  // threads per group
 
 __device__ __forceinline__ void mma_f16_ta(uint32_t dtmem, uint32_t atmem, uint64_t bd,
@@ -261,28 +264,10 @@ __device__ __forceinline__ bool group_sync_and(bool v, int id, int nthreads) {
 
 // Fold, scale and split of one tile for a group of 256 threads: thread (column c = gt % 32,
 // t-blocks tb = gt / 32 and gt / 32 + 8 of 8 rows; h/8 <= 16 t-blocks).  A warp reads or writes
-// whole rows of 32 columns, so the global and staged loads are coalesced and the 16-byte operand
-// stores of a quarter-warp cover eight distinct rows.  The column maximum is reduced in one step:
-// each warp leaves its 32 per-column partial maxima in `part` (8 x 32 floats), the group passes
-// one barrier, and every thread combines the eight partials of its own column.
-__device__ __forceinline__ void load_b_g(int n, int gt, const float *data, long long m,
-                                         long long j0, int je, float (&a)[2][8],
-                                         float (&b)[2][8]) {
-  const int h = n >> 1, hb = h >> 3;
-  const int c = gt & (kTN - 1);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const int tb = (gt >> 5) + 8 * it;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int t = tb * 8 + q;
-      const bool ok = tb < hb && c < je;
-      a[it][q] = ok ? data[(long long)t * m + j0 + c] : 0.f;
-      b[it][q] = ok ? data[(long long)(n - 1 - t) * m + j0 + c] : 0.f;
-    }
-  }
-}
-
+// whole rows of 32 columns, so the staged loads are coalesced and the 16-byte operand stores of
+// a quarter-warp cover eight distinct rows.  The column maximum is reduced in one step: each warp
+// leaves its 32 per-column partial maxima in `part` (8 x 32 floats), the group passes one
+// barrier, and every thread combines the eight partials of its own column.
 template <class Src>
 __device__ __forceinline__ void load_b_g_src(int n, int gt, Src src, float (&a)[2][8],
                                              float (&b)[2][8]) {
@@ -372,51 +357,66 @@ __device__ __forceinline__ void issue_mmas_ta(uint32_t a_base, uint32_t bbase, i
   mma_commit(mbar);
 }
 
-// One DST-I of length len along lines (y, z, or a single time transform): S_len (both
-// parities, hi and lo) in tensor memory as the A operand, two groups of 8 warps, each with its
-// own staged input tile, B operand, Y tile, accumulator (64 columns) and named barrier.
-struct TcYSmem {
-  uint32_t bop, ytile, stage, colinv, colmax, mbar, total;
+// ------------------------------------------------------------------ y-DST: warp-specialised
+// One DST-I of length len along lines (y, z, or a single time transform) of 32-line tiles, with
+// S_len (both parities, hi and lo) in tensor memory as the A operand and the phases of a tile in
+// separate warps that work on different tiles at once, handing off through mbarriers (every wait
+// bounded):
+//   - eight build warps stage the next tile with cp.async, fold, scale and split the current one
+//     into one of two B buffers (with its column factors);
+//   - one thread issues the tile's MMAs into one of two 64-column accumulators and frees the B
+//     buffer when they complete;
+//   - four epilogue warps (one per lane quadrant, both parities of a row) take the accumulator
+//     out, unscale it into the Y tile and write the tile back row by row.
+// A B buffer is free again once its MMAs are done and every epilogue warp has copied its column
+// factors (1 + 4 arrivals), so the build may run a tile ahead of the epilogue.
+constexpr int kEpiW = 4;                              // warps 0..3: epilogue
+constexpr int kBldW = 8;                              // warps 4..11: build
+constexpr int kNTW = (kEpiW + kBldW + 1) * 32;        // and warp 12: the MMA thread (416)
+constexpr int kBarE = 1, kBarBl = 2;                  // named barriers of the two groups
+
+struct TcYwSmem {
+  uint32_t bop, ytile, stage, colinv, colmax, mbar, tmem, total;
 };
 
-__host__ __device__ inline TcYSmem tcy_layout(int len) {
+__host__ __device__ inline TcYwSmem tcyw_layout(int len) {
   const int h = (len + 1) / 2;
-  TcYSmem L{};
+  TcYwSmem L{};
   uint32_t o = 0;
-  L.bop = o;
-  o += 2u * 2u * kTN * h * 2u;
+  L.bop = o;  // two B buffers, each [parity][piece][32][h] fp16
+  o += 2u * 2u * 2u * kTN * h * 2u;
   L.ytile = o;
   o += 2u * h * kYS * 4u;
   L.stage = o;
   o += (uint32_t)len * kTN * 4u;
-  L.colinv = o;
-  o += kTN * 4u;
-  L.colmax = o;  // 8 warps x 32 per-column partial maxima
+  L.colinv = o;  // per B buffer: 1/(scale 8) of each column
+  o += 2u * kTN * 4u;
+  L.colmax = o;  // 8 build warps x 32 per-column partial maxima
   o += 8u * kTN * 4u;
-  L.mbar = o;
-  o += 8;
-  L.total = (o + 1023u) & ~1023u;
+  L.mbar = o;  // bfull[2], bempty[2], afull[2], aempty[2], done
+  o += 9u * 8u;
+  L.tmem = o;
+  o += 8u;
+  L.total = o;
   return L;
 }
 
-__host__ __device__ inline uint32_t tcy_block_bytes(int len) { return kGroups * tcy_layout(len).total + 16u; }
-
-__global__ void __launch_bounds__(kNT, 1)
-    k_dst_tc_y2(const float *data, float *out, int len, int mx, long long m, long long nplanes,
+__global__ void __launch_bounds__(kNTW, 1)
+    k_dst_tc_yw(const float *data, float *out, int len, int mx, long long m, long long nplanes,
                 const __half *sop_g, State *S, int gk) {
   if (gate_closed(S, gk)) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int h = (len + 1) >> 1;
-  const TcYSmem L = tcy_layout(len);
+  const TcYwSmem L = tcyw_layout(len);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int grp = warp >> 3, gt = tid & (kGT - 1), w8 = warp & 7;
-  const int bar = 1 + grp;
-  unsigned char *gs = smem + (uint32_t)grp * L.total;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kGroups * L.total);
-  const float *colinv = reinterpret_cast<const float *>(gs + L.colinv);
-  float *stage = reinterpret_cast<float *>(gs + L.stage);
-  float *ytile = reinterpret_cast<float *>(gs + L.ytile);
-  const uint32_t mbar = smem_u32(gs + L.mbar);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+  float *stage = reinterpret_cast<float *>(smem + L.stage);
+  float *ytile = reinterpret_cast<float *>(smem + L.ytile);
+  float *colinv = reinterpret_cast<float *>(smem + L.colinv);
+  const uint32_t bbuf = 2u * 2u * kTN * h * 2u;  // one B buffer
+  const uint32_t mb = smem_u32(smem + L.mbar);
+  const uint32_t bfull = mb, bempty = mb + 16u, afull = mb + 32u, aempty = mb + 48u,
+                 done = mb + 64u;
   const int tpp = (mx + kTN - 1) / kTN;  // tiles per plane
   const long long ntiles = nplanes * tpp;
   auto tile_at = [&](long long tile, long long &base, int &je) {
@@ -425,28 +425,14 @@ __global__ void __launch_bounds__(kNT, 1)
     base = t * m + x0;
     je = min(kTN, mx - x0);
   };
-  auto prefetch = [&](long long tile) {
-    long long base;
-    int je;
-    tile_at(tile, base, je);
-    // thread gt copies column c = gt % 32 of rows gt / 32, + 8, + 16, ... (running pointers)
-    const int c = gt & (kTN - 1), e0 = gt >> 5;
-    const float *gp = data + base + (long long)e0 * mx + c;
-    const long long gstep = (long long)(kGT / kTN) * mx;
-    uint32_t sa = smem_u32(stage) + 4u * (uint32_t)gt;
-    for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
-      if (c < je)
-        cp_async4(sa, gp);
-      else
-        stage[e * kTN + c] = 0.f;
+  if (tid == 0) {
+    for (int i = 0; i < 9; ++i) {
+      uint32_t cnt = 1u;
+      if (i == 2 || i == 3) cnt = 1u + kEpiW;              // bempty: MMA commit + epilogue warps
+      if (i == 6 || i == 7) cnt = (uint32_t)kEpiW;         // aempty: every epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb + 8u * i), "r"(cnt)
+                   : "memory");
     }
-    cp_async_commit();
-  };
-  const long long first = (long long)blockIdx.x * kGroups + grp;
-  const long long tstride = (long long)kGroups * gridDim.x;
-  if (first < ntiles) prefetch(first);
-  if (gt == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -458,84 +444,171 @@ __global__ void __launch_bounds__(kNT, 1)
   fence_before();
   __syncthreads();
   fence_after();
+  if (tid == 0) {  // both B buffers and both accumulators start free
+    for (int k = 0; k < 1 + kEpiW; ++k) {
+      mbar_arrive(bempty);
+      mbar_arrive(bempty + 8u);
+    }
+    for (int k = 0; k < kEpiW; ++k) {
+      mbar_arrive(aempty);
+      mbar_arrive(aempty + 8u);
+    }
+  }
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_base = tmem;
-  const uint32_t dcol = tmem + 256u + (uint32_t)grp * 64u;
+  const uint32_t dcol = tmem + 256u;  // the two 64-column accumulators follow S
+  // S_len (four fp16 pieces) into tensor memory: warp w writes lanes 32 (w % 4).., the pieces
+  // split among the warps of that quadrant
   {
-    const int q = warp & 3, piece = warp >> 2;
-    const int r = q * 32 + lane;
-    const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
-                               (size_t)piece * kM * h * 2u;
+    const int q = warp & 3, nq = (kNTW / 32 - q + 3) / 4, r = q * 32 + lane;
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
-    for (int ks = 0; ks < h / 16; ++ks) {
-      uint32_t w[8];
-      const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
-      const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
-      w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
-      w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
-      tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
+    for (int piece = warp >> 2; piece < 4; piece += nq) {
+      const unsigned char *img = reinterpret_cast<const unsigned char *>(sop_g) +
+                                 (size_t)piece * kM * h * 2u;
+      for (int ks = 0; ks < h / 16; ++ks) {
+        uint32_t w[8];
+        const uint4 c0 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16, h));
+        const uint4 c1 = *reinterpret_cast<const uint4 *>(img + canon_off(r, ks * 16 + 8, h));
+        w[0] = c0.x; w[1] = c0.y; w[2] = c0.z; w[3] = c0.w;
+        w[4] = c1.x; w[5] = c1.y; w[6] = c1.z; w[7] = c1.w;
+        tmem_st8(a_base + lanes + (uint32_t)piece * 64u + (uint32_t)ks * 8u, w);
+      }
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
-  uint32_t phase = 0;
   bool ok = true;
-  bool outstanding = false;
-  const int q = warp & 3, P = w8 >> 2;
-  const int r = (q << 5) + lane;
-  const uint32_t tl = dcol + ((uint32_t)(q * 32) << 16) + (uint32_t)(P * kTN);
-  const bool row_ok = r < h && (P == 0 ? 2 * r + 1 : 2 * r + 2) <= len;
-  float *yrow = ytile + (P * h + r) * kYS;
-  for (long long tile = first; tile < ntiles && ok; tile += tstride) {
-    long long base;
-    int je;
-    tile_at(tile, base, je);
-    cp_async_wait_all();
-    group_sync(bar, kGT);
-    {
-      float a[2][8], b[2][8];
-      load_b_g_src(len, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, b);
-      build_b_g(gs + L.bop, reinterpret_cast<float *>(gs + L.colinv),
-                reinterpret_cast<float *>(gs + L.colmax), len, a, b, gt, bar);
-    }
-    fence_async_smem();
-    group_sync(bar, kGT);
-    fence_after();
-    if (gt == 0) issue_mmas_ta(a_base, smem_u32(gs + L.bop), h, dcol, mbar);
-    outstanding = true;
-    // the stage buffer is free (every thread has read its values): load the next tile
-    if (tile + tstride < ntiles) prefetch(tile + tstride);
-    ok = group_sync_and(mbar_wait(mbar, phase), bar, kGT);
-    if (!ok) break;
-    outstanding = false;
-    phase ^= 1u;
-    fence_after();
-    float v[32];
-    tmem_ld16(tl, v);
-    tmem_ld16(tl + 16u, v + 16);
-    if (row_ok) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) yrow[c] = v[c] * colinv[c];
-    }
-    fence_before();
-    group_sync(bar, kGT);
-    fence_after();
-    {
-      // column c of rows gt / 32, + 8, ...: rows of one parity, 4 rows apart in the Y tile
-      const int c = gt & (kTN - 1), e0 = gt >> 5;
-      if (c < je) {
-        float *op = out + base + (long long)e0 * mx + c;
-        const float *yp = ytile + ((e0 & 1) * h + (e0 >> 1)) * kYS + c;
-        const long long ostep = (long long)(kGT / kTN) * mx;
-        for (int e = e0; e < len; e += kGT / kTN, op += ostep, yp += (kGT / kTN / 2) * kYS)
-          *op = *yp;
+  uint32_t pbf[2] = {0u, 0u}, pbe[2] = {0u, 0u}, paf[2] = {0u, 0u}, pae[2] = {0u, 0u};
+  if (warp == kEpiW + kBldW) {
+    // ------------------------------------------------------------------ MMA thread
+    if (lane == 0) {
+      int u = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
+        const int b = u & 1;
+        if (!mbar_wait(bfull + 8u * b, pbf[b]) || !mbar_wait(aempty + 8u * b, pae[b])) {
+          ok = false;
+          break;
+        }
+        pbf[b] ^= 1u;
+        pae[b] ^= 1u;
+        fence_after();
+        issue_mmas_ta(a_base, smem_u32(smem + L.bop) + (uint32_t)b * bbuf, h,
+                      dcol + 64u * (uint32_t)b, afull + 8u * b);
+        mma_commit(bempty + 8u * b);
       }
+      mma_commit(done);
+    }
+    __syncwarp();
+  } else if (warp >= kEpiW) {
+    // ------------------------------------------------------------------ build warps
+    const int gt = tid - kEpiW * 32;  // 0..255
+    auto prefetch = [&](long long tile) {
+      long long base;
+      int je;
+      tile_at(tile, base, je);
+      const int c = gt & (kTN - 1), e0 = gt >> 5;
+      const float *gp = data + base + (long long)e0 * mx + c;
+      const long long gstep = (long long)(kGT / kTN) * mx;
+      uint32_t sa = smem_u32(stage) + 4u * (uint32_t)gt;
+      for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
+        if (c < je)
+          cp_async4(sa, gp);
+        else
+          stage[e * kTN + c] = 0.f;
+      }
+      cp_async_commit();
+    };
+    if (blockIdx.x < ntiles) prefetch(blockIdx.x);
+    int u = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
+      const int b = u & 1;
+      ok = group_sync_and(mbar_wait(bempty + 8u * b, pbe[b]), kBarBl, kBldW * 32);
+      if (!ok) break;
+      pbe[b] ^= 1u;
+      cp_async_wait_all();
+      group_sync(kBarBl, kBldW * 32);  // the tile is staged
+      {
+        float a[2][8], bb[2][8];
+        load_b_g_src(len, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, bb);
+        build_b_g(smem + L.bop + (uint32_t)b * bbuf, colinv + b * kTN,
+                  reinterpret_cast<float *>(smem + L.colmax), len, a, bb, gt, kBarBl);
+      }
+      // the stage has been read (the column-maximum barrier inside the build): the next tile
+      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+      fence_async_smem();
+      group_sync(kBarBl, kBldW * 32);  // the B buffer and its column factors are written
+      if (gt == 0) mbar_arrive(bfull + 8u * b);
+    }
+    cp_async_wait_all();
+  } else {
+    // ------------------------------------------------------------------ epilogue warps
+    const int q = warp, r = (q << 5) + lane;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    const bool ok0 = r < h && 2 * r + 1 <= len, ok1 = r < h && 2 * r + 2 <= len;
+    int u = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
+      const int b = u & 1;
+      long long base;
+      int je;
+      tile_at(tile, base, je);
+      ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, pbf[b]) ? 1 : 0) != 0;
+      float ci[kTN];
+      if (ok) {
+        pbf[b] ^= 1u;
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) ci[c] = colinv[b * kTN + c];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bempty + 8u * b);  // the column factors are copied
+        ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * b, paf[b]) ? 1 : 0) != 0;
+      }
+      float v0[32], v1[32];
+      if (ok) {
+        paf[b] ^= 1u;
+        fence_after();
+        const uint32_t tl = dcol + 64u * (uint32_t)b + lanes;
+        tmem_ld16(tl, v0);
+        tmem_ld16(tl + 16u, v0 + 16);
+        tmem_ld16(tl + 32u, v1);
+        tmem_ld16(tl + 48u, v1 + 16);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(aempty + 8u * b);  // the accumulator is free
+      }
+      ok = group_sync_and(ok, kBarE, kEpiW * 32);
+      if (!ok) break;
+      if (ok0) {
+        float *y0 = ytile + r * kYS;
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) y0[c] = v0[c] * ci[c];
+      }
+      if (ok1) {
+        float *y1 = ytile + (h + r) * kYS;
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) y1[c] = v1[c] * ci[c];
+      }
+      group_sync(kBarE, kEpiW * 32);
+      {
+        // column c of rows et / 32, + 4, ...: rows of one parity, 2 rows apart in the Y tile
+        const int et = tid, c = et & (kTN - 1), e0 = et >> 5;
+        if (c < je) {
+          float *op = out + base + (long long)e0 * mx + c;
+          const float *yp = ytile + ((e0 & 1) * h + (e0 >> 1)) * kYS + c;
+          const long long ostep = (long long)(kEpiW * 32 / kTN) * mx;
+          for (int e = e0; e < len; e += kEpiW * 32 / kTN, op += ostep,
+                   yp += (kEpiW * 32 / kTN / 2) * kYS)
+            *op = *yp;
+        }
+      }
+      group_sync(kBarE, kEpiW * 32);  // the Y tile is free again
     }
   }
-  cp_async_wait_all();
-  tc_release_cols<512>(ok, outstanding, mbar, phase, false, 0u, 0u, tmem, S);
+  fence_before();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  fence_after();
+  // after a timeout `done` tracks every MMA issued: tc_release_cols waits for it (bounded)
+  tc_release_cols<512>(ok, true, done, 0u, false, 0u, 0u, tmem, S, true);
 }
 
 // ------------------------------------------------------------------ time kernel: three pipelines
@@ -543,7 +616,8 @@ __global__ void __launch_bounds__(kNT, 1)
 // per SM, 4 per scheduler) cannot hide the latency of the ALU phases between the MMAs; three
 // 8-warp pipelines (24 warps) with one B buffer and one 64-column accumulator each run both
 // transforms of a tile in sequence while the other two pipelines fill the gaps (103 against
-// 110 us per 255^2 x 256 launch).  Registers are capped at 80 per thread (768 threads); tensor
+// 110 us per 255^2 x 256 launch); each pipeline stages its next tile with cp.async while the
+// current one is transformed.  Registers are capped at 80 per thread (768 threads); tensor
 // memory holds S in 256 columns and the three accumulators in 192.  The same organisation for
 // the spatial kernel was slower (79 against 54 us): its transformed rows, written from the
 // accumulator registers without a staged Y tile, left the stores uncoalesced.
@@ -1163,7 +1237,7 @@ void time_tc_build_sop(int len, unsigned short *out) {
 bool dst_tc_supported(int len) {
   const int L1 = len + 1;
   return (L1 == 32 || L1 == 64 || L1 == 128 || L1 == 256) &&
-         tcy_block_bytes(len) + 1024u <= 227u * 1024u;
+         tcyw_layout(len).total + 1024u <= 227u * 1024u;
 }
 
 int time_tc_grid() {
@@ -1202,26 +1276,25 @@ cudaError_t launch_time_tc(float *data, const Geom &g, const Spec<float> &sp,
 bool dst_tc_len_supported(int len) {
   if (dst_tc_supported(len)) return true;
   return len >= 32 && len <= 256 && (len % 32) == 0 &&
-         tcy_block_bytes(len) + 1024u <= 227u * 1024u;
+         tcyw_layout(len).total + 1024u <= 227u * 1024u;
 }
 
 // One DST-I of length len along lines `stride` apart, nplanes planes `plane` apart, 32 adjacent
-// lines per tile (k_dst_tc_y2, two tile pipelines per block, S_len in tensor memory), from `in`
-// to `out` (the same array, or one that does not overlap).
+// lines per tile (k_dst_tc_yw, S_len in tensor memory), from `in` to `out` (the same array, or
+// one that does not overlap).
 cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride, long long plane,
                                 long long nplanes, const unsigned short *sop, State *S, int gk,
                                 int kc, cudaStream_t st) {
-  const uint32_t smem_bytes = tcy_block_bytes(len);
-  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const uint32_t smem_bytes = tcyw_layout(len).total;
+  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_yw, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
-  const long long need = (ntiles + kGroups - 1) / kGroups;
   int grid = time_tc_grid();
-  if (need < grid) grid = (int)need;
+  if (ntiles < grid) grid = (int)ntiles;
   prof_begin(kc, st);
-  k_dst_tc_y2<<<grid, kNT, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
-                                             reinterpret_cast<const __half *>(sop), S, gk);
+  k_dst_tc_yw<<<grid, kNTW, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
+                                              reinterpret_cast<const __half *>(sop), S, gk);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -1381,10 +1454,6 @@ __device__ __forceinline__ void st_dd(dd *p, dd v) {
 // 2^e as a float (exact; e outside the normal range through ldexpf)
 __device__ __forceinline__ float pow2f(int e) {
   return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // 1/p in double-float with the per-row parts hoisted (the double-float form of inv_symbol):
