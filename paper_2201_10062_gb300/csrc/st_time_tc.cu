@@ -99,6 +99,21 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+// 16 columns of this warp's 32 lanes into registers; the values are valid only after
+// tmem_wait_ld (several loads may be in flight)
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   uint32_t r[16];
   asm volatile(
@@ -167,6 +182,11 @@ __device__ __forceinline__ void cp_async_commit() {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+// all but the `N` most recent commit groups of this thread are complete
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // fp16 (hi, lo) pieces of two floats, packed as half2 words
@@ -362,18 +382,20 @@ __device__ __forceinline__ void issue_mmas_ta(uint32_t a_base, uint32_t bbase, i
 // S_len (both parities, hi and lo) in tensor memory as the A operand and the phases of a tile in
 // separate warps that work on different tiles at once, handing off through mbarriers (every wait
 // bounded):
-//   - eight build warps stage the next tile with cp.async, fold, scale and split the current one
-//     into one of two B buffers (with its column factors);
+//   - eight build warps keep the loads of the next two tiles in flight (cp.async into a ring of
+//     three staging buffers) while they fold, scale and split the current one into one of two B
+//     buffers (with its column factors);
 //   - one thread issues the tile's MMAs into one of two 64-column accumulators and frees the B
 //     buffer when they complete;
 //   - four epilogue warps (one per lane quadrant, both parities of a row) take the accumulator
 //     out, unscale it into the Y tile and write the tile back row by row.
-// A B buffer is free again once its MMAs are done and every epilogue warp has copied its column
+// A B buffer is free again once its MMAs are done and every epilogue warp has applied its column
 // factors (1 + 4 arrivals), so the build may run a tile ahead of the epilogue.
 constexpr int kEpiW = 4;                              // warps 0..3: epilogue
 constexpr int kBldW = 8;                              // warps 4..11: build
 constexpr int kNTW = (kEpiW + kBldW + 1) * 32;        // and warp 12: the MMA thread (416)
 constexpr int kBarE = 1, kBarBl = 2;                  // named barriers of the two groups
+constexpr int kYwStages = 3;                          // staging ring: the tile built + 2 loading
 
 struct TcYwSmem {
   uint32_t bop, ytile, stage, colinv, colmax, mbar, tmem, total;
@@ -387,8 +409,8 @@ __host__ __device__ inline TcYwSmem tcyw_layout(int len) {
   o += 2u * 2u * 2u * kTN * h * 2u;
   L.ytile = o;
   o += 2u * h * kYS * 4u;
-  L.stage = o;
-  o += (uint32_t)len * kTN * 4u;
+  L.stage = o;  // kYwStages staged input tiles, each [len][32] floats
+  o += (uint32_t)kYwStages * len * kTN * 4u;
   L.colinv = o;  // per B buffer: 1/(scale 8) of each column
   o += 2u * kTN * 4u;
   L.colmax = o;  // 8 build warps x 32 per-column partial maxima
@@ -480,19 +502,20 @@ __global__ void __launch_bounds__(kNTW, 1)
   __syncthreads();
   fence_after();
   bool ok = true;
-  uint32_t pbf[2] = {0u, 0u}, pbe[2] = {0u, 0u}, paf[2] = {0u, 0u}, pae[2] = {0u, 0u};
+  // mbarrier phases, one bit per buffer (registers; an indexed array would live in local memory)
+  uint32_t pbf = 0u, pbe = 0u, paf = 0u, pae = 0u;
   if (warp == kEpiW + kBldW) {
     // ------------------------------------------------------------------ MMA thread
     if (lane == 0) {
       int u = 0;
       for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
         const int b = u & 1;
-        if (!mbar_wait(bfull + 8u * b, pbf[b]) || !mbar_wait(aempty + 8u * b, pae[b])) {
+        if (!mbar_wait(bfull + 8u * b, ((pbf >> b) & 1u)) || !mbar_wait(aempty + 8u * b, ((pae >> b) & 1u))) {
           ok = false;
           break;
         }
-        pbf[b] ^= 1u;
-        pae[b] ^= 1u;
+        pbf ^= 1u << b;
+        pae ^= 1u << b;
         fence_after();
         issue_mmas_ta(a_base, smem_u32(smem + L.bop) + (uint32_t)b * bbuf, h,
                       dcol + 64u * (uint32_t)b, afull + 8u * b);
@@ -504,39 +527,47 @@ __global__ void __launch_bounds__(kNTW, 1)
   } else if (warp >= kEpiW) {
     // ------------------------------------------------------------------ build warps
     const int gt = tid - kEpiW * 32;  // 0..255
-    auto prefetch = [&](long long tile) {
-      long long base;
-      int je;
-      tile_at(tile, base, je);
-      const int c = gt & (kTN - 1), e0 = gt >> 5;
-      const float *gp = data + base + (long long)e0 * mx + c;
-      const long long gstep = (long long)(kGT / kTN) * mx;
-      uint32_t sa = smem_u32(stage) + 4u * (uint32_t)gt;
-      for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
-        if (c < je)
-          cp_async4(sa, gp);
-        else
-          stage[e * kTN + c] = 0.f;
+    // the loads of `tile` into staging buffer s; one commit group per call, empty past the end
+    auto prefetch = [&](long long tile, int s) {
+      if (tile < ntiles) {
+        long long base;
+        int je;
+        tile_at(tile, base, je);
+        const int c = gt & (kTN - 1), e0 = gt >> 5;
+        const float *gp = data + base + (long long)e0 * mx + c;
+        const long long gstep = (long long)(kGT / kTN) * mx;
+        float *sp = stage + (size_t)s * len * kTN;
+        uint32_t sa = smem_u32(sp) + 4u * (uint32_t)gt;
+        for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
+          if (c < je)
+            cp_async4(sa, gp);
+          else
+            sp[e * kTN + c] = 0.f;
+        }
       }
       cp_async_commit();
     };
-    if (blockIdx.x < ntiles) prefetch(blockIdx.x);
-    int u = 0;
+    prefetch(blockIdx.x, 0);
+    prefetch((long long)blockIdx.x + gridDim.x, 1);
+    int u = 0, s = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
       const int b = u & 1;
-      ok = group_sync_and(mbar_wait(bempty + 8u * b, pbe[b]), kBarBl, kBldW * 32);
+      // buffer s + 2 (mod 3) held the tile built last trip, which every build thread has read
+      // (the barriers of that trip): the tile two ahead goes there
+      prefetch(tile + 2LL * gridDim.x, s == 0 ? 2 : s - 1);
+      ok = group_sync_and(mbar_wait(bempty + 8u * b, ((pbe >> b) & 1u)), kBarBl, kBldW * 32);
       if (!ok) break;
-      pbe[b] ^= 1u;
-      cp_async_wait_all();
+      pbe ^= 1u << b;
+      cp_async_wait_pending<2>();  // this tile's group is complete; the next two may load
       group_sync(kBarBl, kBldW * 32);  // the tile is staged
       {
+        const float *sp = stage + (size_t)s * len * kTN;
         float a[2][8], bb[2][8];
-        load_b_g_src(len, gt, [&](int t, int c) -> float { return stage[t * kTN + c]; }, a, bb);
+        load_b_g_src(len, gt, [&](int t, int c) -> float { return sp[t * kTN + c]; }, a, bb);
         build_b_g(smem + L.bop + (uint32_t)b * bbuf, colinv + b * kTN,
                   reinterpret_cast<float *>(smem + L.colmax), len, a, bb, gt, kBarBl);
       }
-      // the stage has been read (the column-maximum barrier inside the build): the next tile
-      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+      s = (s == kYwStages - 1) ? 0 : s + 1;
       fence_async_smem();
       group_sync(kBarBl, kBldW * 32);  // the B buffer and its column factors are written
       if (gt == 0) mbar_arrive(bfull + 8u * b);
@@ -553,40 +584,40 @@ __global__ void __launch_bounds__(kNTW, 1)
       long long base;
       int je;
       tile_at(tile, base, je);
-      ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, pbf[b]) ? 1 : 0) != 0;
-      float ci[kTN];
+      ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, ((pbf >> b) & 1u)) ? 1 : 0) != 0;
       if (ok) {
-        pbf[b] ^= 1u;
-#pragma unroll
-        for (int c = 0; c < kTN; ++c) ci[c] = colinv[b * kTN + c];
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bempty + 8u * b);  // the column factors are copied
-        ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * b, paf[b]) ? 1 : 0) != 0;
+        pbf ^= 1u << b;
+        ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * b, ((paf >> b) & 1u)) ? 1 : 0) != 0;
       }
-      float v0[32], v1[32];
+      uint32_t v0[2][16], v1[2][16];
       if (ok) {
-        paf[b] ^= 1u;
+        paf ^= 1u << b;
         fence_after();
         const uint32_t tl = dcol + 64u * (uint32_t)b + lanes;
-        tmem_ld16(tl, v0);
-        tmem_ld16(tl + 16u, v0 + 16);
-        tmem_ld16(tl + 32u, v1);
-        tmem_ld16(tl + 48u, v1 + 16);
+        tmem_ld16_async(tl, v0[0]);
+        tmem_ld16_async(tl + 16u, v0[1]);
+        tmem_ld16_async(tl + 32u, v1[0]);
+        tmem_ld16_async(tl + 48u, v1[1]);
+        tmem_wait_ld();
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(aempty + 8u * b);  // the accumulator is free
       }
       ok = group_sync_and(ok, kBarE, kEpiW * 32);
       if (!ok) break;
-      if (ok0) {
-        float *y0 = ytile + r * kYS;
+      {
+        // unscale by the column factors of B buffer b, read here from shared memory (the buffer
+        // is released only after this loop)
+        const float *ci = colinv + b * kTN;
+        float *y0 = ytile + r * kYS, *y1 = ytile + (h + r) * kYS;
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) y0[c] = v0[c] * ci[c];
-      }
-      if (ok1) {
-        float *y1 = ytile + (h + r) * kYS;
-#pragma unroll
-        for (int c = 0; c < kTN; ++c) y1[c] = v1[c] * ci[c];
+        for (int c = 0; c < kTN; ++c) {
+          const float f = ci[c];
+          if (ok0) y0[c] = __uint_as_float(v0[c >> 4][c & 15]) * f;
+          if (ok1) y1[c] = __uint_as_float(v1[c >> 4][c & 15]) * f;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bempty + 8u * b);  // the column factors are read
       }
       group_sync(kBarE, kEpiW * 32);
       {
@@ -1565,7 +1596,8 @@ __global__ void __launch_bounds__(kNTG, 1)
   const uint32_t dcol = tmem + (uint32_t)kDg * acol;  // the two accumulators follow S
   bool ok = true;
   // phases of bfull, bempty, afull and aempty as this thread's role waits on them
-  uint32_t pbf[2] = {0u, 0u}, pbe[2] = {0u, 0u}, paf[2] = {0u, 0u}, pae[2] = {0u, 0u};
+  // mbarrier phases, one bit per buffer (registers; an indexed array would live in local memory)
+  uint32_t pbf = 0u, pbe = 0u, paf = 0u, pae = 0u;
   uint32_t G = 0;  // digit groups this thread's role has handled (accumulator G & 1)
   MacAcc<dd> en;   // drain threads: their part of <v, P^-1 v>
   en.zero();
@@ -1599,22 +1631,22 @@ __global__ void __launch_bounds__(kNTG, 1)
         int u = 0;
         for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++u) {
           const int b = u & 1;
-          if (!mbar_wait(bfull + 8u * b, pbf[b])) {
+          if (!mbar_wait(bfull + 8u * b, ((pbf >> b) & 1u))) {
             ok = false;
             break;
           }
-          pbf[b] ^= 1u;
+          pbf ^= 1u << b;
           // descriptors differ only in their start-address field (address / 16), so each MMA
           // takes one add on a descriptor built once per tile
           const uint64_t bdesc = make_desc(smem_u32(smem + L.bdig) + (uint32_t)b * bbytes, h);
           const int ksteps = h / 16;
           for (int g = 0; g < kDg; ++g) {
             const int a = (int)(G & 1u);
-            if (!mbar_wait(aempty + 8u * a, pae[a])) {
+            if (!mbar_wait(aempty + 8u * a, ((pae >> a) & 1u))) {
               ok = false;
               break;
             }
-            pae[a] ^= 1u;
+            pae ^= 1u << a;
             fence_after();
             const uint32_t d = dcol + (uint32_t)(kTN * a);
             uint32_t acc = 0u;
@@ -1643,9 +1675,9 @@ __global__ void __launch_bounds__(kNTG, 1)
         const int b = u & 1;
         const long long j0 = tile * kTN;
         const int je = (int)min((long long)kTN, m - j0);
-        ok = group_sync_and(mbar_wait(bempty + 8u * b, pbe[b]), kBarB, kBuildW * 32);
+        ok = group_sync_and(mbar_wait(bempty + 8u * b, ((pbe >> b) & 1u)), kBarB, kBuildW * 32);
         if (!ok) break;
-        pbe[b] ^= 1u;
+        pbe ^= 1u << b;
         dd f[2][8];
         float mxv = 0.f;
 #pragma unroll
@@ -1717,8 +1749,8 @@ __global__ void __launch_bounds__(kNTG, 1)
         // each warp waits on its own (warp-uniform result); the drain group combines the results
         // once per tile, before its first named barrier, so that no warp leaves a barrier early
         if (ok) {
-          ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, pbf[b]) ? 1 : 0) != 0;
-          if (ok) pbf[b] ^= 1u;
+          ok = __all_sync(0xffffffffu, mbar_wait(bfull + 8u * b, ((pbf >> b) & 1u)) ? 1 : 0) != 0;
+          if (ok) pbf ^= 1u << b;
         }
         float cd[16];
 #pragma unroll
@@ -1738,9 +1770,9 @@ __global__ void __launch_bounds__(kNTG, 1)
           const int a = (int)(G & 1u);
           ++G;
           if (!ok) continue;
-          ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * a, paf[a]) ? 1 : 0) != 0;
+          ok = __all_sync(0xffffffffu, mbar_wait(afull + 8u * a, ((paf >> a) & 1u)) ? 1 : 0) != 0;
           if (!ok) continue;
-          paf[a] ^= 1u;
+          paf ^= 1u << a;
           fence_after();
           float v[16];
           tmem_ld16(dcol + lanes + (uint32_t)(kTN * a + c0), v);
