@@ -332,6 +332,8 @@ struct PrecPlan {
   const unsigned short *sop;  // fp16 S_n operand image for the tensor-core time kernel, or null
   const unsigned short *sop_y;  // fp16 S_my image for the tensor-core y-DST (2D/3D mixed), or null
   const unsigned short *sop_z;  // fp16 S_mz image for the tensor-core z-DST (3D mixed), or null
+  const unsigned short *sop_x;  // fp16 S_mx image for the tensor-core x-DST of the last spatial
+                                // pass (mixed), or null
   const unsigned short *sop_long;  // streamed S_n chunks for the tensor-core time kernel when
                                    // 256 < n <= 512 (mixed), or null
   const unsigned char *sdig;  // integer-digit image of S_n for the float64-accurate tensor-core
@@ -403,6 +405,8 @@ cudaError_t launch_time_tc_long(float *data, const Geom &g, const Spec<float> &s
 cudaError_t launch_dst_tc_y(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st);
 cudaError_t launch_dst_tc_z(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st);
+cudaError_t launch_dst_tc_x(float *data, const Geom &g, const unsigned short *sop, State *S,
                             int gk, cudaStream_t st);
 bool dst_tc_len_supported(int len);
 cudaError_t launch_time_tc_single(const float *in, float *out, const Geom &g,
@@ -592,7 +596,7 @@ struct st_handle {
   void *cheb;            // P_theta, 2D/3D varying a: Chebyshev scalars and scratch vectors
   // the tensor-core operand images the handle was built with (the autotuner may switch a stage
   // to its CUDA-core kernel by clearing the plan's pointer; these keep the originals)
-  const unsigned short *tc_time_img, *tc_y_img, *tc_z_img;
+  const unsigned short *tc_time_img, *tc_y_img, *tc_z_img, *tc_x_img;
   const unsigned char *tc_dig_img;  // the float64 path's digit image of S_n (see PrecPlan::sdig)
   int fp64_dd_ok;        // the float64 preconditioner may take the double-float engine
   st::State *hS;         // pinned host mirror of S

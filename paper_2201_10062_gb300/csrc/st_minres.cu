@@ -504,6 +504,7 @@ size_t workspace_bytes(const Geom &g, bool mixed, int cheb, int ugroup) {
     b += time_tc_long_bytes(g.n) + 256;
   if (mixed && g.dim >= 2 && dst_tc_supported(g.my)) b += time_tc_sop_halves(g.my) * 2 + 256;
   if (mixed && g.dim == 3 && dst_tc_supported(g.mz)) b += time_tc_sop_halves(g.mz) * 2 + 256;
+  if (mixed && dst_tc_supported(g.mx)) b += time_tc_sop_halves(g.mx) * 2 + 256;
   if (!mixed && time_tcd_supported(g.n)) b += time_tcd_bytes(g.n) + 256;  // digits of S_n
   b += 256;  // alignment of the z image
   return b;
@@ -746,7 +747,7 @@ int build_tables(st_handle *h) {
   for (size_t i = 0; i < cz.size(); ++i) cdf[cx.size() + cy.size() + i] = df_of_double(cz[i]);
   const size_t o_cdf = (o_sop + sop.size() * sizeof(unsigned short) + 255) / 256 * 256;
   // fp16 S_my / S_mz images for the tensor-core y- and z-DSTs (mixed precision, supported lengths)
-  std::vector<unsigned short> sopy, sopz;
+  std::vector<unsigned short> sopy, sopz, sopx;
   if (p.precision == ST_MIXED && g.dim >= 2 && dst_tc_supported(g.my) &&
       !(no_tc && no_tc[0] == '1')) {
     sopy.resize(time_tc_sop_halves(g.my));
@@ -757,13 +758,19 @@ int build_tables(st_handle *h) {
     sopz.resize(time_tc_sop_halves(g.mz));
     time_tc_build_sop(g.mz, sopz.data());
   }
+  // and S_mx for the tensor-core x-DST of the last spatial pass
+  if (p.precision == ST_MIXED && dst_tc_supported(g.mx) && !(no_tc && no_tc[0] == '1')) {
+    sopx.resize(time_tc_sop_halves(g.mx));
+    time_tc_build_sop(g.mx, sopx.data());
+  }
   const size_t o_sopy = (o_cdf + cdf.size() * sizeof(df) + 255) / 256 * 256;
   const size_t o_sopz = (o_sopy + sopy.size() * sizeof(unsigned short) + 255) / 256 * 256;
+  const size_t o_sopx = (o_sopz + sopz.size() * sizeof(unsigned short) + 255) / 256 * 256;
   // double-float copies of the spectral tables and twiddles for the float64 preconditioner's
   // double-float engine (each value split exactly: hi the nearest float, lo the rest)
   std::vector<dd> hdd(nd - o_mux);
   for (size_t i = o_mux; i < nd; ++i) hdd[i - o_mux] = dd(hd[i]);
-  const size_t o_dd = (o_sopz + sopz.size() * sizeof(unsigned short) + 255) / 256 * 256;
+  const size_t o_dd = (o_sopx + sopx.size() * sizeof(unsigned short) + 255) / 256 * 256;
   // integer-digit image of S_n for the float64 path's tensor-core time stage (double-float
   // engine, P_H / P-hat and constant-coefficient P_theta)
   std::vector<unsigned char> sdig;
@@ -788,6 +795,9 @@ int build_tables(st_handle *h) {
   if (!sopz.empty())
     ST_TRY(cudaMemcpy((char *)h->tables + o_sopz, sopz.data(),
                       sopz.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+  if (!sopx.empty())
+    ST_TRY(cudaMemcpy((char *)h->tables + o_sopx, sopx.data(),
+                      sopx.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
   ST_TRY(cudaMemcpy((char *)h->tables + o_dd, hdd.data(), hdd.size() * sizeof(dd),
                     cudaMemcpyHostToDevice));
   if (!sdig.empty())
@@ -859,6 +869,17 @@ int build_tables(st_handle *h) {
   h->tc_time_img = pp.sop;
   h->tc_y_img = pp.sop_y;
   h->tc_z_img = pp.sop_z;
+  // The last x pass on the tensor cores is a candidate of the autotuner (st_autotune times it
+  // against the FFT); a handle starts with the FFT, which measured faster at mx = 255 (61 against
+  // 92 us per pass at 255^2 x 256), unless ST_X_TENSOR_CORES=1.  The P_theta paths with varying
+  // a run their x passes through the Chebyshev and PCR kernels.
+  h->tc_x_img = (sopx.empty() || pp.pcr || pp.cheb)
+                    ? nullptr
+                    : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopx);
+  {
+    const char *xtc = std::getenv("ST_X_TENSOR_CORES");
+    pp.sop_x = (xtc && xtc[0] == '1') ? h->tc_x_img : nullptr;
+  }
   pp.Lx = Lx;
   pp.Ly = Ly;
   pp.Lz = Lz;
@@ -1326,6 +1347,7 @@ namespace {
 struct Knobs {
   int st_target, dst_shift, jd, jf;
   int tc_time, tc_y, tc_z;  // 1: the stage runs on the tensor cores (when the handle has them)
+  int tc_x;                 // 1: the last x pass runs on the tensor cores
   int fp64_dd, jdd;         // float64 preconditioner: double-float engine, its time-kernel tile
   int tc_dd;                // 1: the double-float engine's time stage runs on the tensor cores
 };
@@ -1340,11 +1362,13 @@ int st_autotune(st_handle *h, int reps) {
   const auto key = std::make_tuple(h->g.dim, h->g.mx, h->g.my, h->g.mz, h->g.n, (int)fp32,
                                    (h->tc_time_img ? 1 : 0) + (h->pp.pcr ? 2 : 0) +
                                        (h->pp.cheb ? 4 : 0) + (h->tc_y_img ? 8 : 0) +
-                                       (h->tc_z_img ? 16 : 0) + (h->tc_dig_img ? 32 : 0));
+                                       (h->tc_z_img ? 16 : 0) + (h->tc_dig_img ? 32 : 0) +
+                                       (h->tc_x_img ? 64 : 0));
   auto apply_engines = [&](const Knobs &k) {
     h->pp.sop = k.tc_time ? h->tc_time_img : nullptr;
     h->pp.sop_y = k.tc_y ? h->tc_y_img : nullptr;
     h->pp.sop_z = k.tc_z ? h->tc_z_img : nullptr;
+    h->pp.sop_x = k.tc_x ? h->tc_x_img : nullptr;
     h->pp.fp64_dd = h->fp64_dd_ok ? k.fp64_dd : 0;
     h->pp.time_J_dd = k.jdd;
     h->pp.sdig = k.tc_dd ? h->tc_dig_img : nullptr;
@@ -1362,7 +1386,7 @@ int st_autotune(st_handle *h, int reps) {
     }
   }
   // tune from the tensor-core configuration the handle was built with
-  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1, 1, 0, 1});
+  apply_engines(Knobs{0, 0, 0, 0, 1, 1, 1, 1, 1, 0, 1});
   cudaStream_t st = h->stream;
   const Geom &g = h->g;
   cudaEvent_t e0, e1;
@@ -1432,6 +1456,7 @@ int st_autotune(st_handle *h, int reps) {
   // then, where the tensor-core kernel exists, the faster of the two engines (short time axes
   // give the tensor-core kernel little work per tile)
   int tc_time = h->tc_time_img ? 1 : 0, tc_y = h->tc_y_img ? 1 : 0, tc_z = h->tc_z_img ? 1 : 0;
+  int tc_x = h->tc_x_img ? 1 : 0;
   if (!h->pp.sop_long) {
     const int cand[] = {16, 32, 48, 64};
     float best = 1e30f;
@@ -1454,19 +1479,20 @@ int st_autotune(st_handle *h, int reps) {
       tc_time = (ms_tc <= best) ? 1 : 0;
     }
   }
-  // 4. spatial y and z passes (float32): tensor cores against the shared-memory FFT
+  // 4. spatial passes (float32): the last x pass, y and z, tensor cores against the
+  // shared-memory FFT
   if (fp32) {
-    const unsigned short *img[2] = {h->tc_y_img, h->tc_z_img};
-    int *use[2] = {&tc_y, &tc_z};
-    for (int axis = 1; axis <= 2; ++axis) {
-      if (!img[axis - 1]) continue;
+    const unsigned short *img[3] = {h->tc_x_img, h->tc_y_img, h->tc_z_img};
+    int *use[3] = {&tc_x, &tc_y, &tc_z};
+    for (int axis = 0; axis <= 2; ++axis) {
+      if (!img[axis]) continue;
       const float ms_tc = timed([&]() {
-        return tune_run_pass(h->g, h->pp, axis, img[axis - 1], (float *)h->Z[0], h->S, st);
+        return tune_run_pass(h->g, h->pp, axis, img[axis], (float *)h->Z[0], h->S, st);
       });
       const float ms_fft = timed([&]() {
         return tune_run_pass(h->g, h->pp, axis, nullptr, (float *)h->Z[0], h->S, st);
       });
-      *use[axis - 1] = (ms_tc <= ms_fft) ? 1 : 0;
+      *use[axis] = (ms_tc <= ms_fft) ? 1 : 0;
     }
   }
   // 5. float64 preconditioner: double-float engine (the tile of its CUDA-core time kernel first,
@@ -1507,7 +1533,7 @@ int st_autotune(st_handle *h, int reps) {
     fp64_dd = (ms_dd <= ms_d) ? 1 : 0;
   }
   const Knobs chosen{h->g.st_target, h->pp.dst_shift, h->pp.time_J_d, h->pp.time_J_f, tc_time,
-                     tc_y, tc_z, fp64_dd, jdd, tc_dd};
+                     tc_y, tc_z, tc_x, fp64_dd, jdd, tc_dd};
   apply_engines(chosen);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

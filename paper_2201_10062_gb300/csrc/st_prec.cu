@@ -754,6 +754,19 @@ cudaError_t dst_y_pass(Src src, Tc *out, const Geom &g, const PrecPlan &pp, Stat
                                         tw_of<Tc>(pp, false), S, gk, pp.dst_shift, st);
 }
 
+// The last spatial pass, DST-I along x in place: the tensor cores in float32 when the plan has
+// the S_mx image, else the shared-memory FFT.
+template <class Tc, class Tout>
+cudaError_t dst_x_last_pass(Tout *z, const Geom &g, const PrecPlan &pp, State *S, int gk,
+                            cudaStream_t st) {
+  if (sizeof(Tc) == sizeof(float) && pp.sop_x != nullptr)
+    return launch_dst_tc_x(reinterpret_cast<float *>(z), g, pp.sop_x, S, gk, st);
+  const long long nx = (long long)g.n * g.my * g.mz;
+  return launch_dst<Tc, SrcArray<Tc, Tout>, Tout, true>(SrcArray<Tc, Tout>{z}, z, g.mx, pp.Lx,
+                                                        nx, g.mx, g.m, tw_of<Tc>(pp, true), S,
+                                                        gk, pp.dst_shift, st);
+}
+
 template <class Tc>
 static const Tc *twz_of(const PrecPlan &pp);
 template <>
@@ -965,8 +978,7 @@ cudaError_t prec_stages(const Geom &g, const PrecPlan &pp, Src src, Tout *z, Sta
   if (after_time && (e = cudaEventRecord(after_time, st)) != cudaSuccess) return e;
   if (g.dim == 3 && (e = dst_z_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
   if (g.dim >= 2 && (e = dst_y_pass<Tc>(Inner{z}, zt, g, pp, S, gk, st)) != cudaSuccess) return e;
-  return launch_dst<Tc, Inner, Tout, true>(Inner{z}, z, g.mx, pp.Lx, nx, g.mx, g.m,
-                                           tw_of<Tc>(pp, true), S, gk, pp.dst_shift, st);
+  return dst_x_last_pass<Tc>(z, g, pp, S, gk, st);
 }
 
 template <class Tc, class Tin, class Tout>
@@ -1039,6 +1051,10 @@ cudaError_t tune_run_pass(const Geom &g, const PrecPlan &pp, int axis,
                           const unsigned short *tc_img, float *data, State *S, cudaStream_t st) {
   PrecPlan q = pp;
   using A = SrcArray<float, float>;
+  if (axis == 0) {
+    q.sop_x = tc_img;
+    return dst_x_last_pass<float>(data, g, q, S, GK_NONE, st);
+  }
   if (axis == 1) {
     q.sop_y = tc_img;
     return dst_y_pass<float>(A{data}, data, g, q, S, GK_NONE, st);

@@ -177,6 +177,9 @@ constexpr int kYS = kTN + 1;  // padded row of the parity-split Y tile (conflict
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const float *g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const float *g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -423,6 +426,11 @@ __host__ __device__ inline TcYwSmem tcyw_layout(int len) {
   return L;
 }
 
+// XL: the lines are contiguous x-lines instead (line R holds elements R len .. R len + len - 1;
+// `nplanes` is then the number of lines and mx, m are unused).  A tile is 32 consecutive lines,
+// one contiguous block of 32 len floats, staged with 16-byte copies when the block is whole and
+// 16-byte aligned; its transformed lines are written back from the Y tile line by line.
+template <bool XL>
 __global__ void __launch_bounds__(kNTW, 1)
     k_dst_tc_yw(const float *data, float *out, int len, int mx, long long m, long long nplanes,
                 const __half *sop_g, State *S, int gk) {
@@ -439,13 +447,19 @@ __global__ void __launch_bounds__(kNTW, 1)
   const uint32_t mb = smem_u32(smem + L.mbar);
   const uint32_t bfull = mb, bempty = mb + 16u, afull = mb + 32u, aempty = mb + 48u,
                  done = mb + 64u;
-  const int tpp = (mx + kTN - 1) / kTN;  // tiles per plane
-  const long long ntiles = nplanes * tpp;
+  const int tpp = XL ? 1 : (mx + kTN - 1) / kTN;  // tiles per plane
+  const long long ntiles = XL ? (nplanes + kTN - 1) / kTN : nplanes * tpp;
   auto tile_at = [&](long long tile, long long &base, int &je) {
-    const long long t = tile / tpp;
-    const int x0 = (int)(tile - t * tpp) * kTN;
-    base = t * m + x0;
-    je = min(kTN, mx - x0);
+    if (XL) {
+      const long long r0 = tile * kTN;
+      base = r0 * len;
+      je = (int)min((long long)kTN, nplanes - r0);
+    } else {
+      const long long t = tile / tpp;
+      const int x0 = (int)(tile - t * tpp) * kTN;
+      base = t * m + x0;
+      je = min(kTN, mx - x0);
+    }
   };
   if (tid == 0) {
     for (int i = 0; i < 9; ++i) {
@@ -533,16 +547,28 @@ __global__ void __launch_bounds__(kNTW, 1)
         long long base;
         int je;
         tile_at(tile, base, je);
-        const int c = gt & (kTN - 1), e0 = gt >> 5;
-        const float *gp = data + base + (long long)e0 * mx + c;
-        const long long gstep = (long long)(kGT / kTN) * mx;
         float *sp = stage + (size_t)s * len * kTN;
-        uint32_t sa = smem_u32(sp) + 4u * (uint32_t)gt;
-        for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
-          if (c < je)
-            cp_async4(sa, gp);
-          else
-            sp[e * kTN + c] = 0.f;
+        if (XL) {
+          // the tile is one contiguous block of je lines; rows past je are never read
+          const float *gp = data + base;
+          const uint32_t sa0 = smem_u32(sp);
+          const int total = je * len;
+          if (je == kTN && (reinterpret_cast<uintptr_t>(gp) & 15u) == 0) {
+            for (int i = gt; i < total / 4; i += kGT) cp_async16(sa0 + 16u * (uint32_t)i, gp + 4 * i);
+          } else {
+            for (int i = gt; i < total; i += kGT) cp_async4(sa0 + 4u * (uint32_t)i, gp + i);
+          }
+        } else {
+          const int c = gt & (kTN - 1), e0 = gt >> 5;
+          const float *gp = data + base + (long long)e0 * mx + c;
+          const long long gstep = (long long)(kGT / kTN) * mx;
+          uint32_t sa = smem_u32(sp) + 4u * (uint32_t)gt;
+          for (int e = e0; e < len; e += kGT / kTN, gp += gstep, sa += 4u * kGT) {
+            if (c < je)
+              cp_async4(sa, gp);
+            else
+              sp[e * kTN + c] = 0.f;
+          }
         }
       }
       cp_async_commit();
@@ -563,7 +589,17 @@ __global__ void __launch_bounds__(kNTW, 1)
       {
         const float *sp = stage + (size_t)s * len * kTN;
         float a[2][8], bb[2][8];
-        load_b_g_src(len, gt, [&](int t, int c) -> float { return sp[t * kTN + c]; }, a, bb);
+        if (XL) {
+          // line c of the tile at sp + c len (len odd: the lanes' rows fall in distinct banks)
+          long long base;
+          int je;
+          tile_at(tile, base, je);
+          load_b_g_src(len, gt,
+                       [&](int t, int c) -> float { return c < je ? sp[c * len + t] : 0.f; }, a,
+                       bb);
+        } else {
+          load_b_g_src(len, gt, [&](int t, int c) -> float { return sp[t * kTN + c]; }, a, bb);
+        }
         build_b_g(smem + L.bop + (uint32_t)b * bbuf, colinv + b * kTN,
                   reinterpret_cast<float *>(smem + L.colmax), len, a, bb, gt, kBarBl);
       }
@@ -620,7 +656,14 @@ __global__ void __launch_bounds__(kNTW, 1)
         if (lane == 0) mbar_arrive(bempty + 8u * b);  // the column factors are read
       }
       group_sync(kBarE, kEpiW * 32);
-      {
+      if (XL) {
+        // line c of the tile, element e: consecutive threads write consecutive elements
+        for (int c = 0; c < je; ++c) {
+          float *op = out + base + (long long)c * len;
+          for (int e = tid; e < len; e += kEpiW * 32)
+            op[e] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+        }
+      } else {
         // column c of rows et / 32, + 4, ...: rows of one parity, 2 rows apart in the Y tile
         const int et = tid, c = et & (kTN - 1), e0 = et >> 5;
         if (c < je) {
@@ -1317,15 +1360,33 @@ cudaError_t launch_dst_tc_lines(const float *in, float *out, int len, int stride
                                 long long nplanes, const unsigned short *sop, State *S, int gk,
                                 int kc, cudaStream_t st) {
   const uint32_t smem_bytes = tcyw_layout(len).total;
-  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_yw, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_yw<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   const long long ntiles = nplanes * ((stride + kTN - 1) / kTN);
   int grid = time_tc_grid();
   if (ntiles < grid) grid = (int)ntiles;
   prof_begin(kc, st);
-  k_dst_tc_yw<<<grid, kNTW, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
-                                              reinterpret_cast<const __half *>(sop), S, gk);
+  k_dst_tc_yw<false><<<grid, kNTW, smem_bytes, st>>>(in, out, len, stride, plane, nplanes,
+                                                     reinterpret_cast<const __half *>(sop), S, gk);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+// x lines (contiguous, n*my*mz of them), in place
+cudaError_t launch_dst_tc_x(float *data, const Geom &g, const unsigned short *sop, State *S,
+                            int gk, cudaStream_t st) {
+  const uint32_t smem_bytes = tcyw_layout(g.mx).total;
+  cudaError_t e = cudaFuncSetAttribute(k_dst_tc_yw<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  const long long nlines = (long long)g.n * g.my * g.mz;
+  const long long ntiles = (nlines + kTN - 1) / kTN;
+  int grid = time_tc_grid();
+  if (ntiles < grid) grid = (int)ntiles;
+  prof_begin(KC_DSTX, st);
+  k_dst_tc_yw<true><<<grid, kNTW, smem_bytes, st>>>(data, data, g.mx, 0, 0, nlines,
+                                                    reinterpret_cast<const __half *>(sop), S, gk);
   prof_end(st);
   return cudaGetLastError();
 }

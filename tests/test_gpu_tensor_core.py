@@ -150,3 +150,44 @@ def test_fp64_time_digits_match_oracle(pkg, dim, mx, my, n, scheme, theta, var, 
     assert _rel2(u.cpu().numpy().reshape(n, p.m), x_or) <= 1e-10
     s_tc.close()
     s_cc.close()
+
+
+# The last x pass of the preconditioner on the tensor cores (k_dst_tc_yw over contiguous x-lines,
+# 32 lines per tile): a candidate that st_autotune times against the shared-memory FFT, forced on
+# here with ST_X_TENSOR_CORES=1.  mx + 1 in {32, 64, 128, 256}; line counts n my mz with a ragged
+# last tile (40 * 15 = 600, 24 * 7 * 7 = 1176) and whole tiles; 1D, 2D and 3D.
+@pytest.mark.parametrize("dim,mx,my,n,scheme,theta", [
+    (1, 63, 1, 40, "theta", 1.0),
+    (2, 31, 15, 40, "theta", 0.5),
+    (2, 127, 63, 64, "bdf2", 1.0),
+    (2, 255, 31, 32, "theta", 0.5),
+    (3, 31, 7, 24, "theta", 1.0),
+])
+def test_tc_x_pass_matches_oracle_and_fft(pkg, dim, mx, my, n, scheme, theta):
+    w = W.small_case(dim, mx, my, n, scheme=scheme, theta=theta, varcoef=True, seed=3 * n + my,
+                     mz=my)
+    p = H.Problem.from_workload(w)
+    v = np.random.default_rng(10).standard_normal((n, p.m))
+    ref = H.apply_prec(p, v)
+    spec = pkg.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, "PH", "mixed",
+                           0, w.mz)
+    s_fft = pkg.Solver(spec)
+    z_fft = s_fft.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    os.environ["ST_X_TENSOR_CORES"] = "1"
+    try:
+        s_tc = pkg.Solver(spec)
+    finally:
+        del os.environ["ST_X_TENSOR_CORES"]
+    z_tc = s_tc.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    assert _rel2(z_tc.reshape(n, p.m), ref) <= 2e-5
+    assert _rel2(z_fft.reshape(n, p.m), ref) <= 2e-5
+    assert _rel2(z_tc, z_fft) <= 2e-5
+    assert not np.array_equal(z_tc, z_fft)  # a different kernel ran
+    # a mixed solve through it reaches the oracle's converged solution
+    fH = H.rhs(p, w.f, w.u0, w.u_prev)
+    x_ref, _ = H.solve(p, fH, tol=1e-13, maxit=800)
+    u, st = s_tc.st_solve(torch.tensor(fH, device="cuda").reshape(-1), tol=1e-9, maxit=800)
+    assert st["true_rel_res"] <= 1e-9
+    assert _rel2(u.cpu().numpy().reshape(n, p.m), x_ref) <= 1e-8
+    s_fft.close()
+    s_tc.close()
