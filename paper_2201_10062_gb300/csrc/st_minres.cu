@@ -124,7 +124,37 @@ __device__ __forceinline__ float4 lds_f4(const float4 *p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kNT, 4)
+// The G steps of one element: d_j = dz_j z_j + d1_j d_{j-1} + d2_j d_{j-2}, x += xc_j d_j, with the
+// scalars of each pending iteration read from shared memory.
+__device__ __forceinline__ void upd_steps(const float (&zv)[kUpdRing], int np,
+                                          const float4 (*sc)[2], df &d1, df &d2, float &xs,
+                                          float &xt) {
+#pragma unroll
+  for (int j = 0; j < kUpdRing; ++j) {
+    if (j < np) {
+      const float4 a = lds_f4(&sc[j][0]), b = lds_f4(&sc[j][1]);
+      const df cz{a.x, a.y}, c1{a.z, a.w}, c2{b.x, b.y}, cx{b.z, b.w};
+      // the sum starts as the exact product cz.hi z plus its low-order terms
+      float s, t;
+      two_prod(cz.hi, zv[j], s, t);
+      t = fmaf(cz.lo, zv[j], t);
+      dacc_prod(s, t, c1, d1);
+      dacc_prod(s, t, c2, d2);
+      const df d = df_from_sum(s, t);
+      dacc_prod(xs, xt, cx, d);
+      const df xn = df_from_sum(xs, xt);
+      xs = xn.hi;
+      xt = xn.lo;
+      d2 = d1;
+      d1 = d;
+    }
+  }
+}
+
+// ILP elements per thread and trip (ILP = 2: two elements a grid stride apart, every load of
+// both issued before the arithmetic of either; three blocks per SM instead of four)
+template <int ILP>
+__global__ void __launch_bounds__(kNT, ILP == 1 ? 4 : 3)
     k_update_group_df(long long N, ZRing zr, df *__restrict__ da, df *__restrict__ db,
                       df *__restrict__ x, State *S) {
   // per pending iteration: {dz.hi, dz.lo, d1.hi, d1.lo}, {d2.hi, d2.lo, xc.hi, xc.lo}
@@ -140,38 +170,37 @@ __global__ void __launch_bounds__(kNT, 4)
   }
   if (threadIdx.x < np) sz[threadIdx.x] = zr.p[(u + threadIdx.x) % zr.len];
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)kNT + threadIdx.x; i < N;
-       i += (long long)gridDim.x * kNT) {
-    float zv[kUpdRing];
+  const long long stride = (long long)gridDim.x * kNT;
+  for (long long i0 = blockIdx.x * (long long)kNT + threadIdx.x; i0 < N; i0 += ILP * stride) {
+    float zv[ILP][kUpdRing];
+    df d1[ILP], d2[ILP];
+    float xs[ILP], xt[ILP];
+    bool in[ILP];
 #pragma unroll
-    for (int j = 0; j < kUpdRing; ++j)
-      if (j < np) zv[j] = sz[j][i];
-    df d1 = da[i], d2 = db[i];
-    const df xo = x[i];
-    float xs = xo.hi, xt = xo.lo;
+    for (int e = 0; e < ILP; ++e) {
+      const long long i = i0 + e * stride;
+      in[e] = i < N;
+      if (in[e]) {
 #pragma unroll
-    for (int j = 0; j < kUpdRing; ++j) {
-      if (j < np) {
-        const float4 a = lds_f4(&sc[j][0]), b = lds_f4(&sc[j][1]);
-        const df cz{a.x, a.y}, c1{a.z, a.w}, c2{b.x, b.y}, cx{b.z, b.w};
-        // the sum starts as the exact product cz.hi z plus its low-order terms
-        float s, t;
-        two_prod(cz.hi, zv[j], s, t);
-        t = fmaf(cz.lo, zv[j], t);
-        dacc_prod(s, t, c1, d1);
-        dacc_prod(s, t, c2, d2);
-        const df d = df_from_sum(s, t);
-        dacc_prod(xs, xt, cx, d);
-        const df xn = df_from_sum(xs, xt);
-        xs = xn.hi;
-        xt = xn.lo;
-        d2 = d1;
-        d1 = d;
+        for (int j = 0; j < kUpdRing; ++j)
+          if (j < np) zv[e][j] = sz[j][i];
+        d1[e] = da[i];
+        d2[e] = db[i];
+        const df xo = x[i];
+        xs[e] = xo.hi;
+        xt[e] = xo.lo;
       }
     }
-    da[i] = d1;
-    db[i] = d2;
-    x[i] = df{xs, xt};
+#pragma unroll
+    for (int e = 0; e < ILP; ++e) {
+      if (in[e]) {
+        const long long i = i0 + e * stride;
+        upd_steps(zv[e], np, sc, d1[e], d2[e], xs[e], xt[e]);
+        da[i] = d1[e];
+        db[i] = d2[e];
+        x[i] = df{xs[e], xt[e]};
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -276,6 +305,16 @@ cudaError_t launch_fill(long long N, double *p, double v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// elements per thread and trip of the grouped update: two (220.7 against 244.6 us per 8-iteration
+// pass at 255^2 x 256, the same iterates), or one with ST_UPDATE_ILP=1
+int update_ilp() {
+  static const int v = [] {
+    const char *e = std::getenv("ST_UPDATE_ILP");
+    return (e && e[0] == '1') ? 1 : 2;
+  }();
+  return v;
+}
+
 float *zslot(st_handle *h, int s) { return s < 2 ? (float *)h->Z[s] : h->Zx[s - 2]; }
 
 // applies every pending direction/solution update of a mixed solve (see k_update_group_df); the
@@ -285,8 +324,12 @@ cudaError_t launch_update_group(st_handle *h, cudaStream_t st) {
   zr.len = h->ugroup + 1;
   for (int s = 0; s < zr.len; ++s) zr.p[s] = zslot(h, s);
   prof_begin(KC_UPDATE, st);
-  k_update_group_df<<<kStreamBlocks, kNT, 0, st>>>(h->g.N, zr, (df *)h->D[0], (df *)h->D[1],
-                                                   h->Xdf, h->S);
+  if (update_ilp() == 2)
+    k_update_group_df<2><<<kStreamBlocks, kNT, 0, st>>>(h->g.N, zr, (df *)h->D[0],
+                                                        (df *)h->D[1], h->Xdf, h->S);
+  else
+    k_update_group_df<1><<<kStreamBlocks, kNT, 0, st>>>(h->g.N, zr, (df *)h->D[0],
+                                                        (df *)h->D[1], h->Xdf, h->S);
   prof_end(st);
   return cudaGetLastError();
 }
