@@ -912,16 +912,16 @@ int build_tables(st_handle *h) {
   h->tc_time_img = pp.sop;
   h->tc_y_img = pp.sop_y;
   h->tc_z_img = pp.sop_z;
-  // The last x pass on the tensor cores is a candidate of the autotuner (st_autotune times it
-  // against the FFT); a handle starts with the FFT, which measured faster at mx = 255 (61 against
-  // 92 us per pass at 255^2 x 256), unless ST_X_TENSOR_CORES=1.  The P_theta paths with varying
-  // a run their x passes through the Chebyshev and PCR kernels.
+  // The last x pass runs on the tensor cores where mx + 1 allows (41.8 against 61.1 us per pass
+  // for the FFT at 255^2 x 256); st_autotune times both, and ST_X_TENSOR_CORES=0 starts a handle
+  // with the FFT.  The P_theta paths with varying a run their x passes through the Chebyshev and
+  // PCR kernels.
   h->tc_x_img = (sopx.empty() || pp.pcr || pp.cheb)
                     ? nullptr
                     : reinterpret_cast<const unsigned short *>((const char *)h->tables + o_sopx);
   {
     const char *xtc = std::getenv("ST_X_TENSOR_CORES");
-    pp.sop_x = (xtc && xtc[0] == '1') ? h->tc_x_img : nullptr;
+    pp.sop_x = (xtc && xtc[0] == '0') ? nullptr : h->tc_x_img;
   }
   pp.Lx = Lx;
   pp.Ly = Ly;

@@ -404,14 +404,19 @@ struct TcYwSmem {
   uint32_t bop, ytile, stage, colinv, colmax, mbar, tmem, total;
 };
 
+// x lines write a tile back element by element along each line, so consecutive threads read
+// rows e/2 of alternating parity: the odd-parity rows are shifted by this many floats so that the
+// two parities fall 16 banks apart (h is 16, 32, 64 or 128)
+__host__ __device__ inline int yw_odd_off(int h) { return (16 - h) & 31; }
+
 __host__ __device__ inline TcYwSmem tcyw_layout(int len) {
   const int h = (len + 1) / 2;
   TcYwSmem L{};
   uint32_t o = 0;
   L.bop = o;  // two B buffers, each [parity][piece][32][h] fp16
   o += 2u * 2u * 2u * kTN * h * 2u;
-  L.ytile = o;
-  o += 2u * h * kYS * 4u;
+  L.ytile = o;  // (x lines: the odd-parity rows start 16 banks over, see yw_odd_off)
+  o += 2u * h * kYS * 4u + 64u;
   L.stage = o;  // kYwStages staged input tiles, each [len][32] floats
   o += (uint32_t)kYwStages * len * kTN * 4u;
   L.colinv = o;  // per B buffer: 1/(scale 8) of each column
@@ -614,6 +619,11 @@ __global__ void __launch_bounds__(kNTW, 1)
     const int q = warp, r = (q << 5) + lane;
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
     const bool ok0 = r < h && 2 * r + 1 <= len, ok1 = r < h && 2 * r + 2 <= len;
+    const int odd = XL ? yw_odd_off(h) : 0;  // shift of the odd-parity rows in the Y tile
+    // x lines: thread tid writes elements tid and tid + 128 of every line (len <= 255); their
+    // places in the parity-split Y tile
+    const int xo0 = (tid >> 1) * kYS + (tid & 1) * (h * kYS + odd), xo1 = xo0 + 64 * kYS;
+    const bool xw0 = tid < len, xw1 = tid + 128 < len;
     int u = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++u) {
       const int b = u & 1;
@@ -645,7 +655,7 @@ __global__ void __launch_bounds__(kNTW, 1)
         // unscale by the column factors of B buffer b, read here from shared memory (the buffer
         // is released only after this loop)
         const float *ci = colinv + b * kTN;
-        float *y0 = ytile + r * kYS, *y1 = ytile + (h + r) * kYS;
+        float *y0 = ytile + r * kYS, *y1 = ytile + (h + r) * kYS + odd;
 #pragma unroll
         for (int c = 0; c < kTN; ++c) {
           const float f = ci[c];
@@ -657,11 +667,12 @@ __global__ void __launch_bounds__(kNTW, 1)
       }
       group_sync(kBarE, kEpiW * 32);
       if (XL) {
-        // line c of the tile, element e: consecutive threads write consecutive elements
-        for (int c = 0; c < je; ++c) {
-          float *op = out + base + (long long)c * len;
-          for (int e = tid; e < len; e += kEpiW * 32)
-            op[e] = ytile[((e & 1) * h + (e >> 1)) * kYS + c];
+        // line c of the tile: consecutive threads write consecutive elements
+        float *op = out + base;
+        const float *yc = ytile;
+        for (int c = 0; c < je; ++c, op += len, ++yc) {
+          if (xw0) op[tid] = yc[xo0];
+          if (xw1) op[tid + 128] = yc[xo1];
         }
       } else {
         // column c of rows et / 32, + 4, ...: rows of one parity, 2 rows apart in the Y tile

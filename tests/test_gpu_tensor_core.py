@@ -153,8 +153,8 @@ def test_fp64_time_digits_match_oracle(pkg, dim, mx, my, n, scheme, theta, var, 
 
 
 # The last x pass of the preconditioner on the tensor cores (k_dst_tc_yw over contiguous x-lines,
-# 32 lines per tile): a candidate that st_autotune times against the shared-memory FFT, forced on
-# here with ST_X_TENSOR_CORES=1.  mx + 1 in {32, 64, 128, 256}; line counts n my mz with a ragged
+# 32 lines per tile), which a handle takes by default where mx + 1 allows, against the
+# shared-memory FFT that ST_X_TENSOR_CORES=0 selects.  mx + 1 in {32, 64, 128, 256}; line counts n my mz with a ragged
 # last tile (40 * 15 = 600, 24 * 7 * 7 = 1176) and whole tiles; 1D, 2D and 3D.
 @pytest.mark.parametrize("dim,mx,my,n,scheme,theta", [
     (1, 63, 1, 40, "theta", 1.0),
@@ -171,14 +171,14 @@ def test_tc_x_pass_matches_oracle_and_fft(pkg, dim, mx, my, n, scheme, theta):
     ref = H.apply_prec(p, v)
     spec = pkg.ProblemSpec(w.dim, w.mx, w.my, w.n, w.T, w.scheme, w.theta, w.a_nodal, "PH", "mixed",
                            0, w.mz)
-    s_fft = pkg.Solver(spec)
-    z_fft = s_fft.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
-    os.environ["ST_X_TENSOR_CORES"] = "1"
+    s_tc = pkg.Solver(spec)
+    z_tc = s_tc.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    os.environ["ST_X_TENSOR_CORES"] = "0"
     try:
-        s_tc = pkg.Solver(spec)
+        s_fft = pkg.Solver(spec)
     finally:
         del os.environ["ST_X_TENSOR_CORES"]
-    z_tc = s_tc.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
+    z_fft = s_fft.st_apply_prec_f32(torch.tensor(v, device="cuda")).cpu().numpy().astype(np.float64)
     assert _rel2(z_tc.reshape(n, p.m), ref) <= 2e-5
     assert _rel2(z_fft.reshape(n, p.m), ref) <= 2e-5
     assert _rel2(z_tc, z_fft) <= 2e-5
