@@ -63,13 +63,14 @@ CLASS_BYTES = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of every
 # launch of one mixed 2D Crank-Nicolson solve at 255^2 x 256), per kernel class, for the kernels
 # whose code is unchanged since: profiles/dram_traffic_mixed_cn2d_255x255_n256.md
+# (the last x pass, now on the tensor cores, and the grouped update, now two elements per
+# thread, have changed since, so they report none)
 NCU_TRAFFIC = {("mixed", "stencil"): 136.0e6, ("mixed", "lanczos_dst_x"): 539.6e6,
-               ("mixed", "dst_x"): 70.3e6, ("mixed", "residual"): 373.3e6}
-# the grouped update's DRAM bytes per solve (its six launches in the same capture)
-NCU_TRAFFIC_STEP = {("mixed", "update"): 6 * 1212.5e6}
-# the same capture summed over the solve's iteration kernels (stencil, fused Lanczos x pass, y,
-# time, y, x, grouped update), per unknown and iteration
-NCU_ITER_TRAFFIC = {"mixed": 71.5}
+               ("mixed", "residual"): 373.3e6}
+NCU_TRAFFIC_STEP = {}
+# the same capture summed over the solve's iteration kernels, per unknown and iteration: none
+# while two of those kernels differ from the captured ones
+NCU_ITER_TRAFFIC = {"mixed": None}
 # steps of the per-kernel-class profile, run after each timed region
 PROF_STEPS = 3
 
