@@ -12,8 +12,8 @@
 //
 // S (both parities, both pieces: 128 KB for n = 256) lives in tensor memory as the A operand of
 // tcgen05.mma; one block per SM walks tiles of 32 columns: the time kernel (k_time_tc3) runs three
-// independent 8-warp tile pipelines, the spatial one (k_dst_tc_yw) splits build, MMA issue and
-// epilogue over separate warps.
+// independent 8-warp tile pipelines, the spatial one (k_dst_tc_yw: strided y and z lines, or
+// contiguous x lines) splits build, MMA issue and epilogue over separate warps.
 // One thread per pipeline issues tcgen05.mma (M = 128, N = 32, K = 16; B from a shared-memory
 // descriptor, no swizzle, K-major core matrices of 8 rows x 16 bytes), tcgen05.commit signals the
 // pipeline's mbarrier, and its warps read the accumulators with tcgen05.ld.  For 256 < n <= 512
